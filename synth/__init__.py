@@ -1,0 +1,116 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the benchmark.
+
+This module holds none of the method's arithmetic: it only draws matrices and right-hand
+sides with the shapes and value distributions of the workloads (the paper factors dense
+double-precision SPD matrices of order 8192 and 16384 with 512 x 512 tiles, Section 4.1
+"Methodology" and Section 4.2; it does not say how the matrices are drawn, so the recipes
+below stand in for them).
+
+Random numbers come from torch's seeded generators on the device the data is made on; a
+test that feeds the same input to the oracle and to the CUDA library makes it once and
+copies the bytes, so both sides always see identical values.
+
+Recipes
+  gram_spd(n)         A = sym(G G^T)/n + I, G n x n i.i.d. N(0,1) drawn in FP32, product in
+                      FP32 (TF32 off), symmetrised and promoted to FP64; kappa(A) <~ 5.
+  householder_spd(n)  A = Q diag(lambda) Q^T, lambda_i = 10^(6 i/(n-1)), Q = H_1 ... H_32,
+                      H = I - 2 v v^T / v^T v with v ~ N(0,1); kappa(A) = 1e6.
+  integer_factor(n)   integer lower L, diag in [1, 8], off-diagonal in [-8, 8]; A = L L^T is
+                      then exact in FP64 (|a_ij| <= 64 n < 2^53).
+  pascal(n)           P_ij = C(i + j, i) (0-based).
+"""
+import math
+
+import numpy as np
+import torch
+
+
+def _gen(seed, device):
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    return g
+
+
+def gram_spd(n, seed=0, device="cpu"):
+    """A = sym(G G^T)/n + I in float64 (column-major friendly: A is symmetric)."""
+    device = torch.device(device)
+    g = _gen(seed, device)
+    G = torch.randn(n, n, generator=g, device=device, dtype=torch.float32)
+    prev = None
+    if device.type == "cuda":
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        S = G @ G.T
+    finally:
+        if prev is not None:
+            torch.backends.cuda.matmul.allow_tf32 = prev
+    del G
+    A = S.to(torch.float64)
+    del S
+    A = (A + A.T) * (0.5 / n)
+    A.diagonal().add_(1.0)
+    return A
+
+
+def rhs(n, nrhs, seed=1, device="cpu"):
+    """B n x nrhs i.i.d. N(0,1) in float64, column-major (Fortran) layout."""
+    device = torch.device(device)
+    g = _gen(seed, device)
+    B = torch.randn(nrhs, n, generator=g, device=device, dtype=torch.float64)
+    return B.T  # n x nrhs view whose columns are contiguous
+
+
+def householder_spd(n, seed=0, device="cpu", n_reflectors=32, cond=1e6):
+    """A = Q diag(lambda) Q^T with geometrically spaced lambda in [1, cond]."""
+    device = torch.device(device)
+    g = _gen(seed, device)
+    lam = torch.pow(torch.tensor(10.0, dtype=torch.float64, device=device),
+                    torch.arange(n, dtype=torch.float64, device=device) * (math.log10(cond) / max(n - 1, 1)))
+    A = torch.diag(lam)
+    for _ in range(n_reflectors):
+        v = torch.randn(n, generator=g, device=device, dtype=torch.float64)
+        beta = 2.0 / torch.dot(v, v)
+        # H A H with H = I - beta v v^T, applied as two rank-one updates
+        w = A @ v
+        A -= beta * torch.outer(v, w)
+        w = A @ v
+        A -= beta * torch.outer(w, v)
+    A = 0.5 * (A + A.T)
+    return A
+
+
+def integer_factor(n, seed=0):
+    """(L, A) with L integer lower triangular and A = L L^T exact, both float64 numpy."""
+    rng = np.random.default_rng(seed)
+    L = np.tril(rng.integers(-8, 9, size=(n, n)), -1).astype(np.float64)
+    L[np.arange(n), np.arange(n)] = rng.integers(1, 9, size=n)
+    A = L @ L.T  # every partial sum is an integer below 2^53: exact in any order
+    return L, A
+
+
+def integer_vector(n, nrhs, seed=0):
+    rng = np.random.default_rng(seed + 7919)
+    return rng.integers(-4, 5, size=(n, nrhs)).astype(np.float64)
+
+
+def pascal(n):
+    P = np.empty((n, n), dtype=np.float64)
+    for i in range(n):
+        for j in range(n):
+            P[i, j] = math.comb(i + j, i)
+    return P
+
+
+def pascal_lower(n):
+    Lp = np.zeros((n, n), dtype=np.float64)
+    for i in range(n):
+        for j in range(i + 1):
+            Lp[i, j] = math.comb(i, j)
+    return Lp
+
+
+def batch_orders(count, lo=16, hi=512, seed=0):
+    """Orders of a batch of matrices, uniform on [lo, hi]."""
+    rng = np.random.default_rng(seed)
+    return rng.integers(lo, hi + 1, size=count).astype(np.int32)
