@@ -1,0 +1,324 @@
+"""Benchmark: FP64 tiled Cholesky factor + forward/backward solve on GB300.
+
+One step = one pass of the whole hot path over one synthetic input: restore A from its
+pristine copy (the factor works in place), chol_factor (init + persistent data-flow kernel),
+chol_solve (forward and back substitution sweeps). Default workload: n = 32768, tile 256,
+64 right-hand sides, HEFT ready-queue policy; A = sym(G G^T)/n + I with G ~ N(0, 1).
+
+Metric: GFLOP/s with n^3/3 flops for the factor plus 2 n^2 nrhs for the two sweeps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--nb 256] [--policy heft] ...
+  python bench.py --impl reference     # the oracle on the host cores (bounded sample)
+
+Under torchrun (N > 1) every rank factors its own matrix on its own GPU (replicas: the
+method has no exchange step on one GPU); the timed region is bracketed by barriers and the
+maximum time over ranks is used; rank 0 prints the JSON line.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SMS = 152
+FP64_FMA_PER_CLK_PER_SM = 2       # measured: DFMA retires 2 FMA/clk/SM on sm_103 (probe ~1197 GFLOP/s)
+SM_MAX_MHZ = 2070.0
+FP64_PEAK_GFLOPS = SMS * FP64_FMA_PER_CLK_PER_SM * 2 * SM_MAX_MHZ / 1000.0  # 1258.6
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=32768)
+    p.add_argument("--nb", type=int, default=256)
+    p.add_argument("--nrhs", type=int, default=64)
+    p.add_argument("--policy", default="heft")
+    p.add_argument("--alpha", type=float, default=0.5)
+    p.add_argument("--workers-per-sm", type=int, default=2)
+    p.add_argument("--e2e-steps", type=int, default=1)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample-n", type=int, default=6144)
+    p.add_argument("--seed", type=int, default=1)
+    return p.parse_args()
+
+
+def step_flops(n, nrhs):
+    return n ** 3 / 3.0 + 2.0 * n * n * nrhs
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        out.update(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=sorted(reasons), samples=len(rows),
+                   power_w_max=max([num(r[3]) for r in rows if num(r[3]) is not None] or [0.0]))
+        return out
+
+
+# ----------------------------------------------------------------------------- oracle arm
+def oracle_step(n, nrhs, seed):
+    """One factor + solve by the oracle on host cores; returns (seconds, flops)."""
+    import oracle
+    import synth
+    A = synth.gram_spd(n, seed=seed).numpy()
+    B = synth.rhs(n, nrhs, seed=seed + 1).numpy()
+    t0 = time.perf_counter()
+    L = oracle.factor(A)
+    oracle.solve(L, B)
+    return time.perf_counter() - t0, step_flops(n, nrhs)
+
+
+def cpu_baseline(args):
+    import oracle
+    t, f = oracle_step(args.cpu_sample_n, args.nrhs, args.seed)
+    return {"value": round(f / t / 1e9, 3), "unit": "GFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "seconds": round(t, 2),
+            "sample": "oracle (plain C, FP64, unblocked) factor + solve of one n=%d Gram matrix with %d RHS, "
+                      "same generator as the GPU workload" % (args.cpu_sample_n, args.nrhs)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    for _ in range(args.warmup):
+        oracle_step(args.cpu_sample_n, args.nrhs, args.seed)
+    tt, ff = 0.0, 0.0
+    for _ in range(args.steps):
+        t, f = oracle_step(args.cpu_sample_n, args.nrhs, args.seed)
+        tt += t
+        ff += f
+    v = ff / tt / 1e9
+    line = {
+        "metric": "Cholesky GFLOP/s (FP64 factor + solve)", "value": round(v, 3), "unit": "GFLOP/s",
+        "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(tt / args.steps * 1000, 2), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args),
+        "cpu_baseline": {"value": round(v, 3), "unit": "GFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": "each step: oracle factor + solve of one n=%d Gram matrix with %d RHS (a bounded "
+                                   "sample of the n=%d workload)" % (args.cpu_sample_n, args.nrhs, args.n)},
+        "e2e": {"value": round(v, 3), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args):
+    return {"workload": "FP64 tiled Cholesky factor + solve, n=%d, tile %d, %d RHS, %s ready queues%s; "
+                        "A = sym(G G^T)/n + I, G ~ N(0,1)" % (
+                            args.n, args.nb, args.nrhs, args.policy.upper(),
+                            " alpha=%g" % args.alpha if args.policy == "dada" else ""),
+            "n": args.n, "nb": args.nb, "nrhs": args.nrhs, "policy": args.policy, "alpha": args.alpha,
+            "workers_per_sm": args.workers_per_sm,
+            "l2": "inputs larger than L2 (A is %.1f GB)" % (args.n * args.n * 8 / 1e9),
+            "parallelism": "replicas x%d" % args.gpus}
+
+
+# ----------------------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import synth
+    import paper_1402_6601_gb300 as chol
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    n, nb, nrhs = args.n, args.nb, args.nrhs
+    o = chol.opts(nb=nb, policy=args.policy, alpha=args.alpha, workers_per_sm=args.workers_per_sm)
+    A0 = chol.colmajor(synth.gram_spd(n, seed=args.seed + rank, device=dev))
+    B0 = chol.colmajor(synth.rhs(n, nrhs, seed=args.seed + 1000 + rank, device=dev))
+    A = torch.empty_like(A0)
+    B = torch.empty_like(B0)
+    work = torch.empty(chol.workspace_size(n, o), dtype=torch.uint8, device=dev)
+    swork = torch.empty(chol.solve_workspace_size(n, nrhs), dtype=torch.uint8, device=dev)
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    launches_per_step = 7  # init, bottom levels, persistent factor, info copy; 2 sweeps, info copy
+
+    def step(ev=None):
+        A.copy_(A0)
+        B.copy_(B0)
+        if ev is not None:
+            ev[0].record(stream)
+        chol.factor(A, o, work=work, info=info, stream=stream)
+        if ev is not None:
+            ev[1].record(stream)
+        chol.solve(A, B, work=swork, info=info, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if int(info.item()) != 0:
+        raise RuntimeError("factor info %d" % int(info.item()))
+
+    clocks = ClockSampler(local)
+    fac_events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+    e_start = torch.cuda.Event(enable_timing=True)
+    e_end = torch.cuda.Event(enable_timing=True)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e_start.record(stream)
+    for k in range(args.steps):
+        step(fac_events[k])
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e_start.elapsed_time(e_end)
+    fac_ms = [a.elapsed_time(b) for a, b in fac_events]
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    total_flops = step_flops(n, nrhs) * args.steps * world
+    value = total_flops / (ms / 1000.0) / 1e9
+
+    # correctness of the timed result (cheap O(n^2 nrhs) check on the device)
+    R = B0 - torch.mm(A0, B)
+    berr = float((R.abs().amax(0) / (A0.abs().sum(1).amax() * B.abs().amax(0) + B0.abs().amax(0))).amax())
+
+    fac_avg = sum(fac_ms) / len(fac_ms)
+    achieved = n ** 3 / 3.0 / (fac_avg / 1000.0) / 1e9
+    roofline = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(FP64_PEAK_GFLOPS, 1),
+                "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": None,
+                "kernel": "factor_kernel (persistent data-flow, DFMA tile bodies)",
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz (DFMA; FP64 mma.sync is "
+                               "slower on sm_103)"}
+
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        e2e = run_e2e(args, chol, A0, B0, o, dev)
+    barrier()
+
+    del A, B, work, R
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        cpu = cpu_baseline(args)
+
+    if rank == 0:
+        line = {
+            "metric": "Cholesky GFLOP/s (FP64 factor + solve)", "value": round(value, 2), "unit": "GFLOP/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms / args.steps, 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args),
+            "factor_ms": round(fac_avg, 2), "solve_backward_error": berr,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
+                       "reasons": clk.get("reasons"), "samples": clk.get("samples"),
+                       "power_w_max": clk.get("power_w_max")},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, chol, A0, B0, o, dev):
+    """Same metric through chol_posv_host with pinned host buffers: every step copies A and B
+    to the device, factors, solves and copies L and X back inside the timed region."""
+    import torch
+    n, nrhs = args.n, args.nrhs
+    hA0 = A0.cpu().numpy()   # Fortran-ordered (column-major) host copy
+    hB0 = B0.cpu().numpy()
+    pA = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()  # column-major pinned
+    pB = torch.empty((nrhs, n), dtype=torch.float64, pin_memory=True).t()
+    hA = pA.numpy()
+    hB = pB.numpy()
+    stage = torch.empty(chol.lib.chol_posv_host_stage_size(n, nrhs, __import__("ctypes").byref(o)),
+                        dtype=torch.uint8, device=dev)
+    tt = 0.0
+    for _ in range(max(1, args.e2e_steps)):
+        hA[...] = hA0
+        hB[...] = hB0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = chol.posv_host(hA, hB, o, stage=stage)
+        tt += time.perf_counter() - t0
+        if info != 0:
+            raise RuntimeError("posv_host info %d" % info)
+    steps = max(1, args.e2e_steps)
+    del stage
+    return {"value": round(step_flops(n, nrhs) * steps / tt / 1e9, 2), "unit": "GFLOP/s",
+            "h2d_bytes_per_step": n * n * 8 + n * nrhs * 8, "d2h_bytes_per_step": n * n * 8 + n * nrhs * 8 + 4,
+            "steps": steps, "api": "chol_posv_host (pinned host buffers)"}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * chol.h -- C ABI of the GB300 (sm_103a) tiled Cholesky library.
+ *
+ * The library factors a dense symmetric positive definite matrix with the right-looking
+ * tile algorithm that the paper schedules (PLASMA DPOTRF: POTRF, TRSM, SYRK and GEMM tile
+ * tasks; Section 4.1 "Benchmarks", double precision and 512 x 512 tiles in Section 4.1
+ * "Methodology"), and solves with the factor. The tile task graph runs on one GPU inside a
+ * persistent data-flow kernel: every thread block is a worker with its own ready queue,
+ * and the pop / push / steal / activate operations of Section 2.2 place newly ready tasks
+ * with HEFT (Algorithm 1), DADA(alpha) (Algorithm 2), work stealing (Section 4.3
+ * "Comparison with work stealing") or a static owner-computes map.
+ *
+ * Conventions shared by every entry point
+ *  - Matrices are column-major with a leading dimension (LAPACK), double precision.
+ *  - Pointers named d... are DEVICE pointers on the current CUDA device; h... are host
+ *    pointers. The caller owns all memory, including the workspaces; the library keeps no
+ *    pointer after a call returns and allocates nothing on the device except inside
+ *    chol_posv_host (which documents it).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream). Calls
+ *    that take a stream are asynchronous with respect to the host: the return value only
+ *    reports argument checks and launch errors; numerical status is written to device
+ *    memory (dInfo) and is valid once the stream has reached that point.
+ *  - Return values are chol_status codes. A negative code means nothing was launched,
+ *    except CHOL_ERR_CUDA raised by a failed launch.
+ */
+#ifndef CHOL_GB300_H
+#define CHOL_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CHOL_OK = 0,
+  CHOL_ERR_INVALID_ARG = -1,  /* a size, leading dimension, option or pointer is invalid */
+  CHOL_ERR_CUDA = -2,         /* a CUDA runtime call failed (cudaGetLastError has the cause) */
+  CHOL_ERR_WORKSPACE = -3,    /* the workspace is smaller than the matching _workspace_size */
+  CHOL_ERR_TIMEOUT = -4,      /* a device wait saw no progress for opts.timeout_ns (sync calls) */
+  CHOL_ERR_UNSUPPORTED = -5,  /* the device is not sm_103 or the shape exceeds a limit */
+  CHOL_ERR_NOT_SPD = 1        /* the matrix is not positive definite (sync calls) */
+} chol_status;
+
+/* Values written to *dInfo by the factorization (LAPACK convention for j > 0). */
+#define CHOL_INFO_OK 0
+/* j > 0: the leading minor of order j is not positive definite (pivot <= 0 or NaN). */
+#define CHOL_INFO_TIMEOUT (-1)      /* a bounded device wait expired; results are undefined */
+#define CHOL_INFO_QUEUE_FULL (-2)   /* internal: a ready queue overflowed (never expected) */
+
+/* Ready-queue policies of the activate operation (Section 3). */
+typedef enum {
+  CHOL_POLICY_HEFT = 0,   /* Algorithm 1: priority order, earliest-finish-time worker */
+  CHOL_POLICY_DADA = 1,   /* Algorithm 2: affinity phase up to alpha*lambda, then dual approx. */
+  CHOL_POLICY_STEAL = 2,  /* successors stay on the finishing worker, FIFO, idle workers steal */
+  CHOL_POLICY_STATIC = 3  /* owner computes: the worker is fixed by the tile a task writes */
+} chol_policy;
+
+/* Options of chol_factor. Initialise with chol_opts_default and change what is needed. */
+typedef struct {
+  int nb;                 /* tile order; 0 = 256. 16 <= nb <= 1024 and ceil(n/nb) <= 1024 */
+  int policy;             /* chol_policy */
+  double alpha;           /* DADA affinity parameter, 0 <= alpha <= 1 (Section 3.2) */
+  int steal;              /* 1: an idle worker steals from random victims (Section 2.1) */
+  int workers_per_sm;     /* persistent thread blocks per SM: 1 or 2; 0 = 2 */
+  int num_workers;        /* 0 = all SMs x workers_per_sm; else a smaller worker count */
+  int queue_order;        /* 0 = by priority (bottom level), 1 = FIFO (arrival order) */
+  int dada_max_iter;      /* bisection steps of Algorithm 2; 0 = 16 */
+  double dada_eps;        /* stop when upper - lower <= dada_eps * first upper; 0 = 0.01 */
+  long long cost_ns[4];   /* predicted time of one POTRF, TRSM, SYRK, GEMM tile task (ns);
+                             0 = derived from the task's flops at 7.5 GFLOP/s per worker */
+  long long timeout_ns;   /* a device wait that sees no progress for this long gives up and
+                             writes CHOL_INFO_TIMEOUT; 0 = 10 s */
+  int trace;              /* 1: record per task (worker, queue, start ns, end ns) */
+  long long hold_task;    /* fault injection for tests of the bounded waits: the task with
+                             this id gets one extra dependency, so it never becomes ready
+                             and the run ends with CHOL_INFO_TIMEOUT; -1 (default) = none */
+} chol_opts;
+
+void chol_opts_default(chol_opts *opts);
+
+/* ---------------------------------------------------------------------------------------
+ * Factorization A = L L^T (Section 4.1: tile Cholesky DPOTRF; Section 2: data-flow
+ * execution; Section 2.2: pop/push/steal/activate; Section 2.3: per-processor predicted
+ * completion time-stamps; Algorithms 1 and 2: the activate policies).
+ *
+ * dA    n x n, leading dimension lda >= max(1, n). On entry the lower triangle holds A; on
+ *       exit it holds L. The strict upper triangle is neither read nor written.
+ * opts  host pointer, may be NULL (defaults).
+ * dWork device workspace of at least chol_factor_workspace_size(n, opts) bytes, 256-byte
+ *       aligned. Its contents on entry do not matter; on exit it holds the schedule state
+ *       (and the trace when opts->trace is set, see chol_factor_trace_offset).
+ * dInfo device int: CHOL_INFO_OK, j > 0 (the leading minor of order j is not positive
+ *       definite; A is then left in an unspecified state) or a negative CHOL_INFO_*.
+ * Runs one initialisation kernel and one persistent kernel on `stream`.
+ */
+size_t chol_factor_workspace_size(int n, const chol_opts *opts);
+chol_status chol_factor(int n, double *dA, int lda, const chol_opts *opts, void *dWork,
+                        size_t work_bytes, int *dInfo, void *stream);
+
+/* Byte offset inside dWork of the trace written when opts->trace = 1: one record of four
+ * int64 per task, in task-id order: {worker that ran it, worker whose queue it was taken
+ * from, start time (ns, %globaltimer), end time (ns)}. -1 if tracing is off. */
+long long chol_factor_trace_offset(int n, const chol_opts *opts);
+
+/* ---------------------------------------------------------------------------------------
+ * Solve A X = B with the factor from chol_factor: forward substitution L Y = B, then back
+ * substitution L^T X = Y (the solves that consume the factor; the paper's experiments
+ * stop at the factorization).
+ *
+ * dL    the array written by chol_factor (lower triangle used), leading dimension lda.
+ * dB    n x nrhs, leading dimension ldb >= max(1, n); overwritten by X.
+ * dWork at least chol_solve_workspace_size(n, nrhs) bytes.
+ * dInfo device int or NULL: 0, or CHOL_INFO_TIMEOUT if a bounded wait expired.
+ */
+size_t chol_solve_workspace_size(int n, int nrhs);
+chol_status chol_solve(int n, int nrhs, const double *dL, int lda, double *dB, int ldb,
+                       void *dWork, size_t work_bytes, int *dInfo, void *stream);
+
+/* One sweep only: uplo_t = 0 solves L Y = B, uplo_t = 1 solves L^T X = B, in place on dB. */
+chol_status chol_trsm_sweep(int uplo_t, int n, int nrhs, const double *dL, int lda, double *dB,
+                            int ldb, void *dWork, size_t work_bytes, int *dInfo, void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Host-buffer convenience: factor and solve from host memory (LAPACK dposv semantics).
+ * hA (n x n, lda) is copied to the device, factored, and L is copied back into hA's lower
+ * triangle; hB (n x nrhs, ldb) is overwritten by X. dStage is a device buffer of at least
+ * chol_posv_host_stage_size(n, nrhs, opts) bytes that the call uses for A, B and the
+ * workspaces. Synchronous: returns CHOL_ERR_NOT_SPD or CHOL_ERR_TIMEOUT from the info.
+ * Host buffers may be pageable or pinned (pinned copies are faster).
+ */
+size_t chol_posv_host_stage_size(int n, int nrhs, const chol_opts *opts);
+chol_status chol_posv_host(int n, int nrhs, double *hA, int lda, double *hB, int ldb,
+                           const chol_opts *opts, void *dStage, size_t stage_bytes,
+                           int *hInfo, void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Introspection of the task graph and of the activate policies. These run on the HOST,
+ * with host pointers, using the same code the persistent kernel runs; they exist so the
+ * graph and the placement rules can be checked without a GPU.
+ */
+
+/* Number of tasks for T x T tiles: T + T(T-1) + T(T-1)(T-2)/6. */
+long long chol_dag_task_count(int T);
+/* Number of successor edges. */
+long long chol_dag_edge_count(int T);
+/* Fill, for every task id in [0, count): kind (0 POTRF, 1 TRSM, 2 SYRK, 3 GEMM), tile
+ * indices (i, j, k) -- POTRF(k) = (k,k,k), TRSM(i,k) = (i,k,k), SYRK(i,k) = (i,i,k),
+ * GEMM(i,j,k) = (i,j,k) --, the initial dependency count, and the successors in CSR form
+ * (succ_ptr has count + 1 entries, succ has chol_dag_edge_count entries). Any output
+ * pointer may be NULL. Returns CHOL_OK or CHOL_ERR_INVALID_ARG (T < 1 or T > 1024). */
+chol_status chol_dag_describe(int T, int *kind, int *ti, int *tj, int *tk, int *indeg,
+                              long long *succ_ptr, long long *succ);
+/* Bottom level of every task: its cost plus the longest cost-weighted path to the exit
+ * (the upward rank that orders the original HEFT, Section 3.1). cost_ns[4] per kind. */
+chol_status chol_dag_bottom_levels(int T, const long long *cost_ns, long long *bl);
+
+/* One activate operation on identical workers (Algorithm 1 for CHOL_POLICY_HEFT,
+ * Algorithm 2 for CHOL_POLICY_DADA). Ready list of m tasks: task ids tid[m], processing
+ * times p[m] (ns), priorities prio[m] (bottom levels), affinity worker aff[m] (-1: none)
+ * and affinity score score[m] (bytes of the tile the task writes held by that worker).
+ * load[W]: each worker's predicted remaining busy time (ns). Writes the push order
+ * out_tid[m] and the chosen worker out_worker[m]; *out_iters gets the number of
+ * bisection steps (0 for HEFT). Host pointers. Ties go to the lowest worker index. */
+chol_status chol_sched_activate(int policy, double alpha, int max_iter, double eps, int m,
+                                const int *tid, const long long *p, const long long *prio,
+                                const int *aff, const long long *score, int W,
+                                const long long *load, int *out_tid, int *out_worker,
+                                int *out_iters);
+/* The same decision computed by one warp on the device (device pointers, all sizes as
+ * above; m <= 1024, W <= 1024). Used to check that device and host agree. */
+chol_status chol_sched_activate_device(int policy, double alpha, int max_iter, double eps, int m,
+                                       const int *dtid, const long long *dp,
+                                       const long long *dprio, const int *daff,
+                                       const long long *dscore, int W, const long long *dload,
+                                       int *dout_tid, int *dout_worker, int *dout_iters,
+                                       void *stream);
+
+/* Library version string and the number of workers chol_factor would launch on the
+ * current device for these options (0 if no usable device). */
+const char *chol_version(void);
+int chol_num_workers(const chol_opts *opts);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHOL_GB300_H */

@@ -1,0 +1,323 @@
+"""GB300 (sm_103a) tiled Cholesky factorization and solves behind a C ABI.
+
+This module is a thin ctypes binding over ``include/chol.h``: the functions with the C names
+(``chol_factor``, ``chol_solve``, ...) marshal arguments and call the CUDA library; the
+Pythonic helpers (``factor``, ``solve``, ``posv``) only allocate workspaces with torch and
+check layouts. Every step of the computation runs in the library's kernels; there is no
+CPU or PyTorch fallback, and a missing library raises at import time.
+
+Matrices are float64 and column-major: a CUDA tensor ``A`` with ``A.stride(0) == 1`` and
+``A.stride(1) >= A.shape[0]`` (``colmajor(x)`` makes one).
+"""
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+__all__ = [
+    "lib", "ChOpts", "POLICIES", "opts", "colmajor", "factor", "solve", "trsm_sweep", "posv",
+    "posv_host", "workspace_size", "solve_workspace_size", "num_workers", "trace",
+    "dag_describe", "dag_bottom_levels", "sched_activate", "sched_activate_device",
+    "CholeskyError",
+]
+
+POLICIES = {"heft": 0, "dada": 1, "steal": 2, "static": 3}
+STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "workspace too small",
+          -4: "device wait timed out", -5: "unsupported device or shape", 1: "not positive definite"}
+INFO_TIMEOUT = -1
+INFO_QUEUE_FULL = -2
+
+
+class CholeskyError(RuntimeError):
+    pass
+
+
+class ChOpts(ctypes.Structure):
+    _fields_ = [
+        ("nb", ctypes.c_int),
+        ("policy", ctypes.c_int),
+        ("alpha", ctypes.c_double),
+        ("steal", ctypes.c_int),
+        ("workers_per_sm", ctypes.c_int),
+        ("num_workers", ctypes.c_int),
+        ("queue_order", ctypes.c_int),
+        ("dada_max_iter", ctypes.c_int),
+        ("dada_eps", ctypes.c_double),
+        ("cost_ns", ctypes.c_longlong * 4),
+        ("timeout_ns", ctypes.c_longlong),
+        ("trace", ctypes.c_int),
+        ("hold_task", ctypes.c_longlong),
+    ]
+
+
+_c = ctypes
+_P = ctypes.c_void_p
+_SZ = ctypes.c_size_t
+_I = ctypes.c_int
+_LL = ctypes.c_longlong
+_D = ctypes.c_double
+_OPTS = ctypes.POINTER(ChOpts)
+
+_SIGNATURES = {
+    "chol_opts_default": (None, [_OPTS]),
+    "chol_factor_workspace_size": (_SZ, [_I, _OPTS]),
+    "chol_factor": (_I, [_I, _P, _I, _OPTS, _P, _SZ, _P, _P]),
+    "chol_factor_trace_offset": (_LL, [_I, _OPTS]),
+    "chol_solve_workspace_size": (_SZ, [_I, _I]),
+    "chol_solve": (_I, [_I, _I, _P, _I, _P, _I, _P, _SZ, _P, _P]),
+    "chol_trsm_sweep": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _SZ, _P, _P]),
+    "chol_posv_host_stage_size": (_SZ, [_I, _I, _OPTS]),
+    "chol_posv_host": (_I, [_I, _I, _P, _I, _P, _I, _OPTS, _P, _SZ, _P, _P]),
+    "chol_dag_task_count": (_LL, [_I]),
+    "chol_dag_edge_count": (_LL, [_I]),
+    "chol_dag_describe": (_I, [_I, _P, _P, _P, _P, _P, _P, _P]),
+    "chol_dag_bottom_levels": (_I, [_I, _P, _P]),
+    "chol_sched_activate": (_I, [_I, _D, _I, _D, _I, _P, _P, _P, _P, _P, _I, _P, _P, _P, _P]),
+    "chol_sched_activate_device": (_I, [_I, _D, _I, _D, _I, _P, _P, _P, _P, _P, _I, _P, _P, _P, _P, _P]),
+    "chol_version": (ctypes.c_char_p, []),
+    "chol_num_workers": (_I, [_OPTS]),
+}
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError("the CUDA library is not built (%s); run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`" % path)
+    L = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+lib = _load()
+for _name in _SIGNATURES:
+    globals()[_name] = getattr(lib, _name)
+    __all__.append(_name)
+
+
+def opts(nb=256, policy="heft", alpha=0.5, steal=None, workers_per_sm=2, num_workers=0,
+         queue_order=None, dada_max_iter=16, dada_eps=0.01, cost_ns=None, timeout_ns=0, trace=False,
+         hold_task=-1):
+    o = ChOpts()
+    lib.chol_opts_default(ctypes.byref(o))
+    o.nb = nb
+    o.policy = POLICIES[policy] if isinstance(policy, str) else int(policy)
+    o.alpha = alpha
+    o.steal = (0 if o.policy == 3 else 1) if steal is None else int(bool(steal))
+    o.workers_per_sm = workers_per_sm
+    o.num_workers = num_workers
+    o.queue_order = (1 if o.policy == 2 else 0) if queue_order is None else int(queue_order)
+    o.dada_max_iter = dada_max_iter
+    o.dada_eps = dada_eps
+    if cost_ns is not None:
+        for k in range(4):
+            o.cost_ns[k] = int(cost_ns[k])
+    o.timeout_ns = int(timeout_ns)
+    o.trace = int(bool(trace))
+    o.hold_task = int(hold_task)
+    return o
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(status, what):
+    if status != 0:
+        raise CholeskyError("%s: %s (%d)" % (what, STATUS.get(status, "?"), status))
+
+
+def colmajor(x):
+    """Column-major copy of a 2-D tensor (or a 1-D tensor as one column)."""
+    if x.dim() == 1:
+        x = x.reshape(-1, 1)
+    return x.t().contiguous().t()
+
+
+def _check_matrix(A, name):
+    if not (A.is_cuda and A.dtype == torch.float64 and A.dim() == 2):
+        raise ValueError("%s must be a 2-D float64 CUDA tensor" % name)
+    if A.shape[0] > 0 and A.shape[1] > 0 and A.stride(0) != 1:
+        raise ValueError("%s must be column-major (stride(0) == 1); use colmajor()" % name)
+    return max(1, A.stride(1) if A.shape[1] > 1 else A.shape[0])
+
+
+def workspace_size(n, o=None):
+    o = o or opts()
+    return int(lib.chol_factor_workspace_size(n, ctypes.byref(o)))
+
+
+def solve_workspace_size(n, nrhs):
+    return int(lib.chol_solve_workspace_size(n, nrhs))
+
+
+def num_workers(o=None):
+    o = o or opts()
+    return int(lib.chol_num_workers(ctypes.byref(o)))
+
+
+def _workspace(nbytes, device):
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+
+
+def factor(A, o=None, work=None, info=None, stream=None, check=False):
+    """Factor A = L L^T in place (lower triangle of A). Returns (info tensor, workspace).
+
+    With check=True the call synchronises and raises CholeskyError on a non-zero info."""
+    o = o or opts()
+    n = A.shape[0]
+    if A.shape[1] != n:
+        raise ValueError("A must be square")
+    lda = _check_matrix(A, "A")
+    if work is None:
+        work = _workspace(workspace_size(n, o), A.device)
+    if info is None:
+        info = torch.zeros(1, dtype=torch.int32, device=A.device)
+    st = lib.chol_factor(n, A.data_ptr(), lda, ctypes.byref(o), work.data_ptr(), work.numel(),
+                         info.data_ptr(), _stream(stream))
+    _check(st, "chol_factor")
+    if check:
+        v = int(info.item())
+        if v != 0:
+            raise CholeskyError("chol_factor: info = %d" % v)
+    return info, work
+
+
+def solve(L, B, work=None, info=None, stream=None):
+    """Overwrite B with A^{-1} B given the factor from factor()."""
+    n = L.shape[0]
+    lda = _check_matrix(L, "L")
+    ldb = _check_matrix(B, "B")
+    nrhs = B.shape[1]
+    if work is None:
+        work = _workspace(solve_workspace_size(n, nrhs), L.device)
+    st = lib.chol_solve(n, nrhs, L.data_ptr(), lda, B.data_ptr(), ldb, work.data_ptr(), work.numel(),
+                        info.data_ptr() if info is not None else None, _stream(stream))
+    _check(st, "chol_solve")
+    return B
+
+
+def trsm_sweep(L, B, transpose=False, work=None, info=None, stream=None):
+    n = L.shape[0]
+    lda = _check_matrix(L, "L")
+    ldb = _check_matrix(B, "B")
+    nrhs = B.shape[1]
+    if work is None:
+        work = _workspace(solve_workspace_size(n, nrhs), L.device)
+    st = lib.chol_trsm_sweep(int(bool(transpose)), n, nrhs, L.data_ptr(), lda, B.data_ptr(), ldb,
+                             work.data_ptr(), work.numel(),
+                             info.data_ptr() if info is not None else None, _stream(stream))
+    _check(st, "chol_trsm_sweep")
+    return B
+
+
+def posv(A, B, o=None, stream=None):
+    """Factor A in place and overwrite B with the solution; returns the info tensor."""
+    info, _ = factor(A, o, stream=stream)
+    solve(A, B, stream=stream)
+    return info
+
+
+def posv_host(A, B, o=None, stage=None, stream=None):
+    """Host-buffer call: A, B are float64 Fortran-ordered numpy arrays (A is overwritten by
+    L in its lower triangle, B by X). Returns info."""
+    import numpy as np
+    o = o or opts()
+    n = A.shape[0]
+    nrhs = B.shape[1] if B.ndim == 2 else 1
+    assert A.dtype == np.float64 and A.flags.f_contiguous and B.dtype == np.float64 and B.flags.f_contiguous
+    need = int(lib.chol_posv_host_stage_size(n, nrhs, ctypes.byref(o)))
+    if stage is None:
+        stage = _workspace(need, torch.device("cuda", torch.cuda.current_device()))
+    info = ctypes.c_int(0)
+    st = lib.chol_posv_host(n, nrhs, A.ctypes.data, max(1, n), B.ctypes.data, max(1, n), ctypes.byref(o),
+                            stage.data_ptr(), stage.numel(), ctypes.byref(info), _stream(stream))
+    if st not in (0, 1, -4):
+        _check(st, "chol_posv_host")
+    return int(info.value)
+
+
+def trace(work, n, o):
+    """The per-task trace (ntasks x 4 int64) recorded when o.trace is set."""
+    off = int(lib.chol_factor_trace_offset(n, ctypes.byref(o)))
+    if off < 0:
+        raise ValueError("tracing is off")
+    T = (n + o.nb - 1) // o.nb
+    nt = int(lib.chol_dag_task_count(T))
+    return work[off:off + nt * 32].view(torch.int64).reshape(nt, 4)
+
+
+def dag_describe(T):
+    """(kind, i, j, k, indeg, succ_ptr, succ) as numpy arrays, from the library (host code)."""
+    import numpy as np
+    nt = int(lib.chol_dag_task_count(T))
+    ne = int(lib.chol_dag_edge_count(T))
+    if nt < 0:
+        raise ValueError("T out of range")
+    arrs = [np.zeros(nt, np.int32) for _ in range(5)]
+    ptr = np.zeros(nt + 1, np.int64)
+    succ = np.zeros(max(ne, 1), np.int64)
+    _check(lib.chol_dag_describe(T, *[a.ctypes.data for a in arrs], ptr.ctypes.data, succ.ctypes.data),
+           "chol_dag_describe")
+    return (*arrs, ptr, succ[:ne])
+
+
+def dag_bottom_levels(T, cost_ns):
+    import numpy as np
+    nt = int(lib.chol_dag_task_count(T))
+    c = np.asarray(cost_ns, dtype=np.int64)
+    bl = np.zeros(nt, np.int64)
+    _check(lib.chol_dag_bottom_levels(T, c.ctypes.data, bl.ctypes.data), "chol_dag_bottom_levels")
+    return bl
+
+
+def _sched_arrays(tasks):
+    import numpy as np
+    m = len(tasks)
+    tid = np.array([t["tid"] for t in tasks], np.int32)
+    p = np.array([t["p"] for t in tasks], np.int64)
+    prio = np.array([t["prio"] for t in tasks], np.int64)
+    aff = np.array([t["aff"] for t in tasks], np.int32)
+    score = np.array([t["score"] for t in tasks], np.int64)
+    return m, tid, p, prio, aff, score
+
+
+def sched_activate(policy, tasks, load, alpha=0.5, max_iter=16, eps=0.01):
+    """Host placement (same code as the device). Returns ([(tid, worker)], iterations)."""
+    import numpy as np
+    m, tid, p, prio, aff, score = _sched_arrays(tasks)
+    ld = np.asarray(load, np.int64)
+    ot = np.zeros(max(m, 1), np.int32)
+    ow = np.zeros(max(m, 1), np.int32)
+    it = ctypes.c_int(0)
+    pol = POLICIES[policy] if isinstance(policy, str) else policy
+    _check(lib.chol_sched_activate(pol, alpha, max_iter, eps, m, tid.ctypes.data, p.ctypes.data,
+                                   prio.ctypes.data, aff.ctypes.data, score.ctypes.data, len(ld),
+                                   ld.ctypes.data, ot.ctypes.data, ow.ctypes.data, ctypes.byref(it)),
+           "chol_sched_activate")
+    return [(int(a), int(b)) for a, b in zip(ot[:m], ow[:m])], int(it.value)
+
+
+def sched_activate_device(policy, tasks, load, alpha=0.5, max_iter=16, eps=0.01, device="cuda"):
+    """The same placement computed by one warp on the GPU."""
+    m, tid, p, prio, aff, score = _sched_arrays(tasks)
+    t = lambda a: torch.from_numpy(a).to(device)
+    dt, dp, dpr, da, ds = t(tid), t(p), t(prio), t(aff), t(score)
+    dl = torch.tensor(list(load), dtype=torch.int64, device=device)
+    ot = torch.zeros(m, dtype=torch.int32, device=device)
+    ow = torch.zeros(m, dtype=torch.int32, device=device)
+    it = torch.zeros(1, dtype=torch.int32, device=device)
+    pol = POLICIES[policy] if isinstance(policy, str) else policy
+    _check(lib.chol_sched_activate_device(pol, alpha, max_iter, eps, m, dt.data_ptr(), dp.data_ptr(),
+                                          dpr.data_ptr(), da.data_ptr(), ds.data_ptr(), len(load),
+                                          dl.data_ptr(), ot.data_ptr(), ow.data_ptr(), it.data_ptr(),
+                                          _stream(None)), "chol_sched_activate_device")
+    torch.cuda.synchronize()
+    return [(int(a), int(b)) for a, b in zip(ot.tolist(), ow.tolist())], int(it.item())

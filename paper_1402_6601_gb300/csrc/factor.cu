@@ -1,0 +1,595 @@
+// Persistent data-flow kernel for the tiled Cholesky factorization.
+//
+// One thread block per worker (Section 2: one worker per processing unit, each with a
+// local ready queue). A worker loops: pop a task from its own queue, else steal from a
+// random victim (Section 2.1 "Execution flow"), run the tile body, then activate the
+// successors whose dependency counters reach zero and place them on workers' queues with
+// the chosen policy (Section 2.2; Algorithms 1 and 2). The predicted completion
+// time-stamp of a worker (Section 2.3) is the predicted end of the task it runs plus the
+// predicted times of the tasks queued on it; both are kept in device memory and updated
+// with atomics, and the running task's term is corrected from the real clock when the
+// task starts and ends.
+//
+// Ready queues are arrays of 64-bit slots (0 = empty; otherwise the priority key in the
+// high word and the complemented task id in the low word). Push claims an empty slot with
+// a compare-and-swap; pop and steal scan a queue with one warp and claim the slot with the
+// largest key. At any time at most one task per tile is ready (the tasks writing a tile
+// form a chain), so at most T(T+1)/2 tasks are queued in total; every queue has
+// C >= T(T+1)/(2W) + 64 slots, and a push that finds its queue full goes to the next
+// queue, so a push always finds a slot (the spill is counted in the control block).
+//
+// Every wait is bounded: a worker that finds no work sleeps with back-off, and if the
+// count of completed tasks does not move for opts.timeout_ns (or a matching iteration
+// count) it raises the abort flag and writes CHOL_INFO_TIMEOUT; all workers then return.
+#include <algorithm>
+#include <mutex>
+#include "common.cuh"
+#include "dag.cuh"
+#include "sched.cuh"
+#include "tiles_f64.cuh"
+
+namespace chol {
+
+struct Ctrl {
+  int done;
+  int abort;
+  int info;
+  unsigned int fifo_seq;
+  int spills;
+  int pad[59];
+};
+
+struct FactorArgs {
+  double *A;
+  int64_t lda;
+  int n, nb, T;
+  int64_t ntasks;
+  int W, C;
+  int policy, queue_order, steal, dada_max_iter, trace;
+  double alpha, dada_eps;
+  int64_t cost[4];
+  int64_t timeout_ns, iter_limit;
+  Ctrl *ctrl;
+  int *cnt;
+  int64_t *bl;
+  int *owner;
+  unsigned long long *slots;
+  unsigned int *qhead;
+  int *qcount;
+  unsigned long long *qcost;   // int64 two's complement
+  unsigned long long *run_end; // ns, 0 = idle
+  long long *trace_buf;
+};
+
+struct Resolved {
+  int nb, T, policy, queue_order, steal, wps, W, max_iter, trace;
+  double alpha, eps;
+  int64_t cost[4];
+  int64_t timeout_ns;
+  int64_t hold_task;
+};
+
+struct Layout {
+  size_t ctrl, qhead, qcount, qcost, run_end, slots, zero_end, cnt, owner, bl, trace, total;
+  int C;
+  int64_t ntasks;
+};
+
+static size_t sched_smem_bytes(int T, int W) {
+  size_t b = align_up((size_t)T * sizeof(ReadyTask), 16);
+  b += align_up((size_t)T * 4 * 5, 16);
+  b += (size_t)W * 8 * 2;
+  return b;
+}
+
+static size_t factor_smem_bytes(int T, int W) {
+  return std::max((size_t)TILE_SMEM_BYTES, sched_smem_bytes(T, W));
+}
+
+static Layout make_layout(int n, const Resolved &r, int W) {
+  Layout L;
+  const int T = r.T;
+  L.ntasks = task_count(T);
+  {
+    const int64_t need = ((int64_t)T * (T + 1) / 2 + W - 1) / W + 64;
+    L.C = (int)std::max<int64_t>(128, (need + 31) / 32 * 32);
+  }
+  size_t o = 0;
+  L.ctrl = o; o += align_up(sizeof(Ctrl), 256);
+  L.qhead = o; o += align_up((size_t)W * 4, 256);
+  L.qcount = o; o += align_up((size_t)W * 4, 256);
+  L.qcost = o; o += align_up((size_t)W * 8, 256);
+  L.run_end = o; o += align_up((size_t)W * 8, 256);
+  L.slots = o; o += align_up((size_t)W * L.C * 8, 256);
+  L.zero_end = o;
+  L.cnt = o; o += align_up((size_t)L.ntasks * 4, 256);
+  L.owner = o; o += align_up((size_t)T * T * 4, 256);
+  L.bl = o; o += align_up((size_t)L.ntasks * 8, 256);
+  L.trace = o;
+  if (r.trace) o += align_up((size_t)L.ntasks * 32, 256);
+  L.total = o;
+  (void)n;
+  return L;
+}
+
+// ------------------------------------------------------------------------------------
+// device side
+
+__device__ __forceinline__ unsigned long long make_entry(uint32_t key, int64_t tid) {
+  return ((unsigned long long)key << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)tid);
+}
+__device__ __forceinline__ int64_t entry_tid(unsigned long long e) {
+  return (int64_t)(0xFFFFFFFFu - (uint32_t)(e & 0xFFFFFFFFull));
+}
+__device__ __forceinline__ uint32_t prio_key(int64_t bl) {
+  int64_t k = bl >> 8;
+  if (k > 0xFFFFFFFEll) k = 0xFFFFFFFEll;
+  if (k < 0) k = 0;
+  return (uint32_t)k + 1u;
+}
+
+__device__ __forceinline__ int tile_dim(const FactorArgs &a, int t) {
+  return min(a.nb, a.n - t * a.nb);
+}
+__device__ __forceinline__ double *tile_ptr(const FactorArgs &a, int i, int j) {
+  return a.A + (int64_t)j * a.nb * a.lda + (int64_t)i * a.nb;
+}
+
+// Push by a single thread onto queue w, or onto the next queue with a free slot if w is
+// full. Returns the queue used, or -1 if every queue is full (cannot happen, see above).
+__device__ int push_task(const FactorArgs &a, int w, unsigned long long entry) {
+  for (int hop = 0; hop < a.W; ++hop) {
+    const int q = (w + hop) % a.W;
+    unsigned long long *s = a.slots + (size_t)q * a.C;
+    unsigned int idx = atomicAdd(&a.qhead[q], 1u) % (unsigned)a.C;
+    for (int probe = 0; probe < a.C; ++probe) {
+      if (atomicCAS(&s[idx], 0ull, entry) == 0ull) {
+        atomicAdd(&a.qcount[q], 1);
+        if (hop) atomicAdd(&a.ctrl->spills, 1);
+        return q;
+      }
+      if (++idx == (unsigned)a.C) idx = 0;
+    }
+  }
+  return -1;
+}
+
+// Pop the highest-key entry of queue q; called by all lanes of one warp.
+__device__ int64_t try_pop(const FactorArgs &a, int q) {
+  const int lane = threadIdx.x & 31;
+  int cnt = 0;
+  if (lane == 0) cnt = ld_volatile(&a.qcount[q]);
+  cnt = __shfl_sync(0xffffffffu, cnt, 0);
+  if (cnt <= 0) return -1;
+  unsigned long long *s = a.slots + (size_t)q * a.C;
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    unsigned long long best = 0ull;
+    int bslot = -1;
+    // C is a multiple of 32: batches of four loads per lane are issued before any compare
+    for (int i0 = 0; i0 < a.C; i0 += 128) {
+      unsigned long long v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + 32 * u + lane;
+        v[u] = i < a.C ? ld_volatile(&s[i]) : 0ull;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (v[u] > best) { best = v[u]; bslot = i0 + 32 * u + lane; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int os = __shfl_xor_sync(0xffffffffu, bslot, o);
+      if (ov > best) { best = ov; bslot = os; }
+    }
+    if (best == 0ull) return -1;
+    int ok = 0;
+    if (lane == 0) ok = atomicCAS(&s[bslot], best, 0ull) == best;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (ok) {
+      if (lane == 0) atomicSub(&a.qcount[q], 1);
+      return entry_tid(best);
+    }
+  }
+  return -1;
+}
+
+__device__ __forceinline__ uint32_t xorshift32(uint32_t x) {
+  x ^= x << 13; x ^= x >> 17; x ^= x << 5;
+  return x;
+}
+
+__device__ __forceinline__ void raise_abort(const FactorArgs &a, int info) {
+  atomicCAS(&a.ctrl->info, 0, info);
+  atomicExch(&a.ctrl->abort, 1);
+}
+
+// Get the next task for worker wid (warp 0). Returns -1 when all tasks are done or the run
+// was aborted. `from` receives the queue the task came from.
+__device__ int64_t acquire(const FactorArgs &a, int wid, uint32_t &rng, int &from) {
+  const int lane = threadIdx.x & 31;
+  int last_done = -1;
+  uint64_t t_last = 0;
+  int64_t iters = 0;
+  unsigned sleep_ns = 32;
+  while (true) {
+    int abort_ = 0, done_ = 0;
+    unsigned long long now = 0;
+    if (lane == 0) {
+      abort_ = ld_volatile(&a.ctrl->abort);
+      done_ = ld_volatile(&a.ctrl->done);
+      now = globaltimer_ns();
+    }
+    abort_ = __shfl_sync(0xffffffffu, abort_, 0);
+    done_ = __shfl_sync(0xffffffffu, done_, 0);
+    now = __shfl_sync(0xffffffffu, now, 0);
+    if (abort_ || done_ >= a.ntasks) return -1;
+    int64_t id = try_pop(a, wid);
+    if (id >= 0) { from = wid; return id; }
+    if (a.steal && a.W > 1) {
+      for (int t = 0; t < 4; ++t) {
+        rng = xorshift32(rng);
+        int v = (int)(rng % (uint32_t)(a.W - 1));
+        if (v >= wid) ++v;
+        id = try_pop(a, v);
+        if (id >= 0) { from = v; return id; }
+      }
+    }
+    if (done_ != last_done) {
+      last_done = done_;
+      t_last = now;
+      iters = 0;
+    } else if (now - t_last > (uint64_t)a.timeout_ns || ++iters > a.iter_limit) {
+      if (lane == 0) raise_abort(a, CHOL_INFO_TIMEOUT);
+      return -1;
+    }
+    __nanosleep(sleep_ns);
+    sleep_ns = sleep_ns < 2048 ? sleep_ns * 2 : 2048;
+  }
+}
+
+// Activate the successors of a finished task and place the ready ones (warp 0).
+__device__ void complete(const FactorArgs &a, int wid, const TaskDesc &d, unsigned char *smem_raw,
+                         int *s_nready) {
+  const int lane = threadIdx.x & 31;
+  const int T = a.T;
+  ReadyTask *LR = reinterpret_cast<ReadyTask *>(smem_raw);
+  size_t off = align_up((size_t)T * sizeof(ReadyTask), 16);
+  PlaceScratch ps;
+  int *ints = reinterpret_cast<int *>(smem_raw + off);
+  ps.ord_prio = ints;
+  ps.ord_aff = ints + T;
+  ps.ord_lpt = ints + 2 * T;
+  ps.assign = ints + 3 * T;
+  ps.trial = ints + 4 * T;
+  off += align_up((size_t)T * 4 * 5, 16);
+  int64_t *load = reinterpret_cast<int64_t *>(smem_raw + off);
+  ps.tload = load + a.W;
+
+  if (lane == 0) {
+    int ti, tj;
+    rw_tile(d, ti, tj);
+    *(volatile int *)&a.owner[ti * T + tj] = wid;
+    *(volatile unsigned long long *)&a.run_end[wid] = 0ull;
+    *s_nready = 0;
+  }
+  __syncwarp();
+  const int ns = num_successors(T, d);
+  for (int s = lane; s < ns; s += 32) {
+    const int64_t sid = successor(T, d, s);
+    if (atomicSub(&a.cnt[sid], 1) == 1) {
+      const int pos = atomicAdd(s_nready, 1);
+      LR[pos].tid = (int)sid;
+    }
+  }
+  __syncwarp();
+  __threadfence();
+  const int m = *(volatile int *)s_nready;
+  if (m > 0) {
+    for (int i = lane; i < m; i += 32) {
+      const TaskDesc sd = task_desc(T, LR[i].tid);
+      int ti, tj;
+      rw_tile(sd, ti, tj);
+      LR[i].p = a.cost[sd.kind];
+      LR[i].prio = a.queue_order == 0 ? a.bl[LR[i].tid] : 0;
+      const int aff = ld_volatile(&a.owner[ti * T + tj]);
+      LR[i].aff = aff;
+      LR[i].score = aff >= 0 ? (int64_t)min(a.nb, a.n - ti * a.nb) * min(a.nb, a.n - tj * a.nb) * 8 : 0;
+    }
+    __syncwarp();
+    const bool model = a.policy == P_HEFT || a.policy == P_DADA;
+    if (model) {
+      unsigned long long now = 0;
+      if (lane == 0) now = globaltimer_ns();
+      now = __shfl_sync(0xffffffffu, now, 0);
+      for (int w = lane; w < a.W; w += 32) {
+        const unsigned long long re = ld_volatile(&a.run_end[w]);
+        const int64_t rem = re > now ? (int64_t)(re - now) : 0;
+        int64_t q = (int64_t)ld_volatile(&a.qcost[w]);
+        load[w] = rem + (q > 0 ? q : 0);
+      }
+      __syncwarp();
+      place<WarpExec>(a.policy, a.alpha, a.dada_max_iter, a.dada_eps, LR, m, load, a.W, ps);
+    } else {
+      for (int i = lane; i < m; i += 32) {
+        if (a.policy == P_STEAL) {
+          ps.assign[i] = wid;
+        } else {
+          const TaskDesc sd = task_desc(T, LR[i].tid);
+          int ti, tj;
+          rw_tile(sd, ti, tj);
+          ps.assign[i] = (ti + tj * T) % a.W;
+        }
+        ps.ord_prio[i] = i;
+      }
+    }
+    __syncwarp();
+    unsigned int seq0 = 0;
+    if (a.queue_order == 1) {
+      if (lane == 0) seq0 = atomicAdd(&a.ctrl->fifo_seq, (unsigned)m);
+      seq0 = __shfl_sync(0xffffffffu, seq0, 0);
+    }
+    for (int q = lane; q < m; q += 32) {
+      const int i = ps.ord_prio[q];
+      const uint32_t key = a.queue_order == 1 ? (0xFFFFFFFFu - ((seq0 + (unsigned)q) & 0x7FFFFFFFu))
+                                              : prio_key(LR[i].prio);
+      const int w = push_task(a, ps.assign[i], make_entry(key, LR[i].tid));
+      if (w < 0) raise_abort(a, CHOL_INFO_QUEUE_FULL);
+      else atomicAdd(&a.qcost[w], (unsigned long long)LR[i].p);
+    }
+  }
+  __syncwarp();
+  if (lane == 0) atomicAdd(&a.ctrl->done, 1);
+}
+
+// Run one tile task with the whole block. Returns 0 or a 1-based failing global column.
+__device__ int run_task(const FactorArgs &a, const TaskDesc &d, double *smem) {
+  switch (d.kind) {
+    case K_POTRF: {
+      const int f = potrf_tile(tile_ptr(a, d.k, d.k), a.lda, tile_dim(a, d.k), smem);
+      return f ? d.k * a.nb + f : 0;
+    }
+    case K_TRSM:
+      trsm_tile(tile_ptr(a, d.i, d.k), a.lda, tile_ptr(a, d.k, d.k), a.lda, tile_dim(a, d.i),
+                tile_dim(a, d.k), smem);
+      return 0;
+    case K_SYRK:
+      update_nt(tile_ptr(a, d.i, d.i), a.lda, tile_ptr(a, d.i, d.k), a.lda, tile_ptr(a, d.i, d.k),
+                a.lda, tile_dim(a, d.i), tile_dim(a, d.i), tile_dim(a, d.k), true, smem);
+      return 0;
+    default:
+      update_nt(tile_ptr(a, d.i, d.j), a.lda, tile_ptr(a, d.i, d.k), a.lda, tile_ptr(a, d.j, d.k),
+                a.lda, tile_dim(a, d.i), tile_dim(a, d.j), tile_dim(a, d.k), false, smem);
+      return 0;
+  }
+}
+
+__global__ void __launch_bounds__(NT, 2) factor_kernel(const __grid_constant__ FactorArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double *smem = reinterpret_cast<double *>(smem_raw);
+  __shared__ long long s_id;
+  __shared__ int s_from;
+  __shared__ int s_nready;
+  const int wid = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t rng = 0x9E3779B9u ^ ((uint32_t)wid * 0x85EBCA6Bu + 1u);
+  if (wid == 0 && threadIdx.x == 0) {
+    const uint32_t key = a.queue_order == 1 ? 0xFFFFFFFFu : prio_key(a.bl[0]);
+    atomicAdd(&a.qcost[0], (unsigned long long)a.cost[K_POTRF]);
+    if (push_task(a, 0, make_entry(key, 0)) < 0) raise_abort(a, CHOL_INFO_QUEUE_FULL);
+  }
+  while (true) {
+    if (warp == 0) {
+      int from = -1;
+      const int64_t id = acquire(a, wid, rng, from);
+      if (id >= 0 && lane == 0) {
+        const TaskDesc d = task_desc(a.T, id);
+        const int64_t c = a.cost[d.kind];
+        atomicAdd(&a.qcost[from], (unsigned long long)(-c));
+        *(volatile unsigned long long *)&a.run_end[wid] = globaltimer_ns() + (uint64_t)c;
+      }
+      if (lane == 0) { s_id = id; s_from = from; }
+    }
+    __syncthreads();
+    const int64_t id = s_id;
+    if (id < 0) break;
+    __threadfence();
+    const TaskDesc d = task_desc(a.T, id);
+    unsigned long long t0 = 0;
+    if (a.trace && threadIdx.x == 0) t0 = globaltimer_ns();
+    const int fail = run_task(a, d, smem);
+    __threadfence();
+    __syncthreads();
+    if (warp == 0) {
+      // the end time is taken before the successors are activated, so a successor's start
+      // time is never earlier than it
+      unsigned long long t1 = 0;
+      if (a.trace && lane == 0) t1 = globaltimer_ns();
+      if (fail) {
+        if (lane == 0) raise_abort(a, fail);
+      } else {
+        complete(a, wid, d, smem_raw, &s_nready);
+      }
+      if (a.trace && lane == 0) {
+        long long *tr = a.trace_buf + 4 * id;
+        tr[0] = wid;
+        tr[1] = s_from;
+        tr[2] = (long long)t0;
+        tr[3] = (long long)t1;
+      }
+    }
+  }
+}
+
+__global__ void init_kernel(int T, int64_t ntasks, int *cnt, int *owner, int64_t hold_task) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; id < ntasks; id += stride)
+    cnt[id] = initial_count(task_desc(T, id)) + (id == hold_task ? 1 : 0);
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)T * T; t += stride)
+    owner[t] = -1;
+}
+
+// Bottom levels by steps k = T-1 .. 0; inside a step GEMM/SYRK first (their successors are
+// in step k+1), then TRSM (successors in step k), then POTRF. One block.
+__global__ void __launch_bounds__(1024) bottom_level_kernel(int T, int64_t c0, int64_t c1, int64_t c2,
+                                                            int64_t c3, int64_t *bl) {
+  const int64_t cost[4] = {c0, c1, c2, c3};
+  for (int k = T - 1; k >= 0; --k) {
+    const int64_t base = step_offset(T, k);
+    const int64_t m = T - 1 - k;
+    const int64_t end = base + step_size(m);
+    for (int64_t id = base + 1 + m + threadIdx.x; id < end; id += blockDim.x)
+      bl[id] = bottom_level_of(T, task_desc(T, id), cost, bl);
+    __syncthreads();
+    for (int64_t id = base + 1 + threadIdx.x; id <= base + m; id += blockDim.x)
+      bl[id] = bottom_level_of(T, task_desc(T, id), cost, bl);
+    __syncthreads();
+    if (threadIdx.x == 0) bl[base] = bottom_level_of(T, task_desc(T, base), cost, bl);
+    __syncthreads();
+  }
+}
+
+__global__ void copy_info_kernel(const Ctrl *ctrl, int *dInfo) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *dInfo = ctrl->info;
+}
+
+// ------------------------------------------------------------------------------------
+// host side
+
+static std::once_flag g_attr_once;
+
+static bool resolve(int n, const chol_opts *opts, Resolved &r) {
+  chol_opts o;
+  chol_opts_default(&o);
+  if (opts) o = *opts;
+  r.nb = o.nb > 0 ? o.nb : 256;
+  if (r.nb < 16 || r.nb > 1024) return false;
+  r.T = n > 0 ? (n + r.nb - 1) / r.nb : 1;
+  if (r.T > 1024) return false;
+  if (o.policy < 0 || o.policy > 3) return false;
+  r.policy = o.policy;
+  if (!(o.alpha >= 0.0 && o.alpha <= 1.0)) return false;
+  r.alpha = o.alpha;
+  r.steal = o.steal ? 1 : 0;
+  r.wps = o.workers_per_sm > 0 ? o.workers_per_sm : 2;
+  if (r.wps > 2) return false;
+  r.W = o.num_workers;
+  if (r.W < 0 || r.W > 1024) return false;
+  r.queue_order = o.queue_order ? 1 : 0;
+  r.max_iter = o.dada_max_iter > 0 ? o.dada_max_iter : 16;
+  r.eps = o.dada_eps > 0.0 ? o.dada_eps : 0.01;
+  const double nb = (double)r.nb;
+  const double rate = 7.5 / (double)r.wps;  // GFLOP/s per worker = flop per ns
+  const double flops[4] = {nb * nb * nb / 3.0, nb * nb * nb, nb * nb * nb, 2.0 * nb * nb * nb};
+  for (int k = 0; k < 4; ++k) {
+    if (o.cost_ns[k] < 0) return false;
+    r.cost[k] = o.cost_ns[k] > 0 ? o.cost_ns[k] : std::max<int64_t>(1, (int64_t)(flops[k] / rate));
+  }
+  r.timeout_ns = o.timeout_ns > 0 ? o.timeout_ns : 10000000000ll;
+  r.trace = o.trace ? 1 : 0;
+  r.hold_task = o.hold_task;
+  if (r.hold_task >= task_count(r.T)) return false;
+  return true;
+}
+
+// Workers that will be launched: all SMs x workers per SM, limited by occupancy.
+static int launch_workers(const Resolved &r, const DeviceInfo &di) {
+  if (di.sms <= 0) return 1024;
+  std::call_once(g_attr_once, [] {
+    cudaFuncSetAttribute(factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  });
+  const size_t smem = factor_smem_bytes(r.T, 2 * di.sms);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, factor_kernel, NT, smem) != cudaSuccess)
+    per_sm = 1;
+  per_sm = std::max(1, std::min(per_sm, r.wps));
+  int W = di.sms * per_sm;
+  if (r.W > 0) W = std::min(W, r.W);
+  return W;
+}
+
+}  // namespace chol
+
+using namespace chol;
+
+extern "C" size_t chol_factor_workspace_size(int n, const chol_opts *opts) {
+  Resolved r;
+  if (n < 0 || !resolve(n, opts, r)) return 0;
+  const DeviceInfo di = current_device_info();
+  const int W = launch_workers(r, di);
+  return make_layout(n, r, W).total;
+}
+
+extern "C" long long chol_factor_trace_offset(int n, const chol_opts *opts) {
+  Resolved r;
+  if (n < 0 || !resolve(n, opts, r) || !r.trace) return -1;
+  const DeviceInfo di = current_device_info();
+  const int W = launch_workers(r, di);
+  return (long long)make_layout(n, r, W).trace;
+}
+
+extern "C" int chol_num_workers(const chol_opts *opts) {
+  Resolved r;
+  if (!resolve(1, opts, r)) return 0;
+  const DeviceInfo di = current_device_info();
+  if (di.sms <= 0) return 0;
+  return launch_workers(r, di);
+}
+
+extern "C" chol_status chol_factor(int n, double *dA, int lda, const chol_opts *opts, void *dWork,
+                                   size_t work_bytes, int *dInfo, void *stream) {
+  Resolved r;
+  if (n < 0 || !dInfo || !resolve(n, opts, r)) return CHOL_ERR_INVALID_ARG;
+  if (lda < std::max(1, n) || (n > 0 && !dA)) return CHOL_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n == 0) {
+    CHOL_CUDA_TRY(cudaMemsetAsync(dInfo, 0, sizeof(int), s));
+    return CHOL_OK;
+  }
+  const DeviceInfo di = current_device_info();
+  if (di.sms <= 0) return CHOL_ERR_CUDA;
+  if (di.cc_major != 10 || di.cc_minor != 3) return CHOL_ERR_UNSUPPORTED;
+  const int W = launch_workers(r, di);
+  const Layout L = make_layout(n, r, W);
+  if (!dWork || work_bytes < L.total || ((uintptr_t)dWork & 255)) return CHOL_ERR_WORKSPACE;
+  unsigned char *ws = static_cast<unsigned char *>(dWork);
+
+  FactorArgs a;
+  a.A = dA; a.lda = lda; a.n = n; a.nb = r.nb; a.T = r.T; a.ntasks = L.ntasks;
+  a.W = W; a.C = L.C;
+  a.policy = r.policy; a.queue_order = r.queue_order; a.steal = r.steal;
+  a.dada_max_iter = r.max_iter; a.trace = r.trace;
+  a.alpha = r.alpha; a.dada_eps = r.eps;
+  for (int k = 0; k < 4; ++k) a.cost[k] = r.cost[k];
+  a.timeout_ns = r.timeout_ns;
+  a.iter_limit = std::max<int64_t>(100000, r.timeout_ns / 256);
+  a.ctrl = reinterpret_cast<Ctrl *>(ws + L.ctrl);
+  a.cnt = reinterpret_cast<int *>(ws + L.cnt);
+  a.bl = reinterpret_cast<int64_t *>(ws + L.bl);
+  a.owner = reinterpret_cast<int *>(ws + L.owner);
+  a.slots = reinterpret_cast<unsigned long long *>(ws + L.slots);
+  a.qhead = reinterpret_cast<unsigned int *>(ws + L.qhead);
+  a.qcount = reinterpret_cast<int *>(ws + L.qcount);
+  a.qcost = reinterpret_cast<unsigned long long *>(ws + L.qcost);
+  a.run_end = reinterpret_cast<unsigned long long *>(ws + L.run_end);
+  a.trace_buf = r.trace ? reinterpret_cast<long long *>(ws + L.trace) : nullptr;
+
+  CHOL_CUDA_TRY(cudaMemsetAsync(ws, 0, L.zero_end, s));
+  if (r.trace) CHOL_CUDA_TRY(cudaMemsetAsync(ws + L.trace, 0xff, (size_t)L.ntasks * 32, s));
+  {
+    const int64_t work = std::max<int64_t>(L.ntasks, (int64_t)r.T * r.T);
+    const int blocks = (int)std::min<int64_t>((work + 255) / 256, (int64_t)di.sms * 8);
+    init_kernel<<<blocks, 256, 0, s>>>(r.T, L.ntasks, a.cnt, a.owner, r.hold_task);
+    CHOL_CUDA_TRY(cudaGetLastError());
+  }
+  if (r.queue_order == 0) {
+    bottom_level_kernel<<<1, 1024, 0, s>>>(r.T, r.cost[0], r.cost[1], r.cost[2], r.cost[3], a.bl);
+    CHOL_CUDA_TRY(cudaGetLastError());
+  }
+  const size_t smem = factor_smem_bytes(r.T, W);
+  void *args[] = {(void *)&a};
+  CHOL_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)factor_kernel, dim3(W), dim3(NT), args, smem, s));
+  copy_info_kernel<<<1, 32, 0, s>>>(a.ctrl, dInfo);
+  CHOL_CUDA_TRY(cudaGetLastError());
+  return CHOL_OK;
+}

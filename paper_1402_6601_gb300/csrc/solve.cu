@@ -1,0 +1,311 @@
+// Forward and back substitution with the Cholesky factor, L Y = B then L^T X = Y.
+//
+// The right-hand sides are cut into 32-row blocks r and groups g of up to 64 columns. One
+// thread block handles one item (r, g) at a time: it accumulates B_r - sum_m L_rm Y_m over
+// the blocks m already solved (forward; L_mr^T X_m over m > r backward), waiting on each
+// m's ready flag, then solves the 32 x 32 diagonal block and publishes Y_r. Items are
+// claimed from an atomic counter in solve order, so every item waits only on items that
+// were claimed earlier and are held by running blocks: the sweep always progresses, with
+// or without co-residency. Waits are bounded (timeout -> CHOL_INFO_TIMEOUT in *dInfo).
+//
+// Both sweeps are FP64 FMA bound on sm_103 (n^2 nrhs fused multiply-adds against n^2/2 * 8
+// bytes of L): the inner products run from shared memory, four-way unrolled in k.
+#include <algorithm>
+#include <mutex>
+#include "common.cuh"
+
+namespace chol {
+
+constexpr int SB = 32;   // rows per block
+constexpr int SG = 64;   // right-hand sides per group
+constexpr int SNT = 256;
+constexpr int SLD = SB + 1;
+constexpr int SOLVE_EXCL_SMEM = 120 * 1024;  // unused bytes that keep the SM to one block
+
+struct SolveCtrl {
+  unsigned int next_item;
+  int abort;
+  int info;
+  int pad[61];
+};
+
+struct SolveArgs {
+  const double *L;
+  int64_t lda;
+  double *B;
+  int64_t ldb;
+  int n, nrhs, nrb, ngroups;
+  int64_t nitems;
+  int trans;  // 0: L Y = B (forward), 1: L^T X = B (backward)
+  int64_t timeout_ns;
+  SolveCtrl *ctrl;
+  const int *prev_abort;  // abort flag of the sweep that produced B (nullable)
+  int *flags;
+};
+
+// b / d from r = RN(1/d) with one Markstein correction step (see the tile bodies): the
+// correctly rounded quotient in three dependent operations.
+__device__ __forceinline__ double squot(double b, double d, double r) {
+  const double x = b * r;
+  const double e = fma(-x, d, b);
+  return fma(e, r, x);
+}
+
+__global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ SolveArgs a) {
+  __shared__ double Ls[SB * SLD];
+  __shared__ double Ys[SB * SG];
+  __shared__ double Red[8 * SB * 8];  // partial sums of the k-split path [slice][row][col]
+  __shared__ double Rs[SB];           // reciprocals of the diagonal block
+  __shared__ long long s_item;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int rr = lane, cs = warp;  // accumulation: row rr of the block, slice cs
+  while (true) {
+    if (tid == 0) {
+      s_abort = ld_volatile(&a.ctrl->abort) || (a.prev_abort && ld_volatile(a.prev_abort));
+      s_item = s_abort ? -1 : (long long)atomicAdd(&a.ctrl->next_item, 1u);
+    }
+    __syncthreads();
+    const long long item = s_item;
+    if (item < 0 || item >= a.nitems) break;
+    const int g = (int)(item % a.ngroups);
+    const int ord = (int)(item / a.ngroups);
+    const int r = a.trans ? a.nrb - 1 - ord : ord;
+    const int r0 = r * SB, rows = min(SB, a.n - r0);
+    const int c0 = g * SG, cols = min(SG, a.nrhs - c0);
+    // With 8 or more columns, slice cs owns columns cs + 8q over all k. With fewer, every
+    // slice owns all columns and the k range is split: slice cs takes k = cs + 8t.
+    const bool ksplit = cols < 8;
+    double acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int c = cs + 8 * q;
+      acc[q] = (!ksplit && rr < rows && c < cols) ? __ldcg(a.B + (int64_t)(c0 + c) * a.ldb + r0 + rr) : 0.0;
+    }
+    // blocks are consumed in the order the sweep produces them (forward: 0, 1, ...;
+    // backward: nrb-1, nrb-2, ...), so an item only waits on the newest block it needs
+    const int nsteps = a.trans ? a.nrb - 1 - r : r;
+    for (int step = 0; step < nsteps; ++step) {
+      const int m = a.trans ? a.nrb - 1 - step : step;
+      const int m0 = m * SB, mrows = min(SB, a.n - m0);
+      // L block into Ls as Ls[row of the r block][k] (forward: L_rm; backward: L_mr^T)
+      for (int e = tid; e < SB * SB; e += SNT) {
+        const int i = e & 31, j = e >> 5;
+        if (!a.trans) {  // element (r0+i, m0+j)
+          Ls[i * SLD + j] = (i < rows && j < mrows) ? __ldcg(a.L + (int64_t)(m0 + j) * a.lda + r0 + i) : 0.0;
+        } else {         // element (m0+i, r0+j) stored at [j][i]
+          Ls[j * SLD + i] = (i < mrows && j < rows) ? __ldcg(a.L + (int64_t)(r0 + j) * a.lda + m0 + i) : 0.0;
+        }
+      }
+      // wait until block m of this group is solved
+      if (tid == 0) {
+        const uint64_t t0 = globaltimer_ns();
+        int64_t spins = 0;
+        unsigned sl = 32;
+        while (ld_volatile(&a.flags[(int64_t)m * a.ngroups + g]) == 0) {
+          if (ld_volatile(&a.ctrl->abort)) { s_abort = 1; break; }
+          if (globaltimer_ns() - t0 > (uint64_t)a.timeout_ns || ++spins > (a.timeout_ns >> 8) + 100000) {
+            atomicCAS(&a.ctrl->info, 0, CHOL_INFO_TIMEOUT);
+            atomicExch(&a.ctrl->abort, 1);
+            s_abort = 1;
+            break;
+          }
+          __nanosleep(sl);
+          sl = sl < 1024 ? sl * 2 : 1024;
+        }
+        __threadfence();
+      }
+      __syncthreads();
+      if (s_abort) break;
+      for (int e = tid; e < SB * SG; e += SNT) {
+        const int k = e & 31, c = e >> 5;
+        Ys[k * SG + c] = (k < mrows && c < cols) ? __ldcg(a.B + (int64_t)(c0 + c) * a.ldb + m0 + k) : 0.0;
+      }
+      __syncthreads();
+      if (!ksplit) {
+#pragma unroll 4
+        for (int k = 0; k < SB; ++k) {
+          const double l = Ls[rr * SLD + k];
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (cs + 8 * q < cols) acc[q] = fma(-l, Ys[k * SG + cs + 8 * q], acc[q]);
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int k = cs + 8 * t;
+          const double l = Ls[rr * SLD + k];
+#pragma unroll
+          for (int q = 0; q < 7; ++q)
+            if (q < cols) acc[q] = fma(-l, Ys[k * SG + q], acc[q]);
+        }
+      }
+      __syncthreads();
+    }
+    if (s_abort) break;
+    // diagonal block: Ls = L_rr (lower, [i][j]); Ys = accumulated right-hand sides [row][col].
+    // One thread per right-hand side runs the substitution with four interleaved partial
+    // sums, so the block's FP64 instructions are all useful and the chain is short.
+    for (int e = tid; e < SB * SB; e += SNT) {
+      const int i = e & 31, j = e >> 5;
+      Ls[i * SLD + j] = (i < rows && j < rows && i >= j) ? __ldcg(a.L + (int64_t)(r0 + j) * a.lda + r0 + i) : 0.0;
+    }
+    if (tid < rows) Rs[tid] = 1.0 / __ldcg(a.L + (int64_t)(r0 + tid) * a.lda + r0 + tid);
+    if (!ksplit) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) Ys[rr * SG + cs + 8 * q] = acc[q];
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) Red[(cs * SB + rr) * 8 + q] = acc[q];
+    }
+    __syncthreads();
+    if (ksplit && tid < SB * 8) {
+      const int i = tid & 31, q = tid >> 5;
+      if (q < cols) {
+        double t = (i < rows) ? __ldcg(a.B + (int64_t)(c0 + q) * a.ldb + r0 + i) : 0.0;
+        for (int s = 0; s < 8; ++s) t += Red[(s * SB + i) * 8 + q];
+        Ys[i * SG + q] = t;
+      }
+    }
+    __syncthreads();
+    if (tid < cols) {
+      const int c = tid;
+      double x[SB];
+#pragma unroll
+      for (int i = 0; i < SB; ++i) x[i] = Ys[i * SG + c];
+      if (!a.trans) {
+#pragma unroll
+        for (int i = 0; i < SB; ++i) {
+          if (i < rows) {
+            double p[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+            for (int k = 0; k < i; ++k) p[k & 3] = fma(Ls[i * SLD + k], x[k], p[k & 3]);
+            x[i] = squot(x[i] - ((p[0] + p[1]) + (p[2] + p[3])), Ls[i * SLD + i], Rs[i]);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int i = SB - 1; i >= 0; --i) {
+          if (i < rows) {
+            double p[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+            for (int k = i + 1; k < SB; ++k)
+              if (k < rows) p[k & 3] = fma(Ls[k * SLD + i], x[k], p[k & 3]);
+            x[i] = squot(x[i] - ((p[0] + p[1]) + (p[2] + p[3])), Ls[i * SLD + i], Rs[i]);
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < SB; ++i)
+        if (i < rows) __stcg(a.B + (int64_t)(c0 + c) * a.ldb + r0 + i, x[i]);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) *(volatile int *)&a.flags[(int64_t)r * a.ngroups + g] = 1;
+  }
+}
+
+__global__ void solve_info_kernel(const SolveCtrl *c0, const SolveCtrl *c1, int *dInfo) {
+  if (threadIdx.x == 0) *dInfo = c0->info ? c0->info : (c1 ? c1->info : 0);
+}
+
+// workspace: two control blocks (one per sweep) and two flag arrays
+static size_t flags_bytes(int n, int nrhs) {
+  const int64_t nrb = (n + SB - 1) / SB;
+  const int64_t ng = (nrhs + SG - 1) / SG;
+  return align_up((size_t)std::max<int64_t>(1, nrb * ng) * 4, 256);
+}
+static size_t solve_ws(int n, int nrhs) { return 512 + 2 * flags_bytes(n, nrhs); }
+
+static chol_status launch_sweep(int trans, int slot, int n, int nrhs, const double *dL, int lda,
+                                double *dB, int ldb, void *dWork, cudaStream_t s) {
+  SolveArgs a;
+  a.L = dL; a.lda = lda; a.B = dB; a.ldb = ldb; a.n = n; a.nrhs = nrhs;
+  a.nrb = (n + SB - 1) / SB;
+  a.ngroups = (nrhs + SG - 1) / SG;
+  a.nitems = (int64_t)a.nrb * a.ngroups;
+  a.trans = trans;
+  a.timeout_ns = 10000000000ll;
+  unsigned char *ws = static_cast<unsigned char *>(dWork);
+  a.ctrl = reinterpret_cast<SolveCtrl *>(ws + 256 * slot);
+  a.prev_abort = slot == 1 ? &reinterpret_cast<SolveCtrl *>(ws)->abort : nullptr;
+  a.flags = reinterpret_cast<int *>(ws + 512 + flags_bytes(n, nrhs) * slot);
+  CHOL_CUDA_TRY(cudaMemsetAsync(a.ctrl, 0, 256, s));
+  CHOL_CUDA_TRY(cudaMemsetAsync(a.flags, 0, flags_bytes(n, nrhs), s));
+  // One block per SM: FP64 work of a second block on the same SM would starve the
+  // dependent chain of the diagonal solves (a dependent FP64 operation waits behind every
+  // queued FP64 instruction of the SM). The dynamic shared memory request (more than half
+  // of an SM's) makes a second block impossible.
+  const DeviceInfo di = current_device_info();
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_EXCL_SMEM);
+  });
+  const int64_t grid = std::min<int64_t>(a.nitems, (int64_t)std::max(1, di.sms));
+  solve_kernel<<<(int)grid, SNT, SOLVE_EXCL_SMEM, s>>>(a);
+  CHOL_CUDA_TRY(cudaGetLastError());
+  return CHOL_OK;
+}
+
+static chol_status write_info(void *dWork, int slots, int *dInfo, cudaStream_t s) {
+  if (!dInfo) return CHOL_OK;
+  unsigned char *ws = static_cast<unsigned char *>(dWork);
+  const SolveCtrl *c0 = reinterpret_cast<const SolveCtrl *>(ws);
+  const SolveCtrl *c1 = slots > 1 ? reinterpret_cast<const SolveCtrl *>(ws + 256) : nullptr;
+  solve_info_kernel<<<1, 32, 0, s>>>(c0, c1, dInfo);
+  CHOL_CUDA_TRY(cudaGetLastError());
+  return CHOL_OK;
+}
+
+static chol_status check_args(int n, int nrhs, const double *dL, int lda, double *dB, int ldb,
+                              void *dWork, size_t work_bytes) {
+  if (n < 0 || nrhs < 0) return CHOL_ERR_INVALID_ARG;
+  if (lda < std::max(1, n) || ldb < std::max(1, n)) return CHOL_ERR_INVALID_ARG;
+  if (n > 0 && nrhs > 0 && (!dL || !dB)) return CHOL_ERR_INVALID_ARG;
+  if (n > 0 && nrhs > 0 && (!dWork || work_bytes < solve_ws(n, nrhs) || ((uintptr_t)dWork & 255)))
+    return CHOL_ERR_WORKSPACE;
+  return CHOL_OK;
+}
+
+}  // namespace chol
+
+using namespace chol;
+
+extern "C" size_t chol_solve_workspace_size(int n, int nrhs) {
+  if (n < 0 || nrhs < 0) return 0;
+  return solve_ws(n, nrhs);
+}
+
+extern "C" chol_status chol_trsm_sweep(int uplo_t, int n, int nrhs, const double *dL, int lda,
+                                       double *dB, int ldb, void *dWork, size_t work_bytes,
+                                       int *dInfo, void *stream) {
+  const chol_status st = check_args(n, nrhs, dL, lda, dB, ldb, dWork, work_bytes);
+  if (st != CHOL_OK) return st;
+  if (uplo_t != 0 && uplo_t != 1) return CHOL_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n == 0 || nrhs == 0) {
+    if (dInfo) CHOL_CUDA_TRY(cudaMemsetAsync(dInfo, 0, sizeof(int), s));
+    return CHOL_OK;
+  }
+  const chol_status r = launch_sweep(uplo_t, 0, n, nrhs, dL, lda, dB, ldb, dWork, s);
+  if (r != CHOL_OK) return r;
+  return write_info(dWork, 1, dInfo, s);
+}
+
+extern "C" chol_status chol_solve(int n, int nrhs, const double *dL, int lda, double *dB, int ldb,
+                                  void *dWork, size_t work_bytes, int *dInfo, void *stream) {
+  const chol_status st = check_args(n, nrhs, dL, lda, dB, ldb, dWork, work_bytes);
+  if (st != CHOL_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n == 0 || nrhs == 0) {
+    if (dInfo) CHOL_CUDA_TRY(cudaMemsetAsync(dInfo, 0, sizeof(int), s));
+    return CHOL_OK;
+  }
+  chol_status r = launch_sweep(0, 0, n, nrhs, dL, lda, dB, ldb, dWork, s);
+  if (r != CHOL_OK) return r;
+  // the backward sweep skips its work if the forward one aborted
+  r = launch_sweep(1, 1, n, nrhs, dL, lda, dB, ldb, dWork, s);
+  if (r != CHOL_OK) return r;
+  return write_info(dWork, 2, dInfo, s);
+}

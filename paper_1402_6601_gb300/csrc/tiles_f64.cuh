@@ -1,0 +1,244 @@
+// FP64 tile task bodies, executed by one 256-thread block (one worker) at a time.
+//
+// On sm_103 the FP64 units retire two fused multiply-adds per clock per SM, and the FP64
+// mma.sync shapes run slower than plain DFMA, so the contraction is a register-tiled DFMA
+// update fed through shared memory: every operand byte is reused 32 times from shared
+// memory and 4 times from registers, far more than the FP64 rate needs, and the tile
+// bodies stay bound by the FP64 pipe.
+//
+// Global memory is read with ld.global.cg and written with st.global.cg: tiles written by
+// one worker are read by others after the dependency counters say so, and L2 is the point
+// where all SMs see the same bytes.
+#pragma once
+#include <stdint.h>
+
+namespace chol {
+
+constexpr int NT = 256;  // threads per worker
+constexpr int BM = 64, BN = 64, BK = 32;
+constexpr int IB = 32;   // inner block of the POTRF and TRSM bodies
+constexpr int DS_LD = IB + 1;
+
+// shared memory: staging [2][BK][BM] + [2][BK][BN] doubles, then the 32 x 33 diagonal block
+// and the reciprocals of its diagonal
+constexpr int STAGE_DOUBLES = 2 * BK * BM + 2 * BK * BN;
+constexpr int TILE_SMEM_BYTES = (STAGE_DOUBLES + IB * DS_LD + IB) * 8;
+
+__device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ void stcg(double *p, double v) { __stcg(p, v); }
+
+// C[M x N] -= A[M x K] * B[N x K]^T, column-major. With `lower`, only elements with
+// row >= column (relative to C) are written and blocks wholly above the diagonal skipped.
+// Called by all NT threads; ends with the block synchronised.
+__device__ __noinline__ void update_nt(double *C, int64_t ldc, const double *A, int64_t lda,
+                                       const double *B, int64_t ldb, int M, int N, int K,
+                                       bool lower, double *smem) {
+  double *As = smem;
+  double *Bs = smem + 2 * BK * BM;
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int lrow = tid & 63, lk = tid >> 6;  // loader: row lrow, k columns lk + 4q
+  for (int bn = 0; bn < N; bn += BN) {
+    for (int bm = 0; bm < M; bm += BM) {
+      if (lower && bm + BM <= bn) continue;
+      double acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+      double ra[8], rb[8];
+      const bool arow = bm + lrow < M, brow = bn + lrow < N;
+      const double *Ap = A + bm + lrow;
+      const double *Bp = B + bn + lrow;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int kk = lk + 4 * q;
+        ra[q] = (arow && kk < K) ? ldcg(Ap + (int64_t)kk * lda) : 0.0;
+        rb[q] = (brow && kk < K) ? ldcg(Bp + (int64_t)kk * ldb) : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        As[(lk + 4 * q) * BM + lrow] = ra[q];
+        Bs[(lk + 4 * q) * BN + lrow] = rb[q];
+      }
+      __syncthreads();
+      int buf = 0;
+      for (int k0 = 0; k0 < K; k0 += BK) {
+        const bool more = k0 + BK < K;
+        if (more) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int kk = k0 + BK + lk + 4 * q;
+            ra[q] = (arow && kk < K) ? ldcg(Ap + (int64_t)kk * lda) : 0.0;
+            rb[q] = (brow && kk < K) ? ldcg(Bp + (int64_t)kk * ldb) : 0.0;
+          }
+        }
+        const double *as = As + buf * BK * BM;
+        const double *bs = Bs + buf * BK * BN;
+#pragma unroll 8
+        for (int kk = 0; kk < BK; ++kk) {
+          double a[4], b[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) a[i] = as[kk * BM + tx + 16 * i];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) b[j] = bs[kk * BN + ty + 16 * j];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        if (more) {
+          double *an = As + (buf ^ 1) * BK * BM;
+          double *bnx = Bs + (buf ^ 1) * BK * BN;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            an[(lk + 4 * q) * BM + lrow] = ra[q];
+            bnx[(lk + 4 * q) * BN + lrow] = rb[q];
+          }
+        }
+        __syncthreads();
+        buf ^= 1;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = bn + ty + 16 * j;
+        if (c >= N) continue;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int r = bm + tx + 16 * i;
+          if (r < M && (!lower || r >= c)) {
+            double *cp = C + (int64_t)c * ldc + r;
+            stcg(cp, ldcg(cp) - acc[i][j]);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Quotient b / d from the correctly rounded reciprocal r = RN(1/d) with one correction step
+// (Markstein, 1990): x = RN(b r); e = b - x d is exact with a fused multiply-add; RN(x + e r)
+// is the correctly rounded quotient outside overflow and underflow. Three dependent
+// operations instead of a full division on the substitution's critical chain; exact
+// quotients (integer data) are recovered exactly.
+__device__ __forceinline__ double quot(double b, double d, double r) {
+  const double x = b * r;
+  const double e = fma(-x, d, b);
+  return fma(e, r, x);
+}
+
+// Forward substitution of one row against the pb x pb lower block D (shared, ld DS_LD):
+// x D^T = b. Column-oriented: x_c = (b_c - sum_{m<c} x_m d_cm) / d_cc with the sum built up
+// in increasing m as the x_m become known, so each x_c is at the end of a short chain.
+// Row r of the panel P (column-major). Rinv holds 1/d_cc.
+__device__ __forceinline__ void row_solve_lt(double *P, int64_t ldp, int r, int pb, const double *Ds,
+                                             const double *Rinv) {
+  double x[IB];
+#pragma unroll
+  for (int c = 0; c < IB; ++c) x[c] = c < pb ? ldcg(P + (int64_t)c * ldp + r) : 0.0;
+#pragma unroll
+  for (int c = 0; c < IB; ++c) {
+    if (c < pb) {
+      x[c] = quot(x[c], Ds[c * DS_LD + c], Rinv[c]);
+#pragma unroll
+      for (int m = c + 1; m < IB; ++m)
+        if (m < pb) x[m] = fma(-x[c], Ds[m * DS_LD + c], x[m]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < IB; ++c)
+    if (c < pb) stcg(P + (int64_t)c * ldp + r, x[c]);
+}
+
+// Load the lower part of the pb x pb block at G (column-major, ld) into Ds (row-major).
+__device__ __forceinline__ void load_diag_block(const double *G, int64_t ld, int pb, double *Ds) {
+  for (int e = threadIdx.x; e < IB * IB; e += NT) {
+    const int r = e & (IB - 1), c = e >> 5;
+    Ds[r * DS_LD + c] = (r < pb && c < pb && r >= c) ? ldcg(G + (int64_t)c * ld + r) : 0.0;
+  }
+}
+
+// POTRF on the nk x nk diagonal tile G (in place, lower). Returns 0, or the 1-based column
+// inside the tile whose pivot is not positive (or NaN). Called by all threads.
+__device__ __noinline__ int potrf_tile(double *G, int64_t ld, int nk, double *smem) {
+  double *Ds = smem + STAGE_DOUBLES;
+  double *Rinv = Ds + IB * DS_LD;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x;
+  for (int p = 0; p < nk; p += IB) {
+    const int pb = min(IB, nk - p);
+    double *Gpp = G + (int64_t)p * ld + p;
+    load_diag_block(Gpp, ld, pb, Ds);
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    // unblocked right-looking factor of the pb x pb block by warp 0, lane r owns row r
+    if (tid < 32) {
+      const int r = tid;
+      int fail = 0;
+      for (int j = 0; j < pb; ++j) {
+        const double s = Ds[j * DS_LD + j];
+        if (!(s > 0.0)) { fail = p + j + 1; break; }
+        const double ljj = sqrt(s);
+        __syncwarp();
+        if (r == j) Ds[j * DS_LD + j] = ljj;
+        if (r > j && r < pb) Ds[r * DS_LD + j] = Ds[r * DS_LD + j] / ljj;
+        __syncwarp();
+        if (r > j && r < pb) {
+          const double lrj = Ds[r * DS_LD + j];
+          for (int c = j + 1; c <= r; ++c) Ds[r * DS_LD + c] = fma(-lrj, Ds[c * DS_LD + j], Ds[r * DS_LD + c]);
+        }
+        __syncwarp();
+      }
+      if (r == 0) s_fail = fail;
+      if (!fail && r < pb) Rinv[r] = 1.0 / Ds[r * DS_LD + r];
+    }
+    __syncthreads();
+    if (s_fail) return s_fail;
+    for (int e = tid; e < IB * IB; e += NT) {
+      const int r = e & (IB - 1), c = e >> 5;
+      if (r < pb && c < pb && r >= c) stcg(Gpp + (int64_t)c * ld + r, Ds[r * DS_LD + c]);
+    }
+    // panel below the diagonal block: rows p+pb..nk-1 of columns p..p+pb-1
+    const int rows = nk - p - pb;
+    double *Pn = G + (int64_t)p * ld + p + pb;
+    for (int r0 = 0; r0 < rows; r0 += NT) {
+      const int r = r0 + tid;
+      if (r < rows) row_solve_lt(Pn, ld, r, pb, Ds, Rinv);
+    }
+    __syncthreads();
+    if (rows > 0) {
+      double *Gt = G + (int64_t)(p + pb) * ld + p + pb;
+      update_nt(Gt, ld, Pn, ld, Pn, ld, rows, rows, pb, true, smem);
+    }
+  }
+  __syncthreads();
+  return 0;
+}
+
+// TRSM: X L^T = B in place on B (mb x nk), L the nk x nk lower factor tile.
+__device__ __noinline__ void trsm_tile(double *B, int64_t ldb, const double *L, int64_t ldl,
+                                       int mb, int nk, double *smem) {
+  double *Ds = smem + STAGE_DOUBLES;
+  double *Rinv = Ds + IB * DS_LD;
+  const int tid = threadIdx.x;
+  for (int p = 0; p < nk; p += IB) {
+    const int pb = min(IB, nk - p);
+    load_diag_block(L + (int64_t)p * ldl + p, ldl, pb, Ds);
+    if (tid < pb) Rinv[tid] = 1.0 / ldcg(L + (int64_t)(p + tid) * ldl + p + tid);
+    __syncthreads();
+    double *Bp = B + (int64_t)p * ldb;
+    for (int r0 = 0; r0 < mb; r0 += NT) {
+      const int r = r0 + tid;
+      if (r < mb) row_solve_lt(Bp, ldb, r, pb, Ds, Rinv);
+    }
+    __syncthreads();
+    const int rest = nk - p - pb;
+    if (rest > 0)
+      update_nt(B + (int64_t)(p + pb) * ldb, ldb, Bp, ldb, L + (int64_t)p * ldl + p + pb, ldl, mb,
+                rest, pb, false, smem);
+  }
+  __syncthreads();
+}
+
+}  // namespace chol

@@ -1,0 +1,125 @@
+"""CPU checks of the C ABI library: it loads, exports every declared symbol, and its
+host-side graph and placement code (the code the persistent kernel runs) matches the
+oracles derived from the paper's data-flow rule (Section 2) and Algorithms 1 and 2."""
+import ctypes
+import os
+import random
+import re
+
+import numpy as np
+import pytest
+
+import oracle.dag as odag
+import oracle.sched as osched
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "chol.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(chol_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_function():
+    import paper_1402_6601_gb300 as chol
+    names = _declared_functions()
+    assert len(names) >= 15
+    L = ctypes.CDLL(chol.build.LIB)
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_opts_struct_layout_matches_header():
+    import paper_1402_6601_gb300 as chol
+    o = chol.ChOpts()
+    chol.lib.chol_opts_default(ctypes.byref(o))
+    assert o.nb == 256 and o.policy == 0 and o.alpha == 0.5 and o.steal == 1
+    assert o.dada_max_iter == 16 and abs(o.dada_eps - 0.01) < 1e-15
+    assert o.timeout_ns == 10_000_000_000 and o.trace == 0
+    assert ctypes.sizeof(chol.ChOpts) == 104 and o.hold_task == -1
+
+
+@pytest.mark.parametrize("T", [1, 2, 3, 5, 8, 11])
+def test_dag_matches_dataflow_oracle(T):
+    import paper_1402_6601_gb300 as chol
+    kind, ti, tj, tk, indeg, ptr, succ = chol.dag_describe(T)
+    tasks, preds, succs = odag.build(T)
+    assert len(kind) == len(tasks)
+    lib_tasks = [(int(kind[i]), int(ti[i]), int(tj[i]), int(tk[i])) for i in range(len(kind))]
+    assert sorted(lib_tasks) == sorted(tasks)
+    index = {t: i for i, t in enumerate(lib_tasks)}
+    for i, t in enumerate(lib_tasks):
+        assert indeg[i] == len(preds[t]), t
+        got = {lib_tasks[int(s)] for s in succ[ptr[i]:ptr[i + 1]]}
+        assert got == succs[t], t
+    assert int(chol.lib.chol_dag_edge_count(T)) == sum(len(s) for s in succs.values())
+    assert index[(0, 0, 0, 0)] == 0
+
+
+@pytest.mark.parametrize("T,count", [(8, 120), (64, 45760), (128, 357760)])
+def test_task_counts(T, count):
+    import paper_1402_6601_gb300 as chol
+    assert chol.lib.chol_dag_task_count(T) == count
+
+
+@pytest.mark.parametrize("T", [1, 3, 6, 9])
+def test_bottom_levels_match_oracle(T):
+    import paper_1402_6601_gb300 as chol
+    cost = [7, 30, 31, 60]
+    bl = chol.dag_bottom_levels(T, cost)
+    kind, ti, tj, tk, *_ = chol.dag_describe(T)
+    ref = odag.bottom_levels(T, dict(enumerate(cost)))
+    for i in range(len(bl)):
+        assert bl[i] == ref[(int(kind[i]), int(ti[i]), int(tj[i]), int(tk[i]))]
+
+
+def _random_ready(rng, m, W):
+    return [dict(tid=rng.randint(0, 10**6) * 64 + i, p=rng.choice([100, 300, 300, 600, rng.randint(1, 900)]),
+                 prio=rng.randint(0, 5000), aff=rng.choice([-1] + list(range(W))),
+                 score=rng.choice([0, 131072, 524288])) for i in range(m)]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_heft_host_matches_algorithm_1(seed):
+    import paper_1402_6601_gb300 as chol
+    rng = random.Random(seed)
+    for _ in range(40):
+        W = rng.randint(1, 40)
+        LR = _random_ready(rng, rng.randint(1, 30), W)
+        load = [rng.randint(0, 3000) for _ in range(W)]
+        got, it = chol.sched_activate("heft", LR, load)
+        assert got == osched.heft(LR, load) and it == 0
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("alpha", [0.0, 0.5, 1.0])
+def test_dada_host_matches_algorithm_2(seed, alpha):
+    import paper_1402_6601_gb300 as chol
+    rng = random.Random(100 + seed)
+    for _ in range(40):
+        W = rng.randint(1, 40)
+        LR = _random_ready(rng, rng.randint(1, 30), W)
+        load = [rng.choice([0, rng.randint(0, 3000)]) for _ in range(W)]
+        got, it = chol.sched_activate("dada", LR, load, alpha=alpha)
+        ref, rit = osched.dada(LR, load, alpha)
+        assert got == ref and it == rit
+
+
+def test_sched_rejects_bad_arguments():
+    import paper_1402_6601_gb300 as chol
+    with pytest.raises(chol.CholeskyError):
+        chol.sched_activate("dada", [dict(tid=0, p=1, prio=0, aff=-1, score=0)], [0], alpha=1.5)
+    with pytest.raises(chol.CholeskyError):
+        chol.sched_activate("steal", [dict(tid=0, p=1, prio=0, aff=-1, score=0)], [0])
+
+
+def test_workspace_sizes_are_positive_and_monotone():
+    import paper_1402_6601_gb300 as chol
+    o = chol.opts(nb=128)
+    a = chol.workspace_size(1024, o)
+    b = chol.workspace_size(4096, o)
+    assert 0 < a < b
+    assert chol.workspace_size(1024, chol.opts(nb=8)) == 0  # nb below 16 is rejected
+    assert chol.solve_workspace_size(1024, 1) > 0

@@ -1,0 +1,207 @@
+"""GPU parity of the tiled Cholesky factor and solves against the oracle (same input bytes).
+
+Tolerances: the FP64 factor must match the oracle's L within relative Frobenius error
+1e-12 (kappa(A) <= 5 for the Gram workloads), the solve's normwise backward error must be
+<= 1e-14, and integer inputs (exact in binary64 at every step) must match bitwise.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+REL_L = 1e-12
+BERR = 1e-14
+
+
+@pytest.fixture(scope="module")
+def chol():
+    import paper_1402_6601_gb300 as c
+    return c
+
+
+def _gpu(a):
+    t = torch.from_numpy(np.asfortranarray(a)).to("cuda")
+    return t.t().contiguous().t() if t.dim() == 2 else t
+
+
+def _factor(chol, A_np, o, upper_marker=None):
+    A = chol.colmajor(torch.from_numpy(np.ascontiguousarray(A_np)).to("cuda"))
+    info, work = chol.factor(A, o)
+    torch.cuda.synchronize()
+    return A.cpu().numpy(), int(info.item()), work
+
+
+@pytest.mark.parametrize("n,nb", [(1024, 128), (1000, 128), (300, 64), (77, 32), (16, 16), (1, 16),
+                                  (520, 256), (1100, 512)])
+def test_factor_parity_gram(chol, n, nb):
+    A = synth.gram_spd(n, seed=n + nb).numpy()
+    F, info, _ = _factor(chol, A, chol.opts(nb=nb))
+    assert info == 0
+    Lref = oracle.factor(A)
+    assert oracle.rel_frobenius(np.tril(F), Lref) <= REL_L
+    assert np.all(np.diag(F) > 0)
+
+
+def test_upper_triangle_untouched(chol):
+    n = 700
+    A = synth.gram_spd(n, seed=3).numpy()
+    Ain = np.tril(A) + np.triu(np.full((n, n), -7.25), 1)
+    F, info, _ = _factor(chol, Ain, chol.opts(nb=128))
+    assert info == 0
+    np.testing.assert_array_equal(np.triu(F, 1), np.triu(Ain, 1))
+
+
+@pytest.mark.parametrize("n,nb", [(20, 16), (20, 32), (14, 16)])
+def test_pascal_bitwise(chol, n, nb):
+    F, info, _ = _factor(chol, synth.pascal(n), chol.opts(nb=nb))
+    assert info == 0
+    np.testing.assert_array_equal(np.tril(F), synth.pascal_lower(n))
+
+
+@pytest.mark.parametrize("policy,alpha", [("heft", 0.5), ("dada", 0.0), ("dada", 0.5), ("dada", 1.0),
+                                          ("steal", 0.5), ("static", 0.5)])
+def test_integer_factor_bitwise_every_policy(chol, policy, alpha):
+    L, A = synth.integer_factor(600, seed=5)
+    F, info, _ = _factor(chol, A, chol.opts(nb=64, policy=policy, alpha=alpha))
+    assert info == 0
+    np.testing.assert_array_equal(np.tril(F), L)
+
+
+def test_schedule_invariance_bitwise(chol):
+    # every tile's updates are applied in a fixed k order, so L must not depend on the schedule
+    n = 900
+    A = synth.gram_spd(n, seed=21).numpy()
+    ref = None
+    configs = [chol.opts(nb=64, policy="heft"), chol.opts(nb=64, policy="dada", alpha=0.0),
+               chol.opts(nb=64, policy="dada", alpha=1.0), chol.opts(nb=64, policy="steal"),
+               chol.opts(nb=64, policy="static"), chol.opts(nb=64, policy="heft", workers_per_sm=1),
+               chol.opts(nb=64, policy="heft", num_workers=3), chol.opts(nb=64, policy="dada", num_workers=1)]
+    for o in configs:
+        F, info, _ = _factor(chol, A, o)
+        assert info == 0
+        if ref is None:
+            ref = np.tril(F)
+        else:
+            np.testing.assert_array_equal(np.tril(F), ref)
+
+
+@pytest.mark.parametrize("bad", [1, 200, 511, 512, 700])
+def test_not_spd_info(chol, bad):
+    n = 768
+    A = synth.gram_spd(n, seed=8).numpy()
+    # make the leading minor of order `bad` indefinite: a_jj far below what the rest needs
+    A[bad - 1, bad - 1] = -1.0
+    _, info_ref = oracle.cholesky(A)
+    assert info_ref == bad
+    _, info, _ = _factor(chol, A, chol.opts(nb=128))
+    assert info == bad
+
+
+def test_trace_topological_and_complete(chol):
+    import oracle.dag as odag
+    n, nb = 640, 64
+    T = n // nb
+    o = chol.opts(nb=nb, policy="dada", alpha=0.5, trace=True)
+    A = chol.colmajor(synth.gram_spd(n, seed=2).to("cuda"))
+    info, work = chol.factor(A, o)
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    tr = chol.trace(work, n, o).cpu().numpy()
+    kind, ti, tj, tk, indeg, ptr, succ = chol.dag_describe(T)
+    nw = chol.num_workers(o)
+    assert np.all(tr[:, 0] >= 0) and np.all(tr[:, 0] < nw)       # every task ran once
+    assert np.all(tr[:, 3] >= tr[:, 2])
+    for t in range(len(kind)):
+        for s in succ[ptr[t]:ptr[t + 1]]:
+            assert tr[s, 2] >= tr[t, 3], (t, s)                    # start after predecessor ends
+    assert len(kind) == len(odag.build(T)[0])
+
+
+def test_timeout_is_reported_not_hung(chol):
+    # task 5 gets an extra dependency nobody satisfies: every worker's bounded wait expires
+    n, nb = 512, 64
+    o = chol.opts(nb=nb, timeout_ns=200_000_000, hold_task=5)
+    A = chol.colmajor(synth.gram_spd(n, seed=2).to("cuda"))
+    info, _ = chol.factor(A, o)
+    torch.cuda.synchronize()
+    assert int(info.item()) == chol.INFO_TIMEOUT
+    # the context is still usable
+    A2 = chol.colmajor(synth.gram_spd(n, seed=2).to("cuda"))
+    info2, _ = chol.factor(A2, chol.opts(nb=nb))
+    torch.cuda.synchronize()
+    assert int(info2.item()) == 0
+
+
+@pytest.mark.parametrize("n,nrhs", [(1024, 1), (1000, 70), (33, 3), (64, 64), (5, 1)])
+def test_solve_parity(chol, n, nrhs):
+    A = synth.gram_spd(n, seed=n).numpy()
+    B = synth.rhs(n, nrhs, seed=n + 1).numpy()
+    Ad = chol.colmajor(torch.from_numpy(A).to("cuda"))
+    chol.factor(Ad, chol.opts(nb=128), check=True)
+    Bd = _gpu(B)
+    chol.solve(Ad, Bd)
+    torch.cuda.synchronize()
+    X = Bd.cpu().numpy()
+    assert oracle.backward_error(A, X, B) <= BERR
+    Xref = oracle.solve(oracle.factor(A), B)
+    assert oracle.rel_frobenius(X, Xref) <= 1e-12
+
+
+@pytest.mark.parametrize("n,nrhs", [(200, 1), (333, 65)])
+def test_sweeps_exact_on_integers(chol, n, nrhs):
+    L, A = synth.integer_factor(n, seed=9)
+    X = synth.integer_vector(n, nrhs, 4)
+    Y = L.T @ X
+    B = L @ Y
+    Ld = _gpu(L)
+    Bd = _gpu(B)
+    chol.trsm_sweep(Ld, Bd, transpose=False)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(Bd.cpu().numpy(), Y)
+    chol.trsm_sweep(Ld, Bd, transpose=True)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(Bd.cpu().numpy(), X)
+
+
+def test_sched_device_matches_host(chol):
+    import random
+    rng = random.Random(3)
+    for policy in ("heft", "dada"):
+        for alpha in (0.0, 0.5, 1.0):
+            for _ in range(5):
+                W = rng.randint(1, 300)
+                LR = [dict(tid=i * 7 + 1, p=rng.choice([200, 600, 600, 1200]), prio=rng.randint(0, 9000),
+                           aff=rng.choice([-1, rng.randint(0, W - 1)]), score=rng.choice([0, 524288]))
+                      for i in range(rng.randint(1, 127))]
+                load = [rng.choice([0, rng.randint(0, 5000)]) for _ in range(W)]
+                host = chol.sched_activate(policy, LR, load, alpha=alpha)
+                dev = chol.sched_activate_device(policy, LR, load, alpha=alpha)
+                assert host == dev
+
+
+def test_posv_host(chol):
+    n, nrhs = 600, 3
+    A = np.asfortranarray(synth.gram_spd(n, seed=13).numpy())
+    B = np.asfortranarray(synth.rhs(n, nrhs, seed=14).numpy())
+    A0, B0 = A.copy(), B.copy()
+    info = chol.posv_host(A, B, chol.opts(nb=128))
+    assert info == 0
+    assert oracle.backward_error(A0, B, B0) <= BERR
+    assert oracle.rel_frobenius(np.tril(A), oracle.factor(A0)) <= REL_L
+    np.testing.assert_array_equal(np.triu(A, 1), np.triu(A0, 1))
+
+
+def test_zero_size_and_bad_args(chol):
+    A = torch.zeros(0, 0, dtype=torch.float64, device="cuda")
+    info, _ = chol.factor(A)
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    B = torch.zeros(8, 8, dtype=torch.float64, device="cuda")  # row-major: rejected
+    with pytest.raises(ValueError):
+        chol.factor(B)
+    with pytest.raises(chol.CholeskyError):
+        chol.factor(chol.colmajor(torch.eye(64, dtype=torch.float64, device="cuda")), chol.opts(nb=8))
