@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-sample-n", type=int, default=6144)
+    p.add_argument("--cpu-sample-n", type=int, default=10240)
     p.add_argument("--seed", type=int, default=1)
     return p.parse_args()
 

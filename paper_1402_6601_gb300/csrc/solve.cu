@@ -145,13 +145,16 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
     }
     if (s_abort) break;
     // diagonal block: Ls = L_rr (lower, [i][j]); Ys = accumulated right-hand sides [row][col].
-    // One thread per right-hand side runs the substitution with four interleaved partial
-    // sums, so the block's FP64 instructions are all useful and the chain is short.
+    // One thread per right-hand side runs the substitution, so every FP64 instruction of the
+    // block does useful work (the FP64 pipe, not latency, bounds this phase).
     for (int e = tid; e < SB * SB; e += SNT) {
       const int i = e & 31, j = e >> 5;
-      Ls[i * SLD + j] = (i < rows && j < rows && i >= j) ? __ldcg(a.L + (int64_t)(r0 + j) * a.lda + r0 + i) : 0.0;
+      // rows past the end of the matrix get an identity block, so the substitution below
+      // runs over a fixed 32 rows with register-resident data
+      Ls[i * SLD + j] = (i < rows && j < rows && i >= j) ? __ldcg(a.L + (int64_t)(r0 + j) * a.lda + r0 + i)
+                                                          : (i == j ? 1.0 : 0.0);
     }
-    if (tid < rows) Rs[tid] = 1.0 / __ldcg(a.L + (int64_t)(r0 + tid) * a.lda + r0 + tid);
+    if (tid < SB) Rs[tid] = tid < rows ? 1.0 / __ldcg(a.L + (int64_t)(r0 + tid) * a.lda + r0 + tid) : 1.0;
     if (!ksplit) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) Ys[rr * SG + cs + 8 * q] = acc[q];
@@ -174,26 +177,21 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
       double x[SB];
 #pragma unroll
       for (int i = 0; i < SB; ++i) x[i] = Ys[i * SG + c];
+      // right-looking: once x_k is known every later row is updated at once, so each x_k
+      // is one quotient and one multiply-add after x_{k-1}
       if (!a.trans) {
 #pragma unroll
-        for (int i = 0; i < SB; ++i) {
-          if (i < rows) {
-            double p[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int k = 0; k < SB; ++k) {
+          x[k] = squot(x[k], Ls[k * SLD + k], Rs[k]);
 #pragma unroll
-            for (int k = 0; k < i; ++k) p[k & 3] = fma(Ls[i * SLD + k], x[k], p[k & 3]);
-            x[i] = squot(x[i] - ((p[0] + p[1]) + (p[2] + p[3])), Ls[i * SLD + i], Rs[i]);
-          }
+          for (int i = k + 1; i < SB; ++i) x[i] = fma(-Ls[i * SLD + k], x[k], x[i]);
         }
       } else {
 #pragma unroll
-        for (int i = SB - 1; i >= 0; --i) {
-          if (i < rows) {
-            double p[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int k = SB - 1; k >= 0; --k) {
+          x[k] = squot(x[k], Ls[k * SLD + k], Rs[k]);
 #pragma unroll
-            for (int k = i + 1; k < SB; ++k)
-              if (k < rows) p[k & 3] = fma(Ls[k * SLD + i], x[k], p[k & 3]);
-            x[i] = squot(x[i] - ((p[0] + p[1]) + (p[2] + p[3])), Ls[i * SLD + i], Rs[i]);
-          }
+          for (int i = 0; i < k; ++i) x[i] = fma(-Ls[k * SLD + i], x[k], x[i]);
         }
       }
 #pragma unroll
