@@ -118,6 +118,24 @@ size_t chol_solve_workspace_size(int n, int nrhs);
 chol_status chol_solve(int n, int nrhs, const double *dL, int lda, double *dB, int ldb,
                        void *dWork, size_t work_bytes, int *dInfo, void *stream);
 
+/* Allocation-free chol_solve. The paper has no counterpart: this entry point is for callers
+ * that cannot allocate device memory -- code that must not call cudaMalloc while a stream
+ * is being captured into a CUDA graph, or that runs under a fixed device-memory budget in
+ * which every allocation belongs to the host application -- and so cannot provide the
+ * workspace chol_solve needs. Arguments and results are those of chol_solve.
+ *  - The workspace is a fixed 256 KiB array of this library in device global memory
+ *    (each GPU that loads the library holds it until the process exits). Problems whose
+ *    chol_solve_workspace_size(n, nrhs) exceeds 256 KiB -- ceil(n/32) * ceil(nrhs/64) >
+ *    32704 -- are rejected with CHOL_ERR_UNSUPPORTED before anything is launched.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *    with that device current; make that first call before any stream capture.
+ *  - Every call shares the one array and clears what it needs before use; two calls whose
+ *    work overlaps on the GPU (different streams, no ordering between them) race on it.
+ *  - Calls no cudaMalloc, cudaFree or other allocating routine.
+ */
+chol_status chol_solve_noalloc(int n, int nrhs, const double *dL, int lda, double *dB, int ldb,
+                               int *dInfo, void *stream);
+
 /* One sweep only: uplo_t = 0 solves L Y = B, uplo_t = 1 solves L^T X = B, in place on dB. */
 chol_status chol_trsm_sweep(int uplo_t, int n, int nrhs, const double *dL, int lda, double *dB,
                             int ldb, void *dWork, size_t work_bytes, int *dInfo, void *stream);

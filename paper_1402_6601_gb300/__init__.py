@@ -68,6 +68,7 @@ _SIGNATURES = {
     "chol_solve_workspace_size": (_SZ, [_I, _I]),
     "chol_solve": (_I, [_I, _I, _P, _I, _P, _I, _P, _SZ, _P, _P]),
     "chol_trsm_sweep": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _SZ, _P, _P]),
+    "chol_solve_noalloc": (_I, [_I, _I, _P, _I, _P, _I, _P, _P]),
     "chol_posv_host_stage_size": (_SZ, [_I, _I, _OPTS]),
     "chol_posv_host": (_I, [_I, _I, _P, _I, _P, _I, _OPTS, _P, _SZ, _P, _P]),
     "chol_dag_task_count": (_LL, [_I]),

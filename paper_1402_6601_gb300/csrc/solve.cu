@@ -307,3 +307,51 @@ extern "C" chol_status chol_solve(int n, int nrhs, const double *dL, int lda, do
   if (r != CHOL_OK) return r;
   return write_info(dWork, 2, dInfo, s);
 }
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free variant of chol_solve. Its workspace is a fixed array of this library in
+// device global memory, so the caller needs no device allocation at all.
+
+namespace chol {
+
+constexpr size_t SOLVE_NOALLOC_BYTES = 256 * 1024;
+static __device__ __align__(256) unsigned char g_solve_scratch[SOLVE_NOALLOC_BYTES];
+
+// Device address of g_solve_scratch on device `dev` (which must be current). In host code
+// the symbol's name is only a host-side stand-in, so the address is looked up once per
+// device with cudaGetSymbolAddress and cached.
+static void *noalloc_scratch(int dev, cudaError_t *err) {
+  static std::mutex mu;
+  static void *ptrs[128] = {};
+  if (dev < 0 || dev >= 128) {
+    *err = cudaErrorInvalidDevice;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (!ptrs[dev]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_solve_scratch);
+    if (e != cudaSuccess) {
+      *err = e;
+      return nullptr;
+    }
+    ptrs[dev] = p;
+  }
+  *err = cudaSuccess;
+  return ptrs[dev];
+}
+
+}  // namespace chol
+
+extern "C" chol_status chol_solve_noalloc(int n, int nrhs, const double *dL, int lda, double *dB,
+                                          int ldb, int *dInfo, void *stream) {
+  if (n < 0 || nrhs < 0) return CHOL_ERR_INVALID_ARG;
+  if (solve_ws(n, nrhs) > SOLVE_NOALLOC_BYTES) return CHOL_ERR_UNSUPPORTED;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CHOL_ERR_CUDA;
+  cudaError_t err = cudaSuccess;
+  void *scratch = noalloc_scratch(dev, &err);
+  if (!scratch) return CHOL_ERR_CUDA;
+  // the sweeps clear the control blocks and flags they use before every launch
+  return chol_solve(n, nrhs, dL, lda, dB, ldb, scratch, SOLVE_NOALLOC_BYTES, dInfo, stream);
+}
