@@ -32,6 +32,11 @@ FP64_FMA_PER_CLK_PER_SM = 2       # measured: DFMA retires 2 FMA/clk/SM on sm_10
 SM_MAX_MHZ = 2070.0
 FP64_PEAK_GFLOPS = SMS * FP64_FMA_PER_CLK_PER_SM * 2 * SM_MAX_MHZ / 1000.0  # 1258.6
 
+# DRAM bytes (read + write) of one factor launch, from a one-pass ncu capture of this exact
+# configuration (profiles/bench_n32768_nb256_launch_list.txt); None for configurations that
+# were not captured with the current kernel.
+MEASURED_FACTOR_TRAFFIC = {(32768, 256, "heft"): 984613983232 + 197278910208}
+
 
 def parse():
     p = argparse.ArgumentParser()
@@ -256,7 +261,8 @@ def main():
     fac_avg = sum(fac_ms) / len(fac_ms)
     achieved = n ** 3 / 3.0 / (fac_avg / 1000.0) / 1e9
     roofline = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(FP64_PEAK_GFLOPS, 1),
-                "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": None,
+                "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
+                "traffic": MEASURED_FACTOR_TRAFFIC.get((n, nb, args.policy)),
                 "kernel": "factor_kernel (persistent data-flow, DFMA tile bodies)",
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz (DFMA; FP64 mma.sync is "
                                "slower on sm_103)"}
