@@ -141,6 +141,37 @@ chol_status chol_trsm_sweep(int uplo_t, int n, int nrhs, const double *dL, int l
                             int ldb, void *dWork, size_t work_bytes, int *dInfo, void *stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Mixed precision (not in the paper): the same tile factorization in FP32, and a solver
+ * that factors A in FP32 and wins the accuracy back by iterative refinement whose residual
+ * r = b - A x and update x += d run in FP64 (classical iterative refinement).
+ */
+typedef enum { CHOL_F64 = 0, CHOL_F32 = 1, CHOL_BF16 = 2 } chol_precision;
+
+/* chol_factor on an FP32 matrix (same task graph, scheduler, options and workspace size). */
+chol_status chol_factor_f32(int n, float *dA, int lda, const chol_opts *opts, void *dWork,
+                            size_t work_bytes, int *dInfo, void *stream);
+
+/* Solve A X = B to a normwise backward error <= tol (Rigal-Gaches, infinity norm, maximised
+ * over the right-hand sides) with a factor in `low_precision` (CHOL_F32; others return
+ * CHOL_ERR_UNSUPPORTED) and at most max_iter refinement steps (the first low-precision
+ * solve counts as one).
+ * dA    n x n FP64, lower triangle read (A is symmetric); not modified.
+ * dB    n x nrhs FP64 (ldb), not modified; dX n x nrhs FP64 (ldx), overwritten by X.
+ * opts  options of the low-precision factorization (tile size, policy, ...), may be NULL.
+ * dWork at least chol_solve_refine_workspace_size(n, nrhs, opts) bytes, 256-B aligned.
+ * dInfo device int: the low-precision factor's info (j > 0: A is not positive definite in
+ *       that precision; X is then left at zero and *dBerr is +inf).
+ * dIters, dBerr device int / double (nullable): steps taken and the final backward error.
+ * All steps run on `stream` with no host synchronisation: every step's kernels return at
+ * once after convergence, so the call is one fixed sequence of launches.
+ */
+size_t chol_solve_refine_workspace_size(int n, int nrhs, const chol_opts *opts);
+chol_status chol_solve_refine(int n, int nrhs, const double *dA, int lda, const double *dB, int ldb,
+                              double *dX, int ldx, int low_precision, double tol, int max_iter,
+                              const chol_opts *opts, void *dWork, size_t work_bytes, int *dInfo,
+                              int *dIters, double *dBerr, void *stream);
+
+/* ---------------------------------------------------------------------------------------
  * Host-buffer convenience: factor and solve from host memory (LAPACK dposv semantics).
  * hA (n x n, lda) is copied to the device, factored, and L is copied back into hA's lower
  * triangle; hB (n x nrhs, ldb) is overwritten by X. dStage is a device buffer of at least

@@ -18,7 +18,8 @@ from . import build as _build
 
 __all__ = [
     "lib", "ChOpts", "POLICIES", "opts", "colmajor", "factor", "solve", "trsm_sweep", "posv",
-    "posv_host", "workspace_size", "solve_workspace_size", "num_workers", "trace",
+    "posv_host", "workspace_size", "solve_workspace_size", "num_workers", "trace", "factor_f32",
+    "solve_refine", "refine_workspace_size",
     "dag_describe", "dag_bottom_levels", "sched_activate", "sched_activate_device",
     "CholeskyError",
 ]
@@ -69,6 +70,9 @@ _SIGNATURES = {
     "chol_solve": (_I, [_I, _I, _P, _I, _P, _I, _P, _SZ, _P, _P]),
     "chol_trsm_sweep": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _SZ, _P, _P]),
     "chol_solve_noalloc": (_I, [_I, _I, _P, _I, _P, _I, _P, _P]),
+    "chol_factor_f32": (_I, [_I, _P, _I, _OPTS, _P, _SZ, _P, _P]),
+    "chol_solve_refine_workspace_size": (_SZ, [_I, _I, _OPTS]),
+    "chol_solve_refine": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _I, _D, _I, _OPTS, _P, _SZ, _P, _P, _P, _P]),
     "chol_posv_host_stage_size": (_SZ, [_I, _I, _OPTS]),
     "chol_posv_host": (_I, [_I, _I, _P, _I, _P, _I, _OPTS, _P, _SZ, _P, _P]),
     "chol_dag_task_count": (_LL, [_I]),
@@ -189,6 +193,53 @@ def factor(A, o=None, work=None, info=None, stream=None, check=False):
         if v != 0:
             raise CholeskyError("chol_factor: info = %d" % v)
     return info, work
+
+
+def factor_f32(A, o=None, work=None, info=None, stream=None, check=False):
+    """FP32 tile Cholesky in place on a column-major float32 CUDA tensor."""
+    o = o or opts()
+    n = A.shape[0]
+    if not (A.is_cuda and A.dtype == torch.float32 and A.dim() == 2 and A.shape[1] == n):
+        raise ValueError("A must be a square float32 CUDA tensor")
+    if n > 0 and A.stride(0) != 1:
+        raise ValueError("A must be column-major (stride(0) == 1); use colmajor()")
+    lda = max(1, A.stride(1) if n > 1 else n)
+    if work is None:
+        work = _workspace(workspace_size(n, o), A.device)
+    if info is None:
+        info = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _check(lib.chol_factor_f32(n, A.data_ptr(), lda, ctypes.byref(o), work.data_ptr(), work.numel(),
+                               info.data_ptr(), _stream(stream)), "chol_factor_f32")
+    if check and int(info.item()) != 0:
+        raise CholeskyError("chol_factor_f32: info = %d" % int(info.item()))
+    return info, work
+
+
+def refine_workspace_size(n, nrhs, o=None):
+    o = o or opts()
+    return int(lib.chol_solve_refine_workspace_size(n, nrhs, ctypes.byref(o)))
+
+
+def solve_refine(A, B, X=None, tol=1e-14, max_iter=30, o=None, work=None, stream=None):
+    """Mixed-precision solve (FP32 factor, FP64 refinement). Returns (X, info, iters, berr)
+    as device tensors (no synchronisation)."""
+    o = o or opts()
+    n = A.shape[0]
+    lda = _check_matrix(A, "A")
+    ldb = _check_matrix(B, "B")
+    nrhs = B.shape[1]
+    if X is None:
+        X = colmajor(torch.empty(n, nrhs, dtype=torch.float64, device=A.device))
+    ldx = _check_matrix(X, "X")
+    if work is None:
+        work = _workspace(refine_workspace_size(n, nrhs, o), A.device)
+    info = torch.zeros(1, dtype=torch.int32, device=A.device)
+    iters = torch.zeros(1, dtype=torch.int32, device=A.device)
+    berr = torch.zeros(1, dtype=torch.float64, device=A.device)
+    _check(lib.chol_solve_refine(n, nrhs, A.data_ptr(), lda, B.data_ptr(), ldb, X.data_ptr(), ldx, 1, tol,
+                                 max_iter, ctypes.byref(o), work.data_ptr(), work.numel(), info.data_ptr(),
+                                 iters.data_ptr(), berr.data_ptr(), _stream(stream)), "chol_solve_refine")
+    return X, info, iters, berr
 
 
 def solve(L, B, work=None, info=None, stream=None):

@@ -14,8 +14,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libchol_gb300.so")
-SOURCES = ["csrc/api.cu", "csrc/factor.cu", "csrc/solve.cu"]
-HEADERS = ["csrc/common.cuh", "csrc/dag.cuh", "csrc/sched.cuh", "csrc/tiles_f64.cuh"]
+SOURCES = ["csrc/api.cu", "csrc/factor.cu", "csrc/solve.cu", "csrc/refine.cu"]
+HEADERS = ["csrc/common.cuh", "csrc/dag.cuh", "csrc/internal.cuh", "csrc/sched.cuh", "csrc/tiles_f32.cuh",
+           "csrc/tiles_f64.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -25,7 +25,9 @@
 #include <mutex>
 #include "common.cuh"
 #include "dag.cuh"
+#include "internal.cuh"
 #include "sched.cuh"
+#include "tiles_f32.cuh"
 #include "tiles_f64.cuh"
 
 namespace chol {
@@ -40,7 +42,7 @@ struct Ctrl {
 };
 
 struct FactorArgs {
-  double *A;
+  void *A;  // double or float, by the kernel instantiation
   int64_t lda;
   int n, nb, T;
   int64_t ntasks;
@@ -62,7 +64,7 @@ struct FactorArgs {
 };
 
 struct Resolved {
-  int nb, T, policy, queue_order, steal, wps, W, max_iter, trace;
+  int prec, nb, T, policy, queue_order, steal, wps, W, max_iter, trace;
   double alpha, eps;
   int64_t cost[4];
   int64_t timeout_ns;
@@ -82,8 +84,9 @@ static size_t sched_smem_bytes(int T, int W) {
   return b;
 }
 
-static size_t factor_smem_bytes(int T, int W) {
-  return std::max((size_t)TILE_SMEM_BYTES, sched_smem_bytes(T, W));
+static size_t factor_smem_bytes(int prec, int T, int W) {
+  const size_t tiles = prec == PREC_F64 ? (size_t)TILE_SMEM_BYTES : (size_t)f32::TILE_SMEM_BYTES;
+  return std::max(tiles, sched_smem_bytes(T, W));
 }
 
 static Layout make_layout(int n, const Resolved &r, int W) {
@@ -131,8 +134,9 @@ __device__ __forceinline__ uint32_t prio_key(int64_t bl) {
 __device__ __forceinline__ int tile_dim(const FactorArgs &a, int t) {
   return min(a.nb, a.n - t * a.nb);
 }
-__device__ __forceinline__ double *tile_ptr(const FactorArgs &a, int i, int j) {
-  return a.A + (int64_t)j * a.nb * a.lda + (int64_t)i * a.nb;
+template <class T>
+__device__ __forceinline__ T *tile_ptr(const FactorArgs &a, int i, int j) {
+  return static_cast<T *>(a.A) + (int64_t)j * a.nb * a.lda + (int64_t)i * a.nb;
 }
 
 // Push by a single thread onto queue w, or onto the next queue with a free slot if w is
@@ -342,31 +346,62 @@ __device__ void complete(const FactorArgs &a, int wid, const TaskDesc &d, unsign
   if (lane == 0) atomicAdd(&a.ctrl->done, 1);
 }
 
+// Tile bodies per precision of the factored matrix.
+struct TilesF64 {
+  using T = double;
+  static constexpr int SMEM = TILE_SMEM_BYTES;
+  static constexpr int MIN_BLOCKS = 2;  // two workers per SM share the FP64 pipe
+  __device__ static int potrf(T *G, int64_t ld, int nk, T *s) { return potrf_tile(G, ld, nk, s); }
+  __device__ static void trsm(T *B, int64_t ldb, const T *L, int64_t ldl, int mb, int nk, T *s) {
+    trsm_tile(B, ldb, L, ldl, mb, nk, s);
+  }
+  __device__ static void update(T *C, int64_t ldc, const T *A, int64_t lda, const T *B, int64_t ldb, int M,
+                                int N, int K, bool lower, T *s) {
+    update_nt(C, ldc, A, lda, B, ldb, M, N, K, lower, s);
+  }
+};
+struct TilesF32 {
+  using T = float;
+  static constexpr int SMEM = f32::TILE_SMEM_BYTES;
+  static constexpr int MIN_BLOCKS = 1;  // the 8x8 register tiles need more than 128 registers
+  __device__ static int potrf(T *G, int64_t ld, int nk, T *s) { return f32::potrf_tile(G, ld, nk, s); }
+  __device__ static void trsm(T *B, int64_t ldb, const T *L, int64_t ldl, int mb, int nk, T *s) {
+    f32::trsm_tile(B, ldb, L, ldl, mb, nk, s);
+  }
+  __device__ static void update(T *C, int64_t ldc, const T *A, int64_t lda, const T *B, int64_t ldb, int M,
+                                int N, int K, bool lower, T *s) {
+    f32::update_nt(C, ldc, A, lda, B, ldb, M, N, K, lower, s);
+  }
+};
+
 // Run one tile task with the whole block. Returns 0 or a 1-based failing global column.
-__device__ int run_task(const FactorArgs &a, const TaskDesc &d, double *smem) {
+template <class P>
+__device__ int run_task(const FactorArgs &a, const TaskDesc &d, typename P::T *smem) {
+  using T = typename P::T;
   switch (d.kind) {
     case K_POTRF: {
-      const int f = potrf_tile(tile_ptr(a, d.k, d.k), a.lda, tile_dim(a, d.k), smem);
+      const int f = P::potrf(tile_ptr<T>(a, d.k, d.k), a.lda, tile_dim(a, d.k), smem);
       return f ? d.k * a.nb + f : 0;
     }
     case K_TRSM:
-      trsm_tile(tile_ptr(a, d.i, d.k), a.lda, tile_ptr(a, d.k, d.k), a.lda, tile_dim(a, d.i),
-                tile_dim(a, d.k), smem);
+      P::trsm(tile_ptr<T>(a, d.i, d.k), a.lda, tile_ptr<T>(a, d.k, d.k), a.lda, tile_dim(a, d.i),
+              tile_dim(a, d.k), smem);
       return 0;
     case K_SYRK:
-      update_nt(tile_ptr(a, d.i, d.i), a.lda, tile_ptr(a, d.i, d.k), a.lda, tile_ptr(a, d.i, d.k),
+      P::update(tile_ptr<T>(a, d.i, d.i), a.lda, tile_ptr<T>(a, d.i, d.k), a.lda, tile_ptr<T>(a, d.i, d.k),
                 a.lda, tile_dim(a, d.i), tile_dim(a, d.i), tile_dim(a, d.k), true, smem);
       return 0;
     default:
-      update_nt(tile_ptr(a, d.i, d.j), a.lda, tile_ptr(a, d.i, d.k), a.lda, tile_ptr(a, d.j, d.k),
+      P::update(tile_ptr<T>(a, d.i, d.j), a.lda, tile_ptr<T>(a, d.i, d.k), a.lda, tile_ptr<T>(a, d.j, d.k),
                 a.lda, tile_dim(a, d.i), tile_dim(a, d.j), tile_dim(a, d.k), false, smem);
       return 0;
   }
 }
 
-__global__ void __launch_bounds__(NT, 2) factor_kernel(const __grid_constant__ FactorArgs a) {
+template <class P>
+__global__ void __launch_bounds__(NT, P::MIN_BLOCKS) factor_kernel(const __grid_constant__ FactorArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double *smem = reinterpret_cast<double *>(smem_raw);
+  typename P::T *smem = reinterpret_cast<typename P::T *>(smem_raw);
   __shared__ long long s_id;
   __shared__ int s_from;
   __shared__ int s_nready;
@@ -397,7 +432,7 @@ __global__ void __launch_bounds__(NT, 2) factor_kernel(const __grid_constant__ F
     const TaskDesc d = task_desc(a.T, id);
     unsigned long long t0 = 0;
     if (a.trace && threadIdx.x == 0) t0 = globaltimer_ns();
-    const int fail = run_task(a, d, smem);
+    const int fail = run_task<P>(a, d, smem);
     __threadfence();
     __syncthreads();
     if (warp == 0) {
@@ -458,10 +493,11 @@ __global__ void copy_info_kernel(const Ctrl *ctrl, int *dInfo) {
 
 static std::once_flag g_attr_once;
 
-static bool resolve(int n, const chol_opts *opts, Resolved &r) {
+static bool resolve(int n, const chol_opts *opts, Resolved &r, int prec = PREC_F64) {
   chol_opts o;
   chol_opts_default(&o);
   if (opts) o = *opts;
+  r.prec = prec;
   r.nb = o.nb > 0 ? o.nb : 256;
   if (r.nb < 16 || r.nb > 1024) return false;
   r.T = n > 0 ? (n + r.nb - 1) / r.nb : 1;
@@ -479,7 +515,9 @@ static bool resolve(int n, const chol_opts *opts, Resolved &r) {
   r.max_iter = o.dada_max_iter > 0 ? o.dada_max_iter : 16;
   r.eps = o.dada_eps > 0.0 ? o.dada_eps : 0.01;
   const double nb = (double)r.nb;
-  const double rate = 7.5 / (double)r.wps;  // GFLOP/s per worker = flop per ns
+  // predicted rate per worker in GFLOP/s (= flop per ns): FP64 DFMA ~7.5 per SM, FP32 FFMA
+  // tile bodies ~300 per SM
+  const double rate = (prec == PREC_F64 ? 7.5 : 300.0) / (double)r.wps;
   const double flops[4] = {nb * nb * nb / 3.0, nb * nb * nb, nb * nb * nb, 2.0 * nb * nb * nb};
   for (int k = 0; k < 4; ++k) {
     if (o.cost_ns[k] < 0) return false;
@@ -496,11 +534,13 @@ static bool resolve(int n, const chol_opts *opts, Resolved &r) {
 static int launch_workers(const Resolved &r, const DeviceInfo &di) {
   if (di.sms <= 0) return 1024;
   std::call_once(g_attr_once, [] {
-    cudaFuncSetAttribute(factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(factor_kernel<TilesF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(factor_kernel<TilesF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
   });
-  const size_t smem = factor_smem_bytes(r.T, 2 * di.sms);
+  const size_t smem = factor_smem_bytes(r.prec, r.T, 2 * di.sms);
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, factor_kernel, NT, smem) != cudaSuccess)
+  const void *fn = r.prec == PREC_F64 ? (const void *)factor_kernel<TilesF64> : (const void *)factor_kernel<TilesF32>;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, smem) != cudaSuccess)
     per_sm = 1;
   per_sm = std::max(1, std::min(per_sm, r.wps));
   int W = di.sms * per_sm;
@@ -513,11 +553,16 @@ static int launch_workers(const Resolved &r, const DeviceInfo &di) {
 using namespace chol;
 
 extern "C" size_t chol_factor_workspace_size(int n, const chol_opts *opts) {
-  Resolved r;
-  if (n < 0 || !resolve(n, opts, r)) return 0;
-  const DeviceInfo di = current_device_info();
-  const int W = launch_workers(r, di);
-  return make_layout(n, r, W).total;
+  // the same workspace serves both precisions of the factor
+  size_t best = 0;
+  for (int prec = PREC_F64; prec <= PREC_F32; ++prec) {
+    Resolved r;
+    if (n < 0 || !resolve(n, opts, r, prec)) return 0;
+    const DeviceInfo di = current_device_info();
+    const int W = launch_workers(r, di);
+    best = std::max(best, make_layout(n, r, W).total);
+  }
+  return best;
 }
 
 extern "C" long long chol_factor_trace_offset(int n, const chol_opts *opts) {
@@ -536,10 +581,12 @@ extern "C" int chol_num_workers(const chol_opts *opts) {
   return launch_workers(r, di);
 }
 
-extern "C" chol_status chol_factor(int n, double *dA, int lda, const chol_opts *opts, void *dWork,
-                                   size_t work_bytes, int *dInfo, void *stream) {
+namespace chol {
+
+chol_status factor_impl(int prec, int n, void *dA, int lda, const chol_opts *opts, void *dWork,
+                        size_t work_bytes, int *dInfo, void *stream) {
   Resolved r;
-  if (n < 0 || !dInfo || !resolve(n, opts, r)) return CHOL_ERR_INVALID_ARG;
+  if (n < 0 || !dInfo || !resolve(n, opts, r, prec)) return CHOL_ERR_INVALID_ARG;
   if (lda < std::max(1, n) || (n > 0 && !dA)) return CHOL_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   if (n == 0) {
@@ -586,10 +633,23 @@ extern "C" chol_status chol_factor(int n, double *dA, int lda, const chol_opts *
     bottom_level_kernel<<<1, 1024, 0, s>>>(r.T, r.cost[0], r.cost[1], r.cost[2], r.cost[3], a.bl);
     CHOL_CUDA_TRY(cudaGetLastError());
   }
-  const size_t smem = factor_smem_bytes(r.T, W);
+  const size_t smem = factor_smem_bytes(prec, r.T, W);
   void *args[] = {(void *)&a};
-  CHOL_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)factor_kernel, dim3(W), dim3(NT), args, smem, s));
+  const void *fn = prec == PREC_F64 ? (const void *)factor_kernel<TilesF64> : (const void *)factor_kernel<TilesF32>;
+  CHOL_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(W), dim3(NT), args, smem, s));
   copy_info_kernel<<<1, 32, 0, s>>>(a.ctrl, dInfo);
   CHOL_CUDA_TRY(cudaGetLastError());
   return CHOL_OK;
+}
+
+}  // namespace chol
+
+extern "C" chol_status chol_factor(int n, double *dA, int lda, const chol_opts *opts, void *dWork,
+                                   size_t work_bytes, int *dInfo, void *stream) {
+  return factor_impl(PREC_F64, n, dA, lda, opts, dWork, work_bytes, dInfo, stream);
+}
+
+extern "C" chol_status chol_factor_f32(int n, float *dA, int lda, const chol_opts *opts, void *dWork,
+                                       size_t work_bytes, int *dInfo, void *stream) {
+  return factor_impl(PREC_F32, n, dA, lda, opts, dWork, work_bytes, dInfo, stream);
 }

@@ -8,11 +8,13 @@
 // were claimed earlier and are held by running blocks: the sweep always progresses, with
 // or without co-residency. Waits are bounded (timeout -> CHOL_INFO_TIMEOUT in *dInfo).
 //
-// Both sweeps are FP64 FMA bound on sm_103 (n^2 nrhs fused multiply-adds against n^2/2 * 8
-// bytes of L): the inner products run from shared memory, four-way unrolled in k.
+// The kernel is instantiated for FP64 (chol_solve) and FP32 (the low-precision solves of
+// the mixed-precision refinement). In FP64 both sweeps are bound by the FP64 pipe (n^2 nrhs
+// fused multiply-adds against n^2/2 * 8 bytes of L).
 #include <algorithm>
 #include <mutex>
 #include "common.cuh"
+#include "internal.cuh"
 
 namespace chol {
 
@@ -30,9 +32,9 @@ struct SolveCtrl {
 };
 
 struct SolveArgs {
-  const double *L;
+  const void *L;  // T, by the kernel instantiation
   int64_t lda;
-  double *B;
+  void *B;
   int64_t ldb;
   int n, nrhs, nrb, ngroups;
   int64_t nitems;
@@ -40,24 +42,30 @@ struct SolveArgs {
   int64_t timeout_ns;
   SolveCtrl *ctrl;
   const int *prev_abort;  // abort flag of the sweep that produced B (nullable)
+  const int *skip;        // when set (nonzero) on entry, the launch does nothing (nullable)
   int *flags;
 };
 
 // b / d from r = RN(1/d) with one Markstein correction step (see the tile bodies): the
 // correctly rounded quotient in three dependent operations.
-__device__ __forceinline__ double squot(double b, double d, double r) {
-  const double x = b * r;
-  const double e = fma(-x, d, b);
+template <class T>
+__device__ __forceinline__ T squot(T b, T d, T r) {
+  const T x = b * r;
+  const T e = fma(-x, d, b);
   return fma(e, r, x);
 }
 
+template <class T>
 __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ SolveArgs a) {
-  __shared__ double Ls[SB * SLD];
-  __shared__ double Ys[SB * SG];
-  __shared__ double Red[8 * SB * 8];  // partial sums of the k-split path [slice][row][col]
-  __shared__ double Rs[SB];           // reciprocals of the diagonal block
+  __shared__ T Ls[SB * SLD];
+  __shared__ T Ys[SB * SG];
+  __shared__ T Red[8 * SB * 8];  // partial sums of the k-split path [slice][row][col]
+  __shared__ T Rs[SB];           // reciprocals of the diagonal block
   __shared__ long long s_item;
   __shared__ int s_abort;
+  const T *L = static_cast<const T *>(a.L);
+  T *B = static_cast<T *>(a.B);
+  if (a.skip && ld_volatile(a.skip)) return;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int rr = lane, cs = warp;  // accumulation: row rr of the block, slice cs
@@ -77,11 +85,11 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
     // With 8 or more columns, slice cs owns columns cs + 8q over all k. With fewer, every
     // slice owns all columns and the k range is split: slice cs takes k = cs + 8t.
     const bool ksplit = cols < 8;
-    double acc[8];
+    T acc[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int c = cs + 8 * q;
-      acc[q] = (!ksplit && rr < rows && c < cols) ? __ldcg(a.B + (int64_t)(c0 + c) * a.ldb + r0 + rr) : 0.0;
+      acc[q] = (!ksplit && rr < rows && c < cols) ? __ldcg(B + (int64_t)(c0 + c) * a.ldb + r0 + rr) : T(0);
     }
     // blocks are consumed in the order the sweep produces them (forward: 0, 1, ...;
     // backward: nrb-1, nrb-2, ...), so an item only waits on the newest block it needs
@@ -93,9 +101,9 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
       for (int e = tid; e < SB * SB; e += SNT) {
         const int i = e & 31, j = e >> 5;
         if (!a.trans) {  // element (r0+i, m0+j)
-          Ls[i * SLD + j] = (i < rows && j < mrows) ? __ldcg(a.L + (int64_t)(m0 + j) * a.lda + r0 + i) : 0.0;
+          Ls[i * SLD + j] = (i < rows && j < mrows) ? __ldcg(L + (int64_t)(m0 + j) * a.lda + r0 + i) : T(0);
         } else {         // element (m0+i, r0+j) stored at [j][i]
-          Ls[j * SLD + i] = (i < mrows && j < rows) ? __ldcg(a.L + (int64_t)(r0 + j) * a.lda + m0 + i) : 0.0;
+          Ls[j * SLD + i] = (i < mrows && j < rows) ? __ldcg(L + (int64_t)(r0 + j) * a.lda + m0 + i) : T(0);
         }
       }
       // wait until block m of this group is solved
@@ -120,13 +128,13 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
       if (s_abort) break;
       for (int e = tid; e < SB * SG; e += SNT) {
         const int k = e & 31, c = e >> 5;
-        Ys[k * SG + c] = (k < mrows && c < cols) ? __ldcg(a.B + (int64_t)(c0 + c) * a.ldb + m0 + k) : 0.0;
+        Ys[k * SG + c] = (k < mrows && c < cols) ? __ldcg(B + (int64_t)(c0 + c) * a.ldb + m0 + k) : T(0);
       }
       __syncthreads();
       if (!ksplit) {
 #pragma unroll 4
         for (int k = 0; k < SB; ++k) {
-          const double l = Ls[rr * SLD + k];
+          const T l = Ls[rr * SLD + k];
 #pragma unroll
           for (int q = 0; q < 8; ++q)
             if (cs + 8 * q < cols) acc[q] = fma(-l, Ys[k * SG + cs + 8 * q], acc[q]);
@@ -135,7 +143,7 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
           const int k = cs + 8 * t;
-          const double l = Ls[rr * SLD + k];
+          const T l = Ls[rr * SLD + k];
 #pragma unroll
           for (int q = 0; q < 7; ++q)
             if (q < cols) acc[q] = fma(-l, Ys[k * SG + q], acc[q]);
@@ -151,10 +159,10 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
       const int i = e & 31, j = e >> 5;
       // rows past the end of the matrix get an identity block, so the substitution below
       // runs over a fixed 32 rows with register-resident data
-      Ls[i * SLD + j] = (i < rows && j < rows && i >= j) ? __ldcg(a.L + (int64_t)(r0 + j) * a.lda + r0 + i)
-                                                          : (i == j ? 1.0 : 0.0);
+      Ls[i * SLD + j] = (i < rows && j < rows && i >= j) ? __ldcg(L + (int64_t)(r0 + j) * a.lda + r0 + i)
+                                                          : (i == j ? T(1) : T(0));
     }
-    if (tid < SB) Rs[tid] = tid < rows ? 1.0 / __ldcg(a.L + (int64_t)(r0 + tid) * a.lda + r0 + tid) : 1.0;
+    if (tid < SB) Rs[tid] = tid < rows ? T(1) / __ldcg(L + (int64_t)(r0 + tid) * a.lda + r0 + tid) : T(1);
     if (!ksplit) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) Ys[rr * SG + cs + 8 * q] = acc[q];
@@ -166,7 +174,7 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
     if (ksplit && tid < SB * 8) {
       const int i = tid & 31, q = tid >> 5;
       if (q < cols) {
-        double t = (i < rows) ? __ldcg(a.B + (int64_t)(c0 + q) * a.ldb + r0 + i) : 0.0;
+        T t = (i < rows) ? __ldcg(B + (int64_t)(c0 + q) * a.ldb + r0 + i) : T(0);
         for (int s = 0; s < 8; ++s) t += Red[(s * SB + i) * 8 + q];
         Ys[i * SG + q] = t;
       }
@@ -174,7 +182,7 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
     __syncthreads();
     if (tid < cols) {
       const int c = tid;
-      double x[SB];
+      T x[SB];
 #pragma unroll
       for (int i = 0; i < SB; ++i) x[i] = Ys[i * SG + c];
       // right-looking: once x_k is known every later row is updated at once, so each x_k
@@ -196,7 +204,7 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
       }
 #pragma unroll
       for (int i = 0; i < SB; ++i)
-        if (i < rows) __stcg(a.B + (int64_t)(c0 + c) * a.ldb + r0 + i, x[i]);
+        if (i < rows) __stcg(B + (int64_t)(c0 + c) * a.ldb + r0 + i, x[i]);
     }
     __threadfence();
     __syncthreads();
@@ -216,8 +224,11 @@ static size_t flags_bytes(int n, int nrhs) {
 }
 static size_t solve_ws(int n, int nrhs) { return 512 + 2 * flags_bytes(n, nrhs); }
 
-static chol_status launch_sweep(int trans, int slot, int n, int nrhs, const double *dL, int lda,
-                                double *dB, int ldb, void *dWork, cudaStream_t s) {
+size_t solve_workspace_bytes(int n, int nrhs) { return solve_ws(n, nrhs); }
+
+template <class T>
+static chol_status launch_sweep(int trans, int slot, int n, int nrhs, const T *dL, int lda, T *dB, int ldb,
+                                void *dWork, const int *skip, cudaStream_t s) {
   SolveArgs a;
   a.L = dL; a.lda = lda; a.B = dB; a.ldb = ldb; a.n = n; a.nrhs = nrhs;
   a.nrb = (n + SB - 1) / SB;
@@ -225,6 +236,7 @@ static chol_status launch_sweep(int trans, int slot, int n, int nrhs, const doub
   a.nitems = (int64_t)a.nrb * a.ngroups;
   a.trans = trans;
   a.timeout_ns = 10000000000ll;
+  a.skip = skip;
   unsigned char *ws = static_cast<unsigned char *>(dWork);
   a.ctrl = reinterpret_cast<SolveCtrl *>(ws + 256 * slot);
   a.prev_abort = slot == 1 ? &reinterpret_cast<SolveCtrl *>(ws)->abort : nullptr;
@@ -238,10 +250,11 @@ static chol_status launch_sweep(int trans, int slot, int n, int nrhs, const doub
   const DeviceInfo di = current_device_info();
   static std::once_flag once;
   std::call_once(once, [] {
-    cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_EXCL_SMEM);
+    cudaFuncSetAttribute(solve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_EXCL_SMEM);
+    cudaFuncSetAttribute(solve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_EXCL_SMEM);
   });
   const int64_t grid = std::min<int64_t>(a.nitems, (int64_t)std::max(1, di.sms));
-  solve_kernel<<<(int)grid, SNT, SOLVE_EXCL_SMEM, s>>>(a);
+  solve_kernel<T><<<(int)grid, SNT, SOLVE_EXCL_SMEM, s>>>(a);
   CHOL_CUDA_TRY(cudaGetLastError());
   return CHOL_OK;
 }
@@ -256,14 +269,23 @@ static chol_status write_info(void *dWork, int slots, int *dInfo, cudaStream_t s
   return CHOL_OK;
 }
 
-static chol_status check_args(int n, int nrhs, const double *dL, int lda, double *dB, int ldb,
-                              void *dWork, size_t work_bytes) {
+static chol_status check_args(int n, int nrhs, const void *dL, int lda, void *dB, int ldb, void *dWork,
+                              size_t work_bytes) {
   if (n < 0 || nrhs < 0) return CHOL_ERR_INVALID_ARG;
   if (lda < std::max(1, n) || ldb < std::max(1, n)) return CHOL_ERR_INVALID_ARG;
   if (n > 0 && nrhs > 0 && (!dL || !dB)) return CHOL_ERR_INVALID_ARG;
   if (n > 0 && nrhs > 0 && (!dWork || work_bytes < solve_ws(n, nrhs) || ((uintptr_t)dWork & 255)))
     return CHOL_ERR_WORKSPACE;
   return CHOL_OK;
+}
+
+// FP32 forward + back substitution in place on dB (n x nrhs), skipped when *skip != 0.
+chol_status solve_f32(int n, int nrhs, const float *dL, int lda, float *dB, int ldb, void *dWork,
+                      const int *skip, cudaStream_t s) {
+  if (n == 0 || nrhs == 0) return CHOL_OK;
+  chol_status r = launch_sweep<float>(0, 0, n, nrhs, dL, lda, dB, ldb, dWork, skip, s);
+  if (r != CHOL_OK) return r;
+  return launch_sweep<float>(1, 1, n, nrhs, dL, lda, dB, ldb, dWork, skip, s);
 }
 
 }  // namespace chol
@@ -286,7 +308,7 @@ extern "C" chol_status chol_trsm_sweep(int uplo_t, int n, int nrhs, const double
     if (dInfo) CHOL_CUDA_TRY(cudaMemsetAsync(dInfo, 0, sizeof(int), s));
     return CHOL_OK;
   }
-  const chol_status r = launch_sweep(uplo_t, 0, n, nrhs, dL, lda, dB, ldb, dWork, s);
+  const chol_status r = launch_sweep<double>(uplo_t, 0, n, nrhs, dL, lda, dB, ldb, dWork, nullptr, s);
   if (r != CHOL_OK) return r;
   return write_info(dWork, 1, dInfo, s);
 }
@@ -300,10 +322,10 @@ extern "C" chol_status chol_solve(int n, int nrhs, const double *dL, int lda, do
     if (dInfo) CHOL_CUDA_TRY(cudaMemsetAsync(dInfo, 0, sizeof(int), s));
     return CHOL_OK;
   }
-  chol_status r = launch_sweep(0, 0, n, nrhs, dL, lda, dB, ldb, dWork, s);
+  chol_status r = launch_sweep<double>(0, 0, n, nrhs, dL, lda, dB, ldb, dWork, nullptr, s);
   if (r != CHOL_OK) return r;
   // the backward sweep skips its work if the forward one aborted
-  r = launch_sweep(1, 1, n, nrhs, dL, lda, dB, ldb, dWork, s);
+  r = launch_sweep<double>(1, 1, n, nrhs, dL, lda, dB, ldb, dWork, nullptr, s);
   if (r != CHOL_OK) return r;
   return write_info(dWork, 2, dInfo, s);
 }
