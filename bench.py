@@ -50,11 +50,16 @@ def parse():
     p.add_argument("--policy", default="heft")
     p.add_argument("--alpha", type=float, default=0.5)
     p.add_argument("--workers-per-sm", type=int, default=2)
+    p.add_argument("--cp", action="store_true", help="communication prediction in the placement")
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-n", type=int, default=10240)
     p.add_argument("--seed", type=int, default=1)
+    p.add_argument("--no-mixed", action="store_true")
+    p.add_argument("--mixed-n", type=int, default=16384)
+    p.add_argument("--mixed-nrhs", type=int, default=16)
+    p.add_argument("--mixed-steps", type=int, default=2)
     return p.parse_args()
 
 
@@ -172,9 +177,9 @@ def workload_config(args):
     return {"workload": "FP64 tiled Cholesky factor + solve, n=%d, tile %d, %d RHS, %s ready queues%s; "
                         "A = sym(G G^T)/n + I, G ~ N(0,1)" % (
                             args.n, args.nb, args.nrhs, args.policy.upper(),
-                            " alpha=%g" % args.alpha if args.policy == "dada" else ""),
+                            (" alpha=%g" % args.alpha if args.policy == "dada" else "") + (" +CP" if args.cp else "")),
             "n": args.n, "nb": args.nb, "nrhs": args.nrhs, "policy": args.policy, "alpha": args.alpha,
-            "workers_per_sm": args.workers_per_sm,
+            "workers_per_sm": args.workers_per_sm, "communication_prediction": bool(args.cp),
             "l2": "inputs larger than L2 (A is %.1f GB)" % (args.n * args.n * 8 / 1e9),
             "parallelism": "replicas x%d" % args.gpus}
 
@@ -203,7 +208,8 @@ def main():
             dist.barrier()
 
     n, nb, nrhs = args.n, args.nb, args.nrhs
-    o = chol.opts(nb=nb, policy=args.policy, alpha=args.alpha, workers_per_sm=args.workers_per_sm)
+    o = chol.opts(nb=nb, policy=args.policy, alpha=args.alpha, workers_per_sm=args.workers_per_sm,
+                  use_cp=args.cp)
     A0 = chol.colmajor(synth.gram_spd(n, seed=args.seed + rank, device=dev))
     B0 = chol.colmajor(synth.rhs(n, nrhs, seed=args.seed + 1000 + rank, device=dev))
     A = torch.empty_like(A0)
@@ -273,6 +279,9 @@ def main():
     barrier()
 
     del A, B, work, R
+    mixed = None
+    if not args.no_mixed and rank == 0:
+        mixed = run_mixed(args, chol, dev)
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         cpu = cpu_baseline(args)
@@ -285,7 +294,7 @@ def main():
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args),
             "factor_ms": round(fac_avg, 2), "solve_backward_error": berr,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "mixed_precision": mixed,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
                        "reasons": clk.get("reasons"), "samples": clk.get("samples"),
@@ -294,6 +303,68 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def _backward_error(A, X, B):
+    R = B - A @ X
+    return float((R.abs().amax(0) / (A.abs().sum(1).amax() * X.abs().amax(0) + B.abs().amax(0))).amax())
+
+
+def run_mixed(args, chol, dev):
+    """The mixed-precision configuration: A = Q diag(lambda) Q^T with kappa = 1e6 (32
+    Householder reflectors), 16 RHS. FP64 factor + solve against FP32 factor + FP64
+    iterative refinement to the same backward error (1e-14); both timed with CUDA events
+    over --mixed-steps steps after one warm-up step each."""
+    import torch
+    import synth
+    n, nrhs = args.mixed_n, args.mixed_nrhs
+    A = chol.colmajor(synth.householder_spd(n, seed=args.seed, cond=1e6, device=dev))
+    B = chol.colmajor(synth.rhs(n, nrhs, seed=args.seed + 7, device=dev))
+    o = chol.opts(nb=256)
+    W = torch.empty_like(A)
+    Bw = torch.empty_like(B)
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    work = torch.empty(chol.workspace_size(n, o), dtype=torch.uint8, device=dev)
+    sw = torch.empty(chol.solve_workspace_size(n, nrhs), dtype=torch.uint8, device=dev)
+    rwork = torch.empty(chol.refine_workspace_size(n, nrhs, o), dtype=torch.uint8, device=dev)
+    X = chol.colmajor(torch.empty(n, nrhs, dtype=torch.float64, device=dev))
+    stream = torch.cuda.current_stream(dev)
+
+    def fp64_step():
+        W.copy_(A)
+        Bw.copy_(B)
+        chol.factor(W, o, work=work, info=info, stream=stream)
+        chol.solve(W, Bw, work=sw, info=info, stream=stream)
+
+    def mixed_step():
+        return chol.solve_refine(A, B, X=X, tol=1e-14, max_iter=30, o=o, work=rwork, stream=stream)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = None
+        for _ in range(args.mixed_steps):
+            out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.mixed_steps, out
+
+    t64, _ = timed(fp64_step)
+    e64 = _backward_error(A, Bw, B)
+    tmx, out = timed(mixed_step)
+    _, minfo, iters, berr = out
+    emx = _backward_error(A, X, B)
+    rel = float(torch.linalg.norm(X - Bw) / torch.linalg.norm(Bw))
+    return {"workload": "n=%d, %d RHS, A = Q diag(lambda) Q^T, lambda geometric 1..1e6 (32 Householder "
+                        "reflectors), tile 256, HEFT" % (n, nrhs),
+            "fp64_ms": round(t64, 2), "mixed_ms": round(tmx, 2), "speedup": round(t64 / tmx, 2),
+            "low_precision": "f32 (FFMA) factor, FP64 residual and update",
+            "target_backward_error": 1e-14, "fp64_backward_error": e64, "mixed_backward_error": emx,
+            "mixed_reported_backward_error": float(berr.item()), "iterations": int(iters.item()),
+            "info": int(minfo.item()), "x_rel_diff_vs_fp64": rel}
 
 
 def run_e2e(args, chol, A0, B0, o, dev):

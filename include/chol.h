@@ -76,6 +76,10 @@ typedef struct {
   long long hold_task;    /* fault injection for tests of the bounded waits: the task with
                              this id gets one extra dependency, so it never becomes ready
                              and the run ends with CHOL_INFO_TIMEOUT; -1 (default) = none */
+  int use_cp;             /* 1: communication prediction (DADA(alpha)+CP; transfer-aware HEFT):
+                             a task placed on a worker that did not write one of its input
+                             tiles last pays that tile's bytes / cp_gbs (Section 4.1) */
+  double cp_gbs;          /* bandwidth per worker for that prediction, GB/s; 0 = 40 */
 } chol_opts;
 
 void chol_opts_default(chol_opts *opts);
@@ -209,12 +213,16 @@ chol_status chol_dag_bottom_levels(int T, const long long *cost_ns, long long *b
  * Algorithm 2 for CHOL_POLICY_DADA). Ready list of m tasks: task ids tid[m], processing
  * times p[m] (ns), priorities prio[m] (bottom levels), affinity worker aff[m] (-1: none)
  * and affinity score score[m] (bytes of the tile the task writes held by that worker).
+ * With use_cp, comm[m] is the predicted cost of one input tile the chosen worker did not
+ * write last, own3[3m] the workers that last wrote the task's input tiles (-1: none) and
+ * nin[m] the number of input tiles; these may be NULL when use_cp = 0.
  * load[W]: each worker's predicted remaining busy time (ns). Writes the push order
  * out_tid[m] and the chosen worker out_worker[m]; *out_iters gets the number of
  * bisection steps (0 for HEFT). Host pointers. Ties go to the lowest worker index. */
 chol_status chol_sched_activate(int policy, double alpha, int max_iter, double eps, int m,
                                 const int *tid, const long long *p, const long long *prio,
-                                const int *aff, const long long *score, int W,
+                                const int *aff, const long long *score, int use_cp,
+                                const long long *comm, const int *own3, const int *nin, int W,
                                 const long long *load, int *out_tid, int *out_worker,
                                 int *out_iters);
 /* The same decision computed by one warp on the device (device pointers, all sizes as
@@ -222,9 +230,10 @@ chol_status chol_sched_activate(int policy, double alpha, int max_iter, double e
 chol_status chol_sched_activate_device(int policy, double alpha, int max_iter, double eps, int m,
                                        const int *dtid, const long long *dp,
                                        const long long *dprio, const int *daff,
-                                       const long long *dscore, int W, const long long *dload,
-                                       int *dout_tid, int *dout_worker, int *dout_iters,
-                                       void *stream);
+                                       const long long *dscore, int use_cp,
+                                       const long long *dcomm, const int *down3, const int *dnin,
+                                       int W, const long long *dload, int *dout_tid,
+                                       int *dout_worker, int *dout_iters, void *stream);
 
 /* Library version string and the number of workers chol_factor would launch on the
  * current device for these options (0 if no usable device). */

@@ -88,3 +88,76 @@ def dada(LR, load, alpha, eps_frac=0.01, max_iter=16):
         it += 1
     order = sorted(LR, key=lambda t: (-t["prio"], t["tid"]))
     return [(t["tid"], best[t["tid"]]) for t in order], it
+
+
+# ----------------------------------------------------------------------------------------
+# Communication prediction (DADA(alpha)+CP, Section 4.1 "Methodology"; HEFT always counts
+# transfers in its earliest finish time). On one GPU a "transfer" is the cost of bringing a
+# task's input tiles to a worker that did not last write them: each task lists the workers
+# owning its input tiles (own, up to three) and a per-tile cost comm (ns); on worker w the
+# task then costs p + comm * (number of its input tiles not owned by w).
+
+def _cost_on(t, w):
+    own = [o for o in t.get("own", []) if o >= 0]
+    nin = t.get("nin", 0)
+    return t["p"] + t.get("comm", 0) * (nin - sum(1 for o in own if o == w))
+
+
+def _eft(t, load):
+    best_w, best_f = -1, None
+    for w, l in enumerate(load):
+        f = l + _cost_on(t, w)
+        if best_f is None or f < best_f:
+            best_w, best_f = w, f
+    return best_w, best_f
+
+
+def heft_cp(LR, load):
+    """Algorithm 1 with transfer time in the finish time."""
+    load = list(load)
+    out = []
+    for t in sorted(LR, key=lambda t: (-t["prio"], t["tid"])):
+        w, f = _eft(t, load)
+        load[w] = f
+        out.append((t["tid"], w))
+    return out
+
+
+def _dada_cp_trial(LR, load0, alpha, lam):
+    load = list(load0)
+    placed = {}
+    for t in sorted([t for t in LR if t["aff"] >= 0], key=lambda t: (-t["score"], -t["prio"], t["tid"])):
+        w = t["aff"]
+        if float(load[w]) < alpha * float(lam):
+            placed[t["tid"]] = w
+            load[w] += _cost_on(t, w)
+    rest = [t for t in LR if t["tid"] not in placed]
+    for t in sorted(rest, key=lambda t: (-t["p"], -t["prio"], t["tid"])):
+        w, f = _eft(t, load)
+        placed[t["tid"]] = w
+        load[w] = f
+    return placed, float(max(load)) <= (2.0 + alpha) * float(lam)
+
+
+def dada_cp(LR, load, alpha, eps_frac=0.01, max_iter=16):
+    """Algorithm 2 with communication prediction: task costs depend on the worker as above;
+    upper = sum_i (p_i + comm_i * nin_i) + max_w load_w."""
+    if not LR:
+        return [], 0
+    lower = 0
+    upper = sum(t["p"] + t.get("comm", 0) * t.get("nin", 0) for t in LR) + max(load)
+    eps = int(upper * eps_frac)
+    best, fits = _dada_cp_trial(LR, load, alpha, upper)
+    assert fits
+    it = 0
+    while upper - lower > eps and it < max_iter:
+        lam = (upper + lower) // 2
+        placed, fits = _dada_cp_trial(LR, load, alpha, lam)
+        if fits:
+            upper = lam
+            best = placed
+        else:
+            lower = lam
+        it += 1
+    order = sorted(LR, key=lambda t: (-t["prio"], t["tid"]))
+    return [(t["tid"], best[t["tid"]]) for t in order], it

@@ -50,6 +50,8 @@ class ChOpts(ctypes.Structure):
         ("timeout_ns", ctypes.c_longlong),
         ("trace", ctypes.c_int),
         ("hold_task", ctypes.c_longlong),
+        ("use_cp", ctypes.c_int),
+        ("cp_gbs", ctypes.c_double),
     ]
 
 
@@ -79,8 +81,9 @@ _SIGNATURES = {
     "chol_dag_edge_count": (_LL, [_I]),
     "chol_dag_describe": (_I, [_I, _P, _P, _P, _P, _P, _P, _P]),
     "chol_dag_bottom_levels": (_I, [_I, _P, _P]),
-    "chol_sched_activate": (_I, [_I, _D, _I, _D, _I, _P, _P, _P, _P, _P, _I, _P, _P, _P, _P]),
-    "chol_sched_activate_device": (_I, [_I, _D, _I, _D, _I, _P, _P, _P, _P, _P, _I, _P, _P, _P, _P, _P]),
+    "chol_sched_activate": (_I, [_I, _D, _I, _D, _I, _P, _P, _P, _P, _P, _I, _P, _P, _P, _I, _P, _P, _P, _P]),
+    "chol_sched_activate_device": (_I, [_I, _D, _I, _D, _I, _P, _P, _P, _P, _P, _I, _P, _P, _P, _I, _P, _P, _P,
+                                        _P, _P]),
     "chol_version": (ctypes.c_char_p, []),
     "chol_num_workers": (_I, [_OPTS]),
 }
@@ -107,7 +110,7 @@ for _name in _SIGNATURES:
 
 def opts(nb=256, policy="heft", alpha=0.5, steal=None, workers_per_sm=2, num_workers=0,
          queue_order=None, dada_max_iter=16, dada_eps=0.01, cost_ns=None, timeout_ns=0, trace=False,
-         hold_task=-1):
+         hold_task=-1, use_cp=False, cp_gbs=40.0):
     o = ChOpts()
     lib.chol_opts_default(ctypes.byref(o))
     o.nb = nb
@@ -125,6 +128,8 @@ def opts(nb=256, policy="heft", alpha=0.5, steal=None, workers_per_sm=2, num_wor
     o.timeout_ns = int(timeout_ns)
     o.trace = int(bool(trace))
     o.hold_task = int(hold_task)
+    o.use_cp = int(bool(use_cp))
+    o.cp_gbs = float(cp_gbs)
     return o
 
 
@@ -338,37 +343,43 @@ def _sched_arrays(tasks):
     prio = np.array([t["prio"] for t in tasks], np.int64)
     aff = np.array([t["aff"] for t in tasks], np.int32)
     score = np.array([t["score"] for t in tasks], np.int64)
-    return m, tid, p, prio, aff, score
+    comm = np.array([t.get("comm", 0) for t in tasks], np.int64)
+    own = np.array([(list(t.get("own", [])) + [-1, -1, -1])[:3] for t in tasks], np.int32).reshape(-1)
+    nin = np.array([t.get("nin", 0) for t in tasks], np.int32)
+    return m, tid, p, prio, aff, score, comm, own, nin
 
 
-def sched_activate(policy, tasks, load, alpha=0.5, max_iter=16, eps=0.01):
+def sched_activate(policy, tasks, load, alpha=0.5, max_iter=16, eps=0.01, use_cp=False):
     """Host placement (same code as the device). Returns ([(tid, worker)], iterations)."""
     import numpy as np
-    m, tid, p, prio, aff, score = _sched_arrays(tasks)
+    m, tid, p, prio, aff, score, comm, own, nin = _sched_arrays(tasks)
     ld = np.asarray(load, np.int64)
     ot = np.zeros(max(m, 1), np.int32)
     ow = np.zeros(max(m, 1), np.int32)
     it = ctypes.c_int(0)
     pol = POLICIES[policy] if isinstance(policy, str) else policy
     _check(lib.chol_sched_activate(pol, alpha, max_iter, eps, m, tid.ctypes.data, p.ctypes.data,
-                                   prio.ctypes.data, aff.ctypes.data, score.ctypes.data, len(ld),
+                                   prio.ctypes.data, aff.ctypes.data, score.ctypes.data, int(bool(use_cp)),
+                                   comm.ctypes.data, own.ctypes.data, nin.ctypes.data, len(ld),
                                    ld.ctypes.data, ot.ctypes.data, ow.ctypes.data, ctypes.byref(it)),
            "chol_sched_activate")
     return [(int(a), int(b)) for a, b in zip(ot[:m], ow[:m])], int(it.value)
 
 
-def sched_activate_device(policy, tasks, load, alpha=0.5, max_iter=16, eps=0.01, device="cuda"):
+def sched_activate_device(policy, tasks, load, alpha=0.5, max_iter=16, eps=0.01, device="cuda", use_cp=False):
     """The same placement computed by one warp on the GPU."""
-    m, tid, p, prio, aff, score = _sched_arrays(tasks)
+    m, tid, p, prio, aff, score, comm, own, nin = _sched_arrays(tasks)
     t = lambda a: torch.from_numpy(a).to(device)
     dt, dp, dpr, da, ds = t(tid), t(p), t(prio), t(aff), t(score)
+    dc, do, dn = t(comm), t(own), t(nin)
     dl = torch.tensor(list(load), dtype=torch.int64, device=device)
     ot = torch.zeros(m, dtype=torch.int32, device=device)
     ow = torch.zeros(m, dtype=torch.int32, device=device)
     it = torch.zeros(1, dtype=torch.int32, device=device)
     pol = POLICIES[policy] if isinstance(policy, str) else policy
     _check(lib.chol_sched_activate_device(pol, alpha, max_iter, eps, m, dt.data_ptr(), dp.data_ptr(),
-                                          dpr.data_ptr(), da.data_ptr(), ds.data_ptr(), len(load),
+                                          dpr.data_ptr(), da.data_ptr(), ds.data_ptr(), int(bool(use_cp)),
+                                          dc.data_ptr(), do.data_ptr(), dn.data_ptr(), len(load),
                                           dl.data_ptr(), ot.data_ptr(), ow.data_ptr(), it.data_ptr(),
                                           _stream(None)), "chol_sched_activate_device")
     torch.cuda.synchronize()

@@ -37,7 +37,8 @@ DeviceInfo current_device_info() {
 // One thread of a warp-wide placement on the device, for chol_sched_activate_device.
 __global__ void sched_activate_kernel(int policy, double alpha, int max_iter, double eps, int m,
                                       const int *tid, const long long *p, const long long *prio,
-                                      const int *aff, const long long *score, int W,
+                                      const int *aff, const long long *score, int use_cp,
+                                      const long long *comm, const int *own3, const int *nin, int W,
                                       const long long *load_in, int *out_tid, int *out_worker,
                                       int *out_iters) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -60,10 +61,13 @@ __global__ void sched_activate_kernel(int policy, double alpha, int max_iter, do
     LR[i].prio = prio[i];
     LR[i].aff = aff[i];
     LR[i].score = score[i];
+    LR[i].comm = use_cp ? comm[i] : 0;
+    LR[i].nin = use_cp ? nin[i] : 0;
+    for (int a = 0; a < 3; ++a) LR[i].own[a] = use_cp ? own3[3 * i + a] : -1;
   }
   for (int w = lane; w < W; w += 32) load[w] = load_in[w];
   __syncwarp();
-  const int it = place<WarpExec>(policy, alpha, max_iter, eps, LR, m, load, W, ps);
+  const int it = place<WarpExec>(policy, alpha, max_iter, eps, LR, m, load, W, ps, use_cp != 0);
   __syncwarp();
   for (int q = lane; q < m; q += 32) {
     const int i = ps.ord_prio[q];
@@ -99,6 +103,8 @@ extern "C" void chol_opts_default(chol_opts *o) {
   o->timeout_ns = 10000000000ll;
   o->trace = 0;
   o->hold_task = -1;
+  o->use_cp = 0;
+  o->cp_gbs = 40.0;
 }
 
 extern "C" long long chol_dag_task_count(int T) {
@@ -155,12 +161,14 @@ extern "C" chol_status chol_dag_bottom_levels(int T, const long long *cost_ns, l
 extern "C" chol_status chol_sched_activate(int policy, double alpha, int max_iter, double eps,
                                            int m, const int *tid, const long long *p,
                                            const long long *prio, const int *aff,
-                                           const long long *score, int W, const long long *load,
+                                           const long long *score, int use_cp, const long long *comm,
+                                           const int *own3, const int *nin, int W, const long long *load,
                                            int *out_tid, int *out_worker, int *out_iters) {
   if ((policy != CHOL_POLICY_HEFT && policy != CHOL_POLICY_DADA) || m < 0 || m > 1024 || W < 1 ||
       W > 1024 || !(alpha >= 0.0 && alpha <= 1.0) || max_iter < 0 || !(eps >= 0.0))
     return CHOL_ERR_INVALID_ARG;
   if (m > 0 && (!tid || !p || !prio || !aff || !score || !out_tid || !out_worker)) return CHOL_ERR_INVALID_ARG;
+  if (m > 0 && use_cp && (!comm || !own3 || !nin)) return CHOL_ERR_INVALID_ARG;
   if (!load) return CHOL_ERR_INVALID_ARG;
   std::vector<ReadyTask> LR(m > 0 ? m : 1);
   for (int i = 0; i < m; ++i) {
@@ -169,6 +177,9 @@ extern "C" chol_status chol_sched_activate(int policy, double alpha, int max_ite
     LR[i].prio = prio[i];
     LR[i].aff = aff[i];
     LR[i].score = score[i];
+    LR[i].comm = use_cp ? comm[i] : 0;
+    LR[i].nin = use_cp ? nin[i] : 0;
+    for (int a = 0; a < 3; ++a) LR[i].own[a] = use_cp ? own3[3 * i + a] : -1;
   }
   std::vector<int> ints(5 * (m > 0 ? m : 1));
   std::vector<int64_t> ld(2 * W);
@@ -180,7 +191,7 @@ extern "C" chol_status chol_sched_activate(int policy, double alpha, int max_ite
   ps.assign = ints.data() + 3 * m;
   ps.trial = ints.data() + 4 * m;
   ps.tload = ld.data() + W;
-  const int it = place<HostExec>(policy, alpha, max_iter, eps, LR.data(), m, ld.data(), W, ps);
+  const int it = place<HostExec>(policy, alpha, max_iter, eps, LR.data(), m, ld.data(), W, ps, use_cp != 0);
   for (int q = 0; q < m; ++q) {
     const int i = ps.ord_prio[q];
     out_tid[q] = LR[i].tid;
@@ -193,20 +204,24 @@ extern "C" chol_status chol_sched_activate(int policy, double alpha, int max_ite
 extern "C" chol_status chol_sched_activate_device(int policy, double alpha, int max_iter, double eps,
                                                   int m, const int *dtid, const long long *dp,
                                                   const long long *dprio, const int *daff,
-                                                  const long long *dscore, int W,
-                                                  const long long *dload, int *dout_tid,
-                                                  int *dout_worker, int *dout_iters, void *stream) {
+                                                  const long long *dscore, int use_cp,
+                                                  const long long *dcomm, const int *down3,
+                                                  const int *dnin, int W, const long long *dload,
+                                                  int *dout_tid, int *dout_worker, int *dout_iters,
+                                                  void *stream) {
   if ((policy != CHOL_POLICY_HEFT && policy != CHOL_POLICY_DADA) || m < 1 || m > 1024 || W < 1 ||
       W > 1024 || !(alpha >= 0.0 && alpha <= 1.0) || max_iter < 0 || !(eps >= 0.0))
     return CHOL_ERR_INVALID_ARG;
   if (!dtid || !dp || !dprio || !daff || !dscore || !dload || !dout_tid || !dout_worker || !dout_iters)
     return CHOL_ERR_INVALID_ARG;
+  if (use_cp && (!dcomm || !down3 || !dnin)) return CHOL_ERR_INVALID_ARG;
   const size_t smem = sched_smem(m, W);
   CHOL_CUDA_TRY(cudaFuncSetAttribute(sched_activate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
   sched_activate_kernel<<<1, 32, smem, (cudaStream_t)stream>>>(policy, alpha, max_iter, eps, m, dtid, dp,
-                                                                dprio, daff, dscore, W, dload, dout_tid,
-                                                                dout_worker, dout_iters);
+                                                                dprio, daff, dscore, use_cp, dcomm, down3,
+                                                                dnin, W, dload, dout_tid, dout_worker,
+                                                                dout_iters);
   CHOL_CUDA_TRY(cudaGetLastError());
   return CHOL_OK;
 }

@@ -61,6 +61,8 @@ struct FactorArgs {
   unsigned long long *qcost;   // int64 two's complement
   unsigned long long *run_end; // ns, 0 = idle
   long long *trace_buf;
+  int use_cp;       // communication prediction in the placement
+  int64_t comm_ns;  // predicted cost of one input tile a worker did not write last
 };
 
 struct Resolved {
@@ -69,10 +71,12 @@ struct Resolved {
   int64_t cost[4];
   int64_t timeout_ns;
   int64_t hold_task;
+  int use_cp;
+  int64_t comm_ns;
 };
 
 struct Layout {
-  size_t ctrl, qhead, qcount, qcost, run_end, slots, zero_end, cnt, owner, bl, trace, total;
+  size_t ctrl, trace, zero_begin, qhead, qcount, qcost, run_end, slots, zero_end, cnt, owner, bl, total;
   int C;
   int64_t ntasks;
 };
@@ -98,7 +102,11 @@ static Layout make_layout(int n, const Resolved &r, int W) {
     L.C = (int)std::max<int64_t>(128, (need + 31) / 32 * 32);
   }
   size_t o = 0;
+  // the trace comes first so that its offset does not depend on the worker count
   L.ctrl = o; o += align_up(sizeof(Ctrl), 256);
+  L.trace = o;
+  if (r.trace) o += align_up((size_t)L.ntasks * 32, 256);
+  L.zero_begin = o;
   L.qhead = o; o += align_up((size_t)W * 4, 256);
   L.qcount = o; o += align_up((size_t)W * 4, 256);
   L.qcost = o; o += align_up((size_t)W * 8, 256);
@@ -108,8 +116,6 @@ static Layout make_layout(int n, const Resolved &r, int W) {
   L.cnt = o; o += align_up((size_t)L.ntasks * 4, 256);
   L.owner = o; o += align_up((size_t)T * T * 4, 256);
   L.bl = o; o += align_up((size_t)L.ntasks * 8, 256);
-  L.trace = o;
-  if (r.trace) o += align_up((size_t)L.ntasks * 32, 256);
   L.total = o;
   (void)n;
   return L;
@@ -299,6 +305,30 @@ __device__ void complete(const FactorArgs &a, int wid, const TaskDesc &d, unsign
       const int aff = ld_volatile(&a.owner[ti * T + tj]);
       LR[i].aff = aff;
       LR[i].score = aff >= 0 ? (int64_t)min(a.nb, a.n - ti * a.nb) * min(a.nb, a.n - tj * a.nb) * 8 : 0;
+      // communication prediction: the workers holding the task's input tiles
+      LR[i].comm = a.comm_ns;
+      LR[i].own[0] = LR[i].own[1] = LR[i].own[2] = -1;
+      if (a.use_cp) {
+        if (sd.kind == K_POTRF) {
+          LR[i].own[0] = ld_volatile(&a.owner[sd.k * T + sd.k]);
+          LR[i].nin = 1;
+        } else if (sd.kind == K_TRSM) {
+          LR[i].own[0] = ld_volatile(&a.owner[sd.k * T + sd.k]);
+          LR[i].own[1] = ld_volatile(&a.owner[sd.i * T + sd.k]);
+          LR[i].nin = 2;
+        } else if (sd.kind == K_SYRK) {
+          LR[i].own[0] = ld_volatile(&a.owner[sd.i * T + sd.k]);
+          LR[i].own[1] = ld_volatile(&a.owner[sd.i * T + sd.i]);
+          LR[i].nin = 2;
+        } else {
+          LR[i].own[0] = ld_volatile(&a.owner[sd.i * T + sd.k]);
+          LR[i].own[1] = ld_volatile(&a.owner[sd.j * T + sd.k]);
+          LR[i].own[2] = ld_volatile(&a.owner[sd.i * T + sd.j]);
+          LR[i].nin = 3;
+        }
+      } else {
+        LR[i].nin = 0;
+      }
     }
     __syncwarp();
     const bool model = a.policy == P_HEFT || a.policy == P_DADA;
@@ -313,7 +343,7 @@ __device__ void complete(const FactorArgs &a, int wid, const TaskDesc &d, unsign
         load[w] = rem + (q > 0 ? q : 0);
       }
       __syncwarp();
-      place<WarpExec>(a.policy, a.alpha, a.dada_max_iter, a.dada_eps, LR, m, load, a.W, ps);
+      place<WarpExec>(a.policy, a.alpha, a.dada_max_iter, a.dada_eps, LR, m, load, a.W, ps, a.use_cp != 0);
     } else {
       for (int i = lane; i < m; i += 32) {
         if (a.policy == P_STEAL) {
@@ -526,6 +556,12 @@ static bool resolve(int n, const chol_opts *opts, Resolved &r, int prec = PREC_F
   r.timeout_ns = o.timeout_ns > 0 ? o.timeout_ns : 10000000000ll;
   r.trace = o.trace ? 1 : 0;
   r.hold_task = o.hold_task;
+  r.use_cp = o.use_cp ? 1 : 0;
+  {
+    const double gbs = o.cp_gbs > 0.0 ? o.cp_gbs : 40.0;  // GB/s = bytes per ns
+    const double tile_bytes = nb * nb * (prec == PREC_F64 ? 8.0 : 4.0);
+    r.comm_ns = std::max<int64_t>(1, (int64_t)(tile_bytes / gbs));
+  }
   if (r.hold_task >= task_count(r.T)) return false;
   return true;
 }
@@ -609,6 +645,8 @@ chol_status factor_impl(int prec, int n, void *dA, int lda, const chol_opts *opt
   a.alpha = r.alpha; a.dada_eps = r.eps;
   for (int k = 0; k < 4; ++k) a.cost[k] = r.cost[k];
   a.timeout_ns = r.timeout_ns;
+  a.use_cp = r.use_cp;
+  a.comm_ns = r.comm_ns;
   a.iter_limit = std::max<int64_t>(100000, r.timeout_ns / 256);
   a.ctrl = reinterpret_cast<Ctrl *>(ws + L.ctrl);
   a.cnt = reinterpret_cast<int *>(ws + L.cnt);
@@ -621,7 +659,8 @@ chol_status factor_impl(int prec, int n, void *dA, int lda, const chol_opts *opt
   a.run_end = reinterpret_cast<unsigned long long *>(ws + L.run_end);
   a.trace_buf = r.trace ? reinterpret_cast<long long *>(ws + L.trace) : nullptr;
 
-  CHOL_CUDA_TRY(cudaMemsetAsync(ws, 0, L.zero_end, s));
+  CHOL_CUDA_TRY(cudaMemsetAsync(ws + L.ctrl, 0, sizeof(Ctrl), s));
+  CHOL_CUDA_TRY(cudaMemsetAsync(ws + L.zero_begin, 0, L.zero_end - L.zero_begin, s));
   if (r.trace) CHOL_CUDA_TRY(cudaMemsetAsync(ws + L.trace, 0xff, (size_t)L.ntasks * 32, s));
   {
     const int64_t work = std::max<int64_t>(L.ntasks, (int64_t)r.T * r.T);

@@ -15,6 +15,7 @@
 //   berr            eta = max_c ||r_c||_inf / (||A||_inf ||x_c||_inf + ||b_c||_inf)
 #include <algorithm>
 #include "common.cuh"
+#include "blockacc.cuh"
 #include "internal.cuh"
 
 namespace chol {
@@ -88,25 +89,28 @@ __global__ void __launch_bounds__(256) rownorm_kernel(const double *A, int64_t l
   }
 }
 
-// R = B - A X (FP64). Block (I, g): rows I*32.., columns g*64..; thread (row rr, slice cs)
-// owns columns cs + 8q. A's block (I, J) comes from the lower triangle: (I, J) for J < I,
-// (J, I)^T for J > I, the symmetric diagonal block for J = I.
+// R = B - A X (FP64). Block (I, g): rows I*32.., columns g*64..; the 32 x 32 blocks of the
+// symmetric A come from its lower triangle (load_sym_block); the threads share the
+// products as described in blockacc.cuh.
+template <int CPT>
 __global__ void __launch_bounds__(256) symm_residual_kernel(const double *A, int64_t lda, const double *X,
                                                             int64_t ldx, const double *B, int64_t ldb, double *R,
                                                             int64_t ldr, int n, int nrhs, const int *skip) {
   __shared__ double As[RB * RLD];
   __shared__ double Xs[RB * RG];
+  __shared__ double Red[RB * RG];
   if (skip && ld_volatile(skip)) return;
   const int nrb = (n + RB - 1) / RB;
   const int I = blockIdx.x, g = blockIdx.y;
   const int I0 = I * RB, rows = min(RB, n - I0);
   const int c0 = g * RG, cols = min(RG, nrhs - c0);
-  const int tid = threadIdx.x, rr = tid & 31, cs = tid >> 5;
-  double acc[8];
+  const int tid = threadIdx.x, rr = tid & 31, warp = tid >> 5;
+  const Slices<CPT> sl(cols, warp);
+  double acc[CPT];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int c = cs + 8 * q;
-    acc[q] = (rr < rows && c < cols) ? B[(int64_t)(c0 + c) * ldb + I0 + rr] : 0.0;
+  for (int q = 0; q < CPT; ++q) {
+    const int c = sl.col(q);
+    acc[q] = (sl.kslice == 0 && rr < rows && c < cols) ? B[(int64_t)(c0 + c) * ldb + I0 + rr] : 0.0;
   }
   for (int J = 0; J < nrb; ++J) {
     const int J0 = J * RB, jc = min(RB, n - J0);
@@ -116,19 +120,13 @@ __global__ void __launch_bounds__(256) symm_residual_kernel(const double *A, int
       Xs[k * RG + c] = (k < jc && c < cols) ? X[(int64_t)(c0 + c) * ldx + J0 + k] : 0.0;
     }
     __syncthreads();
-#pragma unroll 4
-    for (int k = 0; k < RB; ++k) {
-      const double a = As[rr * RLD + k];
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (cs + 8 * q < cols) acc[q] = fma(-a, Xs[k * RG + cs + 8 * q], acc[q]);
-    }
+    acc_step<double, CPT>(acc, As, RLD, Xs, RG, rr, sl);
     __syncthreads();
   }
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int c = cs + 8 * q;
-    if (rr < rows && c < cols) R[(int64_t)(c0 + c) * ldr + I0 + rr] = acc[q];
+  acc_finish<double, CPT>(acc, Xs, RG, Red, rr, cols, sl);
+  for (int e = tid; e < RB * cols; e += 256) {
+    const int i = e & 31, c = e >> 5;
+    if (i < rows) R[(int64_t)(c0 + c) * ldr + I0 + i] = Xs[i * RG + c];
   }
 }
 
@@ -302,7 +300,11 @@ extern "C" chol_status chol_solve_refine(int n, int nrhs, const double *dA, int 
     st = solve_f32(n, nrhs, A32, (int)L.lda32, R32, (int)L.ld32, ws + L.swork, skip, s);
     if (st != CHOL_OK) return st;
     axpy_kernel<<<eblocks, 256, 0, s>>>(dX, ldx, R32, L.ld32, n, nrhs, skip);
-    symm_residual_kernel<<<rgrid, 256, 0, s>>>(dA, lda, dX, ldx, dB, ldb, R, n, n, nrhs, skip);
+    const int cpt = cpt_for(std::min(nrhs, RG));
+    if (cpt == 8) symm_residual_kernel<8><<<rgrid, 256, 0, s>>>(dA, lda, dX, ldx, dB, ldb, R, n, n, nrhs, skip);
+    else if (cpt == 4) symm_residual_kernel<4><<<rgrid, 256, 0, s>>>(dA, lda, dX, ldx, dB, ldb, R, n, n, nrhs, skip);
+    else if (cpt == 2) symm_residual_kernel<2><<<rgrid, 256, 0, s>>>(dA, lda, dX, ldx, dB, ldb, R, n, n, nrhs, skip);
+    else symm_residual_kernel<1><<<rgrid, 256, 0, s>>>(dA, lda, dX, ldx, dB, ldb, R, n, n, nrhs, skip);
     berr_cols_kernel<<<nrhs, 256, 0, s>>>(R, n, dX, ldx, dB, ldb, n, ctrl, eta, skip);
     refine_step_done_kernel<<<1, 32, 0, s>>>(ctrl, eta, nrhs, tol, finfo);
     CHOL_CUDA_TRY(cudaGetLastError());

@@ -17,6 +17,10 @@
 //  when every load fits in (2 + alpha) * lambda; the last accepted schedule is pushed.
 //  The search stops when upper - lower <= eps * (first upper) or after max_iter halvings.
 //
+//  Communication prediction (DADA(alpha)+CP, and HEFT's transfer-aware finish time): a task
+//  costs p plus `comm` for each input tile the worker did not write last (cost_on); the
+//  finish times of both algorithms and DADA's loads then use that cost.
+//
 // The same code runs on the host (Exec = HostExec, one thread) and on the device inside
 // the persistent kernel (Exec = WarpExec: all 32 lanes of one warp execute it in lockstep,
 // the leader lane performs the sequential writes, and the worker scans are warp-parallel).
@@ -35,7 +39,18 @@ struct ReadyTask {
   int64_t p;      // processing time, ns
   int64_t prio;   // bottom level, ns
   int64_t score;  // affinity score, bytes
+  int64_t comm;   // communication prediction: cost of one input tile not owned by the worker
+  int own[3];     // workers that last wrote the task's input tiles (-1: none)
+  int nin;        // number of input tiles (1..3)
 };
+
+// Cost of task t on worker w; with communication prediction every input tile that w did
+// not write last adds t.comm.
+CHOL_HD int64_t cost_on(const ReadyTask &t, int w, bool cp) {
+  if (!cp) return t.p;
+  const int cnt = (t.own[0] == w) + (t.own[1] == w) + (t.own[2] == w);
+  return t.p + t.comm * (t.nin - cnt);
+}
 
 struct HostExec {
   CHOL_HD static bool leader() { return true; }
@@ -54,9 +69,9 @@ struct HostExec {
     for (int w = 1; w < W; ++w) m = load[w] > m ? load[w] : m;
     return m;
   }
-  CHOL_HD static int64_t sum_p(const ReadyTask *LR, int m) {
+  CHOL_HD static int64_t sum_p(const ReadyTask *LR, int m, bool cp) {
     int64_t s = 0;
-    for (int i = 0; i < m; ++i) s += LR[i].p;
+    for (int i = 0; i < m; ++i) s += LR[i].p + (cp ? LR[i].comm * LR[i].nin : 0);
     return s;
   }
 };
@@ -92,10 +107,10 @@ struct WarpExec {
     }
     return m;
   }
-  __device__ static int64_t sum_p(const ReadyTask *LR, int m) {
+  __device__ static int64_t sum_p(const ReadyTask *LR, int m, bool cp) {
     const int l = threadIdx.x & 31;
     int64_t s = 0;
-    for (int i = l; i < m; i += 32) s += LR[i].p;
+    for (int i = l; i < m; i += 32) s += LR[i].p + (cp ? LR[i].comm * LR[i].nin : 0);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     return s;
   }
@@ -145,10 +160,32 @@ CHOL_HD void sort_indices(int *ord, const ReadyTask *LR, int m) {
   }
 }
 
+// Worker with the earliest finish time load[w] + cost_on(t, w), ties to the lowest index.
+// Without communication prediction that is the least-loaded worker. With it, only the
+// (at most three) workers owning input tiles can beat the least-loaded worker, so they are
+// the only ones evaluated besides it.
+template <class X>
+CHOL_HD int eft_worker(const int64_t *load, int W, const ReadyTask &t, bool cp) {
+  const int w0 = X::argmin(load, W);
+  if (!cp) return w0;
+  int bw = w0;
+  int64_t best = load[w0] + cost_on(t, w0, cp);
+  for (int a = 0; a < 3; ++a) {
+    const int o = t.own[a];
+    if (o < 0 || o >= W) continue;
+    const int64_t v = load[o] + cost_on(t, o, cp);
+    if (v < best || (v == best && o < bw)) {
+      best = v;
+      bw = o;
+    }
+  }
+  return bw;
+}
+
 // One DADA trial at guess lam; returns whether all loads fit in (2 + alpha) lam.
 template <class X>
 CHOL_HD bool dada_trial(const ReadyTask *LR, int m, const int64_t *load, int W, double alpha,
-                        int64_t lam, PlaceScratch &s) {
+                        int64_t lam, PlaceScratch &s, bool cp) {
   for (int w = X::lane(); w < W; w += X::width()) s.tload[w] = load[w];
   for (int i = X::lane(); i < m; i += X::width()) s.trial[i] = -1;
   X::sync();
@@ -160,7 +197,7 @@ CHOL_HD bool dada_trial(const ReadyTask *LR, int m, const int64_t *load, int W, 
       if (w < 0 || w >= W) continue;
       if ((double)s.tload[w] < thr) {
         s.trial[i] = w;
-        s.tload[w] += LR[i].p;
+        s.tload[w] += cost_on(LR[i], w, cp);
       }
     }
   }
@@ -168,11 +205,11 @@ CHOL_HD bool dada_trial(const ReadyTask *LR, int m, const int64_t *load, int W, 
   for (int q = 0; q < m; ++q) {
     const int i = s.ord_lpt[q];
     if (s.trial[i] >= 0) continue;   // uniform: every lane reads the same shared value
-    const int w = X::argmin(s.tload, W);
+    const int w = eft_worker<X>(s.tload, W, LR[i], cp);
     X::sync();
     if (X::leader()) {
       s.trial[i] = w;
-      s.tload[w] += LR[i].p;
+      s.tload[w] += cost_on(LR[i], w, cp);
     }
     X::sync();
   }
@@ -185,7 +222,7 @@ CHOL_HD bool dada_trial(const ReadyTask *LR, int m, const int64_t *load, int W, 
 // of bisection steps taken (DADA) or 0.
 template <class X>
 CHOL_HD int place(int policy, double alpha, int max_iter, double eps, const ReadyTask *LR, int m,
-                  int64_t *load, int W, PlaceScratch &s) {
+                  int64_t *load, int W, PlaceScratch &s, bool cp = false) {
   if (m <= 0) return 0;
   if (X::leader()) sort_indices<0>(s.ord_prio, LR, m);
   X::sync();
@@ -193,11 +230,11 @@ CHOL_HD int place(int policy, double alpha, int max_iter, double eps, const Read
   if (policy == P_HEFT) {
     for (int q = 0; q < m; ++q) {
       const int i = s.ord_prio[q];
-      const int w = X::argmin(load, W);  // argmin of load + p is argmin of load
+      const int w = eft_worker<X>(load, W, LR[i], cp);
       X::sync();
       if (X::leader()) {
         s.assign[i] = w;
-        load[w] += LR[i].p;
+        load[w] += cost_on(LR[i], w, cp);
       }
       X::sync();
     }
@@ -210,15 +247,15 @@ CHOL_HD int place(int policy, double alpha, int max_iter, double eps, const Read
   }
   X::sync();
   int64_t lower = 0;
-  int64_t upper = X::sum_p(LR, m) + X::maxval(load, W);
+  int64_t upper = X::sum_p(LR, m, cp) + X::maxval(load, W);
   X::sync();
   const int64_t eps_abs = (int64_t)((double)upper * eps);
-  dada_trial<X>(LR, m, load, W, alpha, upper, s);  // always fits: every load <= upper
+  dada_trial<X>(LR, m, load, W, alpha, upper, s, cp);  // always fits: every load <= upper
   for (int i = X::lane(); i < m; i += X::width()) s.assign[i] = s.trial[i];
   X::sync();
   while (upper - lower > eps_abs && iters < max_iter) {
     const int64_t lam = (upper + lower) / 2;
-    const bool fits = dada_trial<X>(LR, m, load, W, alpha, lam, s);
+    const bool fits = dada_trial<X>(LR, m, load, W, alpha, lam, s, cp);
     if (fits) {
       upper = lam;
       for (int i = X::lane(); i < m; i += X::width()) s.assign[i] = s.trial[i];
@@ -229,7 +266,7 @@ CHOL_HD int place(int policy, double alpha, int max_iter, double eps, const Read
     ++iters;
   }
   if (X::leader())
-    for (int q = 0; q < m; ++q) load[s.assign[q]] += LR[q].p;
+    for (int q = 0; q < m; ++q) load[s.assign[q]] += cost_on(LR[q], s.assign[q], cp);
   X::sync();
   return iters;
 }

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <mutex>
 #include "common.cuh"
+#include "blockacc.cuh"
 #include "internal.cuh"
 
 namespace chol {
@@ -55,20 +56,20 @@ __device__ __forceinline__ T squot(T b, T d, T r) {
   return fma(e, r, x);
 }
 
-template <class T>
+template <class T, int CPT>
 __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ SolveArgs a) {
-  __shared__ T Ls[SB * SLD];
+  __shared__ T Ls[SB * SLD];  // off-diagonal block of the current step
+  __shared__ T Ld[SB * SLD];  // diagonal block of the item (prefetched)
   __shared__ T Ys[SB * SG];
-  __shared__ T Red[8 * SB * 8];  // partial sums of the k-split path [slice][row][col]
-  __shared__ T Rs[SB];           // reciprocals of the diagonal block
+  __shared__ T Red[SB * SG];  // k-slice partial sums
+  __shared__ T Rs[SB];        // reciprocals of the diagonal
   __shared__ long long s_item;
   __shared__ int s_abort;
   const T *L = static_cast<const T *>(a.L);
   T *B = static_cast<T *>(a.B);
   if (a.skip && ld_volatile(a.skip)) return;
   const int tid = threadIdx.x;
-  const int lane = tid & 31, warp = tid >> 5;
-  const int rr = lane, cs = warp;  // accumulation: row rr of the block, slice cs
+  const int rr = tid & 31, warp = tid >> 5;
   while (true) {
     if (tid == 0) {
       s_abort = ld_volatile(&a.ctrl->abort) || (a.prev_abort && ld_volatile(a.prev_abort));
@@ -82,14 +83,21 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
     const int r = a.trans ? a.nrb - 1 - ord : ord;
     const int r0 = r * SB, rows = min(SB, a.n - r0);
     const int c0 = g * SG, cols = min(SG, a.nrhs - c0);
-    // With 8 or more columns, slice cs owns columns cs + 8q over all k. With fewer, every
-    // slice owns all columns and the k range is split: slice cs takes k = cs + 8t.
-    const bool ksplit = cols < 8;
-    T acc[8];
+    const Slices<CPT> sl(cols, warp);
+    // the diagonal block and its reciprocals do not depend on other items: load them now,
+    // off the chain of waits. Rows past the end of the matrix get an identity block, so
+    // the substitution runs over a fixed 32 rows with register-resident data.
+    for (int e = tid; e < SB * SB; e += SNT) {
+      const int i = e & 31, j = e >> 5;
+      Ld[i * SLD + j] = (i < rows && j < rows && i >= j) ? __ldcg(L + (int64_t)(r0 + j) * a.lda + r0 + i)
+                                                          : (i == j ? T(1) : T(0));
+    }
+    if (tid < SB) Rs[tid] = tid < rows ? T(1) / __ldcg(L + (int64_t)(r0 + tid) * a.lda + r0 + tid) : T(1);
+    T acc[CPT];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int c = cs + 8 * q;
-      acc[q] = (!ksplit && rr < rows && c < cols) ? __ldcg(B + (int64_t)(c0 + c) * a.ldb + r0 + rr) : T(0);
+    for (int q = 0; q < CPT; ++q) {
+      const int c = sl.col(q);
+      acc[q] = (sl.kslice == 0 && rr < rows && c < cols) ? __ldcg(B + (int64_t)(c0 + c) * a.ldb + r0 + rr) : T(0);
     }
     // blocks are consumed in the order the sweep produces them (forward: 0, 1, ...;
     // backward: nrb-1, nrb-2, ...), so an item only waits on the newest block it needs
@@ -110,17 +118,17 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
       if (tid == 0) {
         const uint64_t t0 = globaltimer_ns();
         int64_t spins = 0;
-        unsigned sl = 32;
+        unsigned slp = 32;
         while (ld_volatile(&a.flags[(int64_t)m * a.ngroups + g]) == 0) {
           if (ld_volatile(&a.ctrl->abort)) { s_abort = 1; break; }
-          if (globaltimer_ns() - t0 > (uint64_t)a.timeout_ns || ++spins > (a.timeout_ns >> 8) + 100000) {
+          if (globaltimer_ns() - t0 > (uint64_t)a.timeout_ns || ++spins > (a.timeout_ns >> 7) + 100000) {
             atomicCAS(&a.ctrl->info, 0, CHOL_INFO_TIMEOUT);
             atomicExch(&a.ctrl->abort, 1);
             s_abort = 1;
             break;
           }
-          __nanosleep(sl);
-          sl = sl < 1024 ? sl * 2 : 1024;
+          __nanosleep(slp);
+          slp = slp < 128 ? slp * 2 : 128;
         }
         __threadfence();
       }
@@ -131,55 +139,13 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
         Ys[k * SG + c] = (k < mrows && c < cols) ? __ldcg(B + (int64_t)(c0 + c) * a.ldb + m0 + k) : T(0);
       }
       __syncthreads();
-      if (!ksplit) {
-#pragma unroll 4
-        for (int k = 0; k < SB; ++k) {
-          const T l = Ls[rr * SLD + k];
-#pragma unroll
-          for (int q = 0; q < 8; ++q)
-            if (cs + 8 * q < cols) acc[q] = fma(-l, Ys[k * SG + cs + 8 * q], acc[q]);
-        }
-      } else {
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int k = cs + 8 * t;
-          const T l = Ls[rr * SLD + k];
-#pragma unroll
-          for (int q = 0; q < 7; ++q)
-            if (q < cols) acc[q] = fma(-l, Ys[k * SG + q], acc[q]);
-        }
-      }
+      acc_step<T, CPT>(acc, Ls, SLD, Ys, SG, rr, sl);
       __syncthreads();
     }
     if (s_abort) break;
-    // diagonal block: Ls = L_rr (lower, [i][j]); Ys = accumulated right-hand sides [row][col].
-    // One thread per right-hand side runs the substitution, so every FP64 instruction of the
-    // block does useful work (the FP64 pipe, not latency, bounds this phase).
-    for (int e = tid; e < SB * SB; e += SNT) {
-      const int i = e & 31, j = e >> 5;
-      // rows past the end of the matrix get an identity block, so the substitution below
-      // runs over a fixed 32 rows with register-resident data
-      Ls[i * SLD + j] = (i < rows && j < rows && i >= j) ? __ldcg(L + (int64_t)(r0 + j) * a.lda + r0 + i)
-                                                          : (i == j ? T(1) : T(0));
-    }
-    if (tid < SB) Rs[tid] = tid < rows ? T(1) / __ldcg(L + (int64_t)(r0 + tid) * a.lda + r0 + tid) : T(1);
-    if (!ksplit) {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) Ys[rr * SG + cs + 8 * q] = acc[q];
-    } else {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) Red[(cs * SB + rr) * 8 + q] = acc[q];
-    }
-    __syncthreads();
-    if (ksplit && tid < SB * 8) {
-      const int i = tid & 31, q = tid >> 5;
-      if (q < cols) {
-        T t = (i < rows) ? __ldcg(B + (int64_t)(c0 + q) * a.ldb + r0 + i) : T(0);
-        for (int s = 0; s < 8; ++s) t += Red[(s * SB + i) * 8 + q];
-        Ys[i * SG + q] = t;
-      }
-    }
-    __syncthreads();
+    acc_finish<T, CPT>(acc, Ys, SG, Red, rr, cols, sl);
+    // diagonal block: one thread per right-hand side runs the substitution, so every FP64
+    // instruction of the block does useful work (the FP64 pipe, not latency, bounds it)
     if (tid < cols) {
       const int c = tid;
       T x[SB];
@@ -190,16 +156,16 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
       if (!a.trans) {
 #pragma unroll
         for (int k = 0; k < SB; ++k) {
-          x[k] = squot(x[k], Ls[k * SLD + k], Rs[k]);
+          x[k] = squot(x[k], Ld[k * SLD + k], Rs[k]);
 #pragma unroll
-          for (int i = k + 1; i < SB; ++i) x[i] = fma(-Ls[i * SLD + k], x[k], x[i]);
+          for (int i = k + 1; i < SB; ++i) x[i] = fma(-Ld[i * SLD + k], x[k], x[i]);
         }
       } else {
 #pragma unroll
         for (int k = SB - 1; k >= 0; --k) {
-          x[k] = squot(x[k], Ls[k * SLD + k], Rs[k]);
+          x[k] = squot(x[k], Ld[k * SLD + k], Rs[k]);
 #pragma unroll
-          for (int i = 0; i < k; ++i) x[i] = fma(-Ls[k * SLD + i], x[k], x[i]);
+          for (int i = 0; i < k; ++i) x[i] = fma(-Ld[k * SLD + i], x[k], x[i]);
         }
       }
 #pragma unroll
@@ -226,6 +192,18 @@ static size_t solve_ws(int n, int nrhs) { return 512 + 2 * flags_bytes(n, nrhs);
 
 size_t solve_workspace_bytes(int n, int nrhs) { return solve_ws(n, nrhs); }
 
+template <class T, int CPT>
+static cudaError_t launch_solve(const SolveArgs &a, int grid, cudaStream_t s) {
+  // one block per SM: the dynamic shared memory request (more than half an SM's) makes a
+  // second block impossible
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(solve_kernel<T, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_EXCL_SMEM);
+  });
+  solve_kernel<T, CPT><<<grid, SNT, SOLVE_EXCL_SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <class T>
 static chol_status launch_sweep(int trans, int slot, int n, int nrhs, const T *dL, int lda, T *dB, int ldb,
                                 void *dWork, const int *skip, cudaStream_t s) {
@@ -248,14 +226,14 @@ static chol_status launch_sweep(int trans, int slot, int n, int nrhs, const T *d
   // queued FP64 instruction of the SM). The dynamic shared memory request (more than half
   // of an SM's) makes a second block impossible.
   const DeviceInfo di = current_device_info();
-  static std::once_flag once;
-  std::call_once(once, [] {
-    cudaFuncSetAttribute(solve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_EXCL_SMEM);
-    cudaFuncSetAttribute(solve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_EXCL_SMEM);
-  });
   const int64_t grid = std::min<int64_t>(a.nitems, (int64_t)std::max(1, di.sms));
-  solve_kernel<T><<<(int)grid, SNT, SOLVE_EXCL_SMEM, s>>>(a);
-  CHOL_CUDA_TRY(cudaGetLastError());
+  const int cpt = cpt_for(std::min(nrhs, SG));
+  cudaError_t e;
+  if (cpt == 8) e = launch_solve<T, 8>(a, (int)grid, s);
+  else if (cpt == 4) e = launch_solve<T, 4>(a, (int)grid, s);
+  else if (cpt == 2) e = launch_solve<T, 2>(a, (int)grid, s);
+  else e = launch_solve<T, 1>(a, (int)grid, s);
+  CHOL_CUDA_TRY(e);
   return CHOL_OK;
 }
 

@@ -38,7 +38,7 @@ def test_opts_struct_layout_matches_header():
     assert o.nb == 256 and o.policy == 0 and o.alpha == 0.5 and o.steal == 1
     assert o.dada_max_iter == 16 and abs(o.dada_eps - 0.01) < 1e-15
     assert o.timeout_ns == 10_000_000_000 and o.trace == 0
-    assert ctypes.sizeof(chol.ChOpts) == 104 and o.hold_task == -1
+    assert ctypes.sizeof(chol.ChOpts) == 120 and o.hold_task == -1 and o.use_cp == 0 and o.cp_gbs == 40.0
 
 
 @pytest.mark.parametrize("T", [1, 2, 3, 5, 8, 11])
@@ -123,3 +123,53 @@ def test_workspace_sizes_are_positive_and_monotone():
     assert 0 < a < b
     assert chol.workspace_size(1024, chol.opts(nb=8)) == 0  # nb below 16 is rejected
     assert chol.solve_workspace_size(1024, 1) > 0
+
+
+def _random_ready_cp(rng, m, W):
+    out = []
+    for t in _random_ready(rng, m, W):
+        nin = rng.randint(1, 3)
+        t["own"] = [rng.choice([-1] + list(range(W))) for _ in range(nin)] + [-1] * (3 - nin)
+        t["nin"] = nin
+        t["comm"] = rng.choice([0, 10, 40, 400])
+        out.append(t)
+    return out
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_heft_cp_host_matches_oracle(seed):
+    import paper_1402_6601_gb300 as chol
+    rng = random.Random(500 + seed)
+    for _ in range(40):
+        W = rng.randint(1, 24)
+        LR = _random_ready_cp(rng, rng.randint(1, 20), W)
+        load = [rng.randint(0, 3000) for _ in range(W)]
+        got, _ = chol.sched_activate("heft", LR, load, use_cp=True)
+        assert got == osched.heft_cp(LR, load)
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("alpha", [0.0, 0.5, 1.0])
+def test_dada_cp_host_matches_oracle(seed, alpha):
+    import paper_1402_6601_gb300 as chol
+    rng = random.Random(900 + seed)
+    for _ in range(40):
+        W = rng.randint(1, 24)
+        LR = _random_ready_cp(rng, rng.randint(1, 20), W)
+        load = [rng.choice([0, rng.randint(0, 3000)]) for _ in range(W)]
+        got, it = chol.sched_activate("dada", LR, load, alpha=alpha, use_cp=True)
+        ref, rit = osched.dada_cp(LR, load, alpha)
+        assert got == ref and it == rit
+
+
+def test_cp_with_zero_comm_equals_plain():
+    import paper_1402_6601_gb300 as chol
+    rng = random.Random(77)
+    for _ in range(30):
+        W = rng.randint(1, 16)
+        LR = _random_ready_cp(rng, rng.randint(1, 12), W)
+        for t in LR:
+            t["comm"] = 0
+        load = [rng.randint(0, 999) for _ in range(W)]
+        assert chol.sched_activate("heft", LR, load, use_cp=True) == chol.sched_activate("heft", LR, load)
+        assert chol.sched_activate("dada", LR, load, use_cp=True) == chol.sched_activate("dada", LR, load)

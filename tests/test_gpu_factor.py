@@ -79,7 +79,8 @@ def test_schedule_invariance_bitwise(chol):
     configs = [chol.opts(nb=64, policy="heft"), chol.opts(nb=64, policy="dada", alpha=0.0),
                chol.opts(nb=64, policy="dada", alpha=1.0), chol.opts(nb=64, policy="steal"),
                chol.opts(nb=64, policy="static"), chol.opts(nb=64, policy="heft", workers_per_sm=1),
-               chol.opts(nb=64, policy="heft", num_workers=3), chol.opts(nb=64, policy="dada", num_workers=1)]
+               chol.opts(nb=64, policy="heft", num_workers=3), chol.opts(nb=64, policy="dada", num_workers=1),
+               chol.opts(nb=64, policy="dada", alpha=0.5, use_cp=True), chol.opts(nb=64, policy="heft", use_cp=True)]
     for o in configs:
         F, info, _ = _factor(chol, A, o)
         assert info == 0
@@ -180,6 +181,13 @@ def test_sched_device_matches_host(chol):
                 load = [rng.choice([0, rng.randint(0, 5000)]) for _ in range(W)]
                 host = chol.sched_activate(policy, LR, load, alpha=alpha)
                 dev = chol.sched_activate_device(policy, LR, load, alpha=alpha)
+                assert host == dev
+                for t in LR:
+                    t["own"] = [rng.choice([-1, rng.randint(0, W - 1)]) for _ in range(3)]
+                    t["nin"] = 3
+                    t["comm"] = rng.choice([5, 50, 500])
+                host = chol.sched_activate(policy, LR, load, alpha=alpha, use_cp=True)
+                dev = chol.sched_activate_device(policy, LR, load, alpha=alpha, use_cp=True)
                 assert host == dev
 
 
