@@ -176,6 +176,32 @@ chol_status chol_solve_refine(int n, int nrhs, const double *dA, int lda, const 
                               int *dIters, double *dBerr, void *stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Reverse-mode derivatives (not in the paper: the differentiable form of the factorization).
+ * Gradients with respect to the symmetric A are returned symmetric; gradients with respect
+ * to L are lower triangular. FP64, asynchronous on `stream`, caller-owned workspaces.
+ */
+
+/* Abar = d<Lbar, chol(A)>/dA = (S + S^T)/2, S = L^-T Phi(L^T Lbar) L^-1, Phi = lower triangle
+ * with the diagonal halved (I. Murray, "Differentiation of the Cholesky decomposition",
+ * 2016). dL: the factor (lower triangle read). dLbar (n x n, ldlb): on entry Lbar (lower
+ * triangle read), on exit the full symmetric Abar. Work: chol_backward_workspace_size(n). */
+size_t chol_backward_workspace_size(int n);
+chol_status chol_backward(int n, const double *dL, int lda, double *dLbar, int ldlb, void *dWork,
+                          size_t work_bytes, void *stream);
+
+/* For X = A^-1 B with A = L L^T (X from chol_solve): given Xbar, writes Bbar = A^-1 Xbar
+ * (n x nrhs, ldbb) and Lbar = -tril((Bbar X^T + X Bbar^T) L) (n x n, ldlb, strict upper
+ * triangle set to zero). Work: chol_solve_backward_workspace_size(n, nrhs). */
+size_t chol_solve_backward_workspace_size(int n, int nrhs);
+chol_status chol_solve_backward(int n, int nrhs, const double *dL, int lda, const double *dX, int ldx,
+                                const double *dXbar, int ldxb, double *dBbar, int ldbb,
+                                double *dLbar, int ldlb, void *dWork, size_t work_bytes,
+                                void *stream);
+
+/* dDst = lower triangle of dSrc with the strict upper triangle zeroed (n x n, FP64). */
+chol_status chol_lower_copy(int n, const double *dSrc, int lds, double *dDst, int ldd, void *stream);
+
+/* ---------------------------------------------------------------------------------------
  * Host-buffer convenience: factor and solve from host memory (LAPACK dposv semantics).
  * hA (n x n, lda) is copied to the device, factored, and L is copied back into hA's lower
  * triangle; hB (n x nrhs, ldb) is overwritten by X. dStage is a device buffer of at least

@@ -19,7 +19,8 @@ from . import build as _build
 __all__ = [
     "lib", "ChOpts", "POLICIES", "opts", "colmajor", "factor", "solve", "trsm_sweep", "posv",
     "posv_host", "workspace_size", "solve_workspace_size", "num_workers", "trace", "factor_f32",
-    "solve_refine", "refine_workspace_size",
+    "solve_refine", "refine_workspace_size", "cholesky_backward", "solve_backward", "lower",
+    "cholesky", "cholesky_solve", "solve_spd",
     "dag_describe", "dag_bottom_levels", "sched_activate", "sched_activate_device",
     "CholeskyError",
 ]
@@ -75,6 +76,11 @@ _SIGNATURES = {
     "chol_factor_f32": (_I, [_I, _P, _I, _OPTS, _P, _SZ, _P, _P]),
     "chol_solve_refine_workspace_size": (_SZ, [_I, _I, _OPTS]),
     "chol_solve_refine": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _I, _D, _I, _OPTS, _P, _SZ, _P, _P, _P, _P]),
+    "chol_backward_workspace_size": (_SZ, [_I]),
+    "chol_backward": (_I, [_I, _P, _I, _P, _I, _P, _SZ, _P]),
+    "chol_solve_backward_workspace_size": (_SZ, [_I, _I]),
+    "chol_solve_backward": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _SZ, _P]),
+    "chol_lower_copy": (_I, [_I, _P, _I, _P, _I, _P]),
     "chol_posv_host_stage_size": (_SZ, [_I, _I, _OPTS]),
     "chol_posv_host": (_I, [_I, _I, _P, _I, _P, _I, _OPTS, _P, _SZ, _P, _P]),
     "chol_dag_task_count": (_LL, [_I]),
@@ -145,10 +151,13 @@ def _check(status, what):
 
 
 def colmajor(x):
-    """Column-major copy of a 2-D tensor (or a 1-D tensor as one column)."""
+    """Column-major copy of a 2-D tensor (or a 1-D tensor as one column). Always a new
+    tensor, never a view of x, so that in-place calls on it leave x untouched."""
     if x.dim() == 1:
         x = x.reshape(-1, 1)
-    return x.t().contiguous().t()
+    y = torch.empty_strided(tuple(x.shape), (1, max(1, x.shape[0])), dtype=x.dtype, device=x.device)
+    y.copy_(x)
+    return y
 
 
 def _check_matrix(A, name):
@@ -384,3 +393,120 @@ def sched_activate_device(policy, tasks, load, alpha=0.5, max_iter=16, eps=0.01,
                                           _stream(None)), "chol_sched_activate_device")
     torch.cuda.synchronize()
     return [(int(a), int(b)) for a, b in zip(ot.tolist(), ow.tolist())], int(it.item())
+
+
+# ----------------------------------------------------------------------------------------
+# Derivatives: C ABI wrappers and torch.autograd.Function classes (marshalling only; the
+# forward and backward passes run in the library's kernels).
+
+def lower(A, stream=None):
+    """Lower triangle of a column-major FP64 CUDA matrix (strict upper part zero)."""
+    n = A.shape[0]
+    lda = _check_matrix(A, "A")
+    out = colmajor(torch.empty(n, n, dtype=torch.float64, device=A.device))
+    _check(lib.chol_lower_copy(n, A.data_ptr(), lda, out.data_ptr(), max(1, n), _stream(stream)),
+           "chol_lower_copy")
+    return out
+
+
+def cholesky_backward(L, Lbar, stream=None):
+    """Abar (symmetric) for the gradient Lbar of the factor L."""
+    n = L.shape[0]
+    lda = _check_matrix(L, "L")
+    out = colmajor(Lbar.detach().to(torch.float64))
+    work = _workspace(int(lib.chol_backward_workspace_size(n)), L.device)
+    _check(lib.chol_backward(n, L.data_ptr(), lda, out.data_ptr(), max(1, n), work.data_ptr(), work.numel(),
+                             _stream(stream)), "chol_backward")
+    return out
+
+
+def solve_backward(L, X, Xbar, stream=None):
+    """(Bbar, Lbar) for X = A^-1 B, A = L L^T."""
+    n = L.shape[0]
+    lda = _check_matrix(L, "L")
+    X = colmajor(X.detach()) if X.dim() == 1 or X.stride(0) != 1 else X
+    Xbar = colmajor(Xbar.detach().to(torch.float64))
+    nrhs = X.shape[1]
+    Bbar = colmajor(torch.empty(n, nrhs, dtype=torch.float64, device=L.device))
+    Lbar = colmajor(torch.empty(n, n, dtype=torch.float64, device=L.device))
+    work = _workspace(int(lib.chol_solve_backward_workspace_size(n, nrhs)), L.device)
+    _check(lib.chol_solve_backward(n, nrhs, L.data_ptr(), lda, X.data_ptr(), max(1, n), Xbar.data_ptr(),
+                                   max(1, n), Bbar.data_ptr(), max(1, n), Lbar.data_ptr(), max(1, n),
+                                   work.data_ptr(), work.numel(), _stream(stream)), "chol_solve_backward")
+    return Bbar, Lbar
+
+
+class _CholeskyFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, A, nb):
+        F = colmajor(A.detach().to(torch.float64))
+        factor(F, opts(nb=nb), check=True)
+        L = lower(F)
+        ctx.save_for_backward(L)
+        return L
+
+    @staticmethod
+    def backward(ctx, Lbar):
+        (L,) = ctx.saved_tensors
+        return cholesky_backward(L, Lbar), None
+
+
+class _CholSolveFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, B, L):
+        vec = B.dim() == 1
+        X = colmajor(B.detach().to(torch.float64))
+        solve(L, X)
+        ctx.save_for_backward(L, X)
+        ctx.vec = vec
+        return X.reshape(-1) if vec else X
+
+    @staticmethod
+    def backward(ctx, Xbar):
+        L, X = ctx.saved_tensors
+        Bbar, Lbar = solve_backward(L, X, Xbar.reshape(X.shape))
+        return (Bbar.reshape(-1) if ctx.vec else Bbar), Lbar
+
+
+class _SolveSPDFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, A, B, nb, recompute):
+        vec = B.dim() == 1
+        F = colmajor(A.detach().to(torch.float64))
+        factor(F, opts(nb=nb), check=True)
+        X = colmajor(B.detach().to(torch.float64))
+        solve(F, X)
+        ctx.vec, ctx.nb, ctx.recompute = vec, nb, recompute
+        if recompute:   # keep only A (the caller holds it anyway) and refactor in backward
+            ctx.save_for_backward(A, X)
+        else:
+            ctx.save_for_backward(F, X)
+        return X.reshape(-1) if vec else X
+
+    @staticmethod
+    def backward(ctx, Xbar):
+        M, X = ctx.saved_tensors
+        if ctx.recompute:
+            F = colmajor(M.detach().to(torch.float64))
+            factor(F, opts(nb=ctx.nb), check=True)
+        else:
+            F = M
+        Bbar, Lbar = solve_backward(F, X, Xbar.reshape(X.shape))
+        Abar = cholesky_backward(F, Lbar)
+        return Abar, (Bbar.reshape(-1) if ctx.vec else Bbar), None, None
+
+
+def cholesky(A, nb=256):
+    """Differentiable lower Cholesky factor of a symmetric positive definite FP64 CUDA matrix."""
+    return _CholeskyFn.apply(A, nb)
+
+
+def cholesky_solve(B, L):
+    """Differentiable X = (L L^T)^-1 B."""
+    return _CholSolveFn.apply(B, L)
+
+
+def solve_spd(A, B, nb=256, recompute=False):
+    """Differentiable X = A^-1 B for symmetric positive definite A. With recompute=True the
+    backward pass refactors A instead of keeping L."""
+    return _SolveSPDFn.apply(A, B, nb, recompute)

@@ -23,7 +23,7 @@ __device__ __forceinline__ float ldcg(const float *p) { return __ldcg(p); }
 __device__ __forceinline__ void stcg(float *p, float v) { __stcg(p, v); }
 
 // C[M x N] -= A[M x K] * B[N x K]^T, column-major; `lower` writes only row >= column.
-__device__ __noinline__ void update_nt(float *C, int64_t ldc, const float *A, int64_t lda, const float *B,
+static __device__ __noinline__ void update_nt(float *C, int64_t ldc, const float *A, int64_t lda, const float *B,
                                        int64_t ldb, int M, int N, int K, bool lower, float *smem) {
   float *As = smem;
   float *Bs = smem + 2 * BK * BM;
@@ -145,7 +145,7 @@ __device__ __forceinline__ void load_diag_block(const float *G, int64_t ld, int 
 }
 
 // POTRF on the nk x nk diagonal tile (FP32); returns 0 or the failing 1-based column.
-__device__ __noinline__ int potrf_tile(float *G, int64_t ld, int nk, float *smem) {
+static __device__ __noinline__ int potrf_tile(float *G, int64_t ld, int nk, float *smem) {
   float *Ds = smem + STAGE_FLOATS;
   float *Rinv = Ds + IB * DS_LD;
   __shared__ int s_fail;
@@ -196,7 +196,7 @@ __device__ __noinline__ int potrf_tile(float *G, int64_t ld, int nk, float *smem
 }
 
 // TRSM: X L^T = B in place on B (mb x nk).
-__device__ __noinline__ void trsm_tile(float *B, int64_t ldb, const float *L, int64_t ldl, int mb, int nk,
+static __device__ __noinline__ void trsm_tile(float *B, int64_t ldb, const float *L, int64_t ldl, int mb, int nk,
                                        float *smem) {
   float *Ds = smem + STAGE_FLOATS;
   float *Rinv = Ds + IB * DS_LD;

@@ -30,7 +30,7 @@ __device__ __forceinline__ void stcg(double *p, double v) { __stcg(p, v); }
 // C[M x N] -= A[M x K] * B[N x K]^T, column-major. With `lower`, only elements with
 // row >= column (relative to C) are written and blocks wholly above the diagonal skipped.
 // Called by all NT threads; ends with the block synchronised.
-__device__ __noinline__ void update_nt(double *C, int64_t ldc, const double *A, int64_t lda,
+static __device__ __noinline__ void update_nt(double *C, int64_t ldc, const double *A, int64_t lda,
                                        const double *B, int64_t ldb, int M, int N, int K,
                                        bool lower, double *smem) {
   double *As = smem;
@@ -161,7 +161,7 @@ __device__ __forceinline__ void load_diag_block(const double *G, int64_t ld, int
 
 // POTRF on the nk x nk diagonal tile G (in place, lower). Returns 0, or the 1-based column
 // inside the tile whose pivot is not positive (or NaN). Called by all threads.
-__device__ __noinline__ int potrf_tile(double *G, int64_t ld, int nk, double *smem) {
+static __device__ __noinline__ int potrf_tile(double *G, int64_t ld, int nk, double *smem) {
   double *Ds = smem + STAGE_DOUBLES;
   double *Rinv = Ds + IB * DS_LD;
   __shared__ int s_fail;
@@ -217,7 +217,7 @@ __device__ __noinline__ int potrf_tile(double *G, int64_t ld, int nk, double *sm
 }
 
 // TRSM: X L^T = B in place on B (mb x nk), L the nk x nk lower factor tile.
-__device__ __noinline__ void trsm_tile(double *B, int64_t ldb, const double *L, int64_t ldl,
+static __device__ __noinline__ void trsm_tile(double *B, int64_t ldb, const double *L, int64_t ldl,
                                        int mb, int nk, double *smem) {
   double *Ds = smem + STAGE_DOUBLES;
   double *Rinv = Ds + IB * DS_LD;
