@@ -60,6 +60,9 @@ def parse():
     p.add_argument("--mixed-n", type=int, default=16384)
     p.add_argument("--mixed-nrhs", type=int, default=16)
     p.add_argument("--mixed-steps", type=int, default=2)
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--batch", type=int, default=10000)
+    p.add_argument("--batched-steps", type=int, default=3)
     return p.parse_args()
 
 
@@ -282,6 +285,9 @@ def main():
     mixed = None
     if not args.no_mixed and rank == 0:
         mixed = run_mixed(args, chol, dev)
+    batched = None
+    if not args.no_batched and rank == 0:
+        batched = run_batched(args, chol, dev)
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         cpu = cpu_baseline(args)
@@ -294,7 +300,7 @@ def main():
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args),
             "factor_ms": round(fac_avg, 2), "solve_backward_error": berr,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "mixed_precision": mixed,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "mixed_precision": mixed, "batched": batched,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
                        "reasons": clk.get("reasons"), "samples": clk.get("samples"),
@@ -365,6 +371,72 @@ def run_mixed(args, chol, dev):
             "target_backward_error": 1e-14, "fp64_backward_error": e64, "mixed_backward_error": emx,
             "mixed_reported_backward_error": float(berr.item()), "iterations": int(iters.item()),
             "info": int(minfo.item()), "x_rel_diff_vs_fp64": rel}
+
+
+def run_batched(args, chol, dev):
+    """The batched configuration: --batch SPD matrices with orders uniform in [16, 512]
+    (A_m = sym(G G^T)/n + I), one right-hand side each, factored and solved by one persistent
+    launch, FP64 and FP32. The launch shape comes from the library's autotuner; each step
+    (restore the inputs, order + factor + solve) is one CUDA graph replay."""
+    import torch
+    import synth
+    orders = [int(n) for n in synth.batch_orders(args.batch, 16, 512, seed=args.seed)]
+    flops = sum(n ** 3 / 3.0 + 2.0 * n * n for n in orders)
+    out = {"workload": "%d SPD matrices, n uniform in [16, 512], 1 RHS each, one persistent launch per "
+                       "step under a CUDA graph" % len(orders), "flops_per_step": flops}
+    roffs, off = [], 0
+    for n in orders:
+        roffs.append(off)
+        off += n
+    for name, dtype in (("f64", torch.float64), ("f32", torch.float32)):
+        flat, offs = synth.gram_spd_batch(orders, seed=args.seed + 3, device=dev, dtype=dtype)
+        g = torch.Generator(device=dev).manual_seed(args.seed + 4)
+        rhs = torch.randn(off, generator=g, device=dev, dtype=torch.float64).to(dtype)
+        src = chol.Batch(flat, offs, orders, rhs, roffs)
+        scratch = chol.Batch(flat.clone(), offs, orders, rhs.clone(), roffs)
+        best, tune_ms = chol.batched_autotune(src, scratch)
+        del scratch
+        work = chol.Batch(flat.clone(), offs, orders, rhs.clone(), roffs)
+        stream = torch.cuda.Stream(dev)
+
+        def step():
+            work.flat.copy_(src.flat)
+            work.rhs_flat.copy_(src.rhs_flat)
+            chol.posv_batched(work, best, stream=stream)
+
+        with torch.cuda.stream(stream):
+            step()
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            step()
+        for _ in range(2):
+            graph.replay()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.batched_steps):
+            graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.batched_steps
+        bad = int((work.info != 0).sum().item())
+        berr = 0.0
+        for m in range(0, len(orders), max(1, len(orders) // 16)):
+            A = src.matrix(m).to(torch.float64)
+            b = src.rhs(m).to(torch.float64)
+            x = work.rhs(m).to(torch.float64)
+            r = b - A @ x
+            berr = max(berr, float(r.abs().max() / (A.abs().sum(1).max() * x.abs().max() + b.abs().max())))
+        out[name] = {"ms": round(ms, 3), "gflops": round(flops / ms / 1e6, 1),
+                     "matrices_per_s": round(len(orders) / ms * 1e3, 1), "failed": bad,
+                     "backward_error_sample_max": berr,
+                     "autotuned": {"workers_per_sm": best.workers_per_sm, "lpt_order": best.lpt_order,
+                                   "tuning_ms_best": round(tune_ms, 3)}}
+        del src, work, flat, rhs, graph
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_e2e(args, chol, A0, B0, o, dev):

@@ -48,6 +48,7 @@ typedef enum {
 /* j > 0: the leading minor of order j is not positive definite (pivot <= 0 or NaN). */
 #define CHOL_INFO_TIMEOUT (-1)      /* a bounded device wait expired; results are undefined */
 #define CHOL_INFO_QUEUE_FULL (-2)   /* internal: a ready queue overflowed (never expected) */
+#define CHOL_INFO_BAD_ARG (-3)      /* batched calls: this matrix's size or leading dimension is invalid */
 
 /* Ready-queue policies of the activate operation (Section 3). */
 typedef enum {
@@ -200,6 +201,38 @@ chol_status chol_solve_backward(int n, int nrhs, const double *dL, int lda, cons
 
 /* dDst = lower triangle of dSrc with the strict upper triangle zeroed (n x n, FP64). */
 chol_status chol_lower_copy(int n, const double *dSrc, int lds, double *dDst, int ldd, void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Batched factor + solve of many independent SPD matrices of uneven sizes in one persistent
+ * launch (not in the paper: its factorization applied to a batch). The batch is ordered on
+ * the device by decreasing order (largest first) and each worker block takes the next matrix
+ * from a counter, factors it with the blocked POTRF tile body and solves its right-hand
+ * side. No host synchronisation: the call can be captured into a CUDA graph.
+ *
+ * precision  CHOL_F64 (double matrices) or CHOL_F32 (float matrices).
+ * dN[batch]  orders, 0 <= n <= 4096 (device). dA[batch], dB[batch]: device arrays of device
+ *            pointers to column-major matrices (leading dimension dLda[m]) and right-hand-side
+ *            vectors; dB may be NULL (factor only) and entries of dB may be NULL.
+ * dInfo[batch] per-matrix info (0, j > 0 not positive definite, CHOL_INFO_BAD_ARG).
+ * bopts      launch shape (NULL = defaults); see chol_batched_autotune.
+ * dWork      chol_batched_workspace_size(batch) bytes.
+ */
+typedef struct {
+  int workers_per_sm;  /* worker blocks per SM: 1 or 2 */
+  int lpt_order;       /* 1: largest matrices first; 0: in the given order */
+} chol_batch_opts;
+void chol_batch_opts_default(chol_batch_opts *o);
+size_t chol_batched_workspace_size(int batch);
+chol_status chol_posv_batched(int precision, int batch, const int *dN, void *const *dA, const int *dLda,
+                              void *const *dB, int *dInfo, const chol_batch_opts *bopts, void *dWork,
+                              size_t work_bytes, void *stream);
+/* Autotuner: times every launch shape (workers per SM x order) on the given batch, copying
+ * the matrices dAsrc into dAscratch before each run (both arrays of device pointers with the
+ * same orders and leading dimensions), and writes the fastest shape to *best (and its time in
+ * ms to *best_ms). Synchronises the stream. */
+chol_status chol_batched_autotune(int precision, int batch, const int *dN, void *const *dAsrc,
+                                  void *const *dAscratch, const int *dLda, int *dInfo, void *dWork,
+                                  size_t work_bytes, chol_batch_opts *best, float *best_ms, void *stream);
 
 /* ---------------------------------------------------------------------------------------
  * Host-buffer convenience: factor and solve from host memory (LAPACK dposv semantics).

@@ -20,7 +20,7 @@ __all__ = [
     "lib", "ChOpts", "POLICIES", "opts", "colmajor", "factor", "solve", "trsm_sweep", "posv",
     "posv_host", "workspace_size", "solve_workspace_size", "num_workers", "trace", "factor_f32",
     "solve_refine", "refine_workspace_size", "cholesky_backward", "solve_backward", "lower",
-    "cholesky", "cholesky_solve", "solve_spd",
+    "cholesky", "cholesky_solve", "solve_spd", "BatchOpts", "Batch", "posv_batched", "batched_autotune",
     "dag_describe", "dag_bottom_levels", "sched_activate", "sched_activate_device",
     "CholeskyError",
 ]
@@ -81,6 +81,10 @@ _SIGNATURES = {
     "chol_solve_backward_workspace_size": (_SZ, [_I, _I]),
     "chol_solve_backward": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _SZ, _P]),
     "chol_lower_copy": (_I, [_I, _P, _I, _P, _I, _P]),
+    "chol_batch_opts_default": (None, [_P]),
+    "chol_batched_workspace_size": (_SZ, [_I]),
+    "chol_posv_batched": (_I, [_I, _I, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "chol_batched_autotune": (_I, [_I, _I, _P, _P, _P, _P, _P, _P, _SZ, _P, _P, _P]),
     "chol_posv_host_stage_size": (_SZ, [_I, _I, _OPTS]),
     "chol_posv_host": (_I, [_I, _I, _P, _I, _P, _I, _OPTS, _P, _SZ, _P, _P]),
     "chol_dag_task_count": (_LL, [_I]),
@@ -510,3 +514,73 @@ def solve_spd(A, B, nb=256, recompute=False):
     """Differentiable X = A^-1 B for symmetric positive definite A. With recompute=True the
     backward pass refactors A instead of keeping L."""
     return _SolveSPDFn.apply(A, B, nb, recompute)
+
+
+# ----------------------------------------------------------------------------------------
+# Batched factor + solve
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("workers_per_sm", ctypes.c_int), ("lpt_order", ctypes.c_int)]
+
+
+class Batch:
+    """Device description of a batch: a flat buffer of column-major matrices (lda = n) and
+    right-hand sides, with the pointer, order and leading-dimension arrays the C ABI takes."""
+
+    def __init__(self, flat, offsets, orders, rhs_flat=None, rhs_offsets=None):
+        self.flat, self.orders = flat, [int(n) for n in orders]
+        dev = flat.device
+        es = flat.element_size()
+        self.batch = len(self.orders)
+        self.N = torch.tensor(self.orders, dtype=torch.int32, device=dev)
+        self.lda = torch.tensor([max(1, n) for n in self.orders], dtype=torch.int32, device=dev)
+        self.A = torch.tensor([flat.data_ptr() + es * o for o in offsets], dtype=torch.int64, device=dev)
+        self.offsets = list(offsets)
+        self.rhs_flat, self.rhs_offsets = rhs_flat, rhs_offsets
+        self.B = None
+        if rhs_flat is not None:
+            self.B = torch.tensor([rhs_flat.data_ptr() + es * o for o in rhs_offsets], dtype=torch.int64,
+                                  device=dev)
+        self.info = torch.zeros(self.batch, dtype=torch.int32, device=dev)
+        self.work = _workspace(int(lib.chol_batched_workspace_size(self.batch)), dev)
+
+    def matrix(self, m):
+        n = self.orders[m]
+        return self.flat[self.offsets[m]:self.offsets[m] + n * n].view(n, n).t()
+
+    def rhs(self, m):
+        n = self.orders[m]
+        return self.rhs_flat[self.rhs_offsets[m]:self.rhs_offsets[m] + n]
+
+
+def _prec(flat):
+    if flat.dtype == torch.float64:
+        return 0
+    if flat.dtype == torch.float32:
+        return 1
+    raise ValueError("batched matrices must be float64 or float32")
+
+
+def posv_batched(batch, bopts=None, stream=None, factor_only=False):
+    """Factor every matrix of `batch` in place and (unless factor_only) solve its right-hand
+    side in place. Asynchronous; per-matrix info in batch.info."""
+    o = bopts if bopts is not None else BatchOpts()
+    if bopts is None:
+        lib.chol_batch_opts_default(ctypes.byref(o))
+    bptr = None if (factor_only or batch.B is None) else batch.B.data_ptr()
+    _check(lib.chol_posv_batched(_prec(batch.flat), batch.batch, batch.N.data_ptr(), batch.A.data_ptr(),
+                                 batch.lda.data_ptr(), bptr, batch.info.data_ptr(), ctypes.byref(o),
+                                 batch.work.data_ptr(), batch.work.numel(), _stream(stream)), "chol_posv_batched")
+    return batch.info
+
+
+def batched_autotune(batch, scratch, stream=None):
+    """Time every launch shape on `batch` (copied into `scratch`, a Batch with the same
+    orders) and return (BatchOpts, ms)."""
+    best = BatchOpts()
+    ms = ctypes.c_float(0.0)
+    _check(lib.chol_batched_autotune(_prec(batch.flat), batch.batch, batch.N.data_ptr(), batch.A.data_ptr(),
+                                     scratch.A.data_ptr(), batch.lda.data_ptr(), scratch.info.data_ptr(),
+                                     scratch.work.data_ptr(), scratch.work.numel(), ctypes.byref(best),
+                                     ctypes.byref(ms), _stream(stream)), "chol_batched_autotune")
+    return best, float(ms.value)

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libchol_gb300.so")
-SOURCES = ["csrc/adjoint.cu", "csrc/api.cu", "csrc/factor.cu", "csrc/solve.cu", "csrc/refine.cu"]
+SOURCES = ["csrc/adjoint.cu", "csrc/api.cu", "csrc/batched.cu", "csrc/factor.cu", "csrc/solve.cu", "csrc/refine.cu"]
 HEADERS = ["csrc/blockacc.cuh", "csrc/common.cuh", "csrc/dag.cuh", "csrc/internal.cuh", "csrc/sched.cuh", "csrc/tiles_f32.cuh",
            "csrc/tiles_f64.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

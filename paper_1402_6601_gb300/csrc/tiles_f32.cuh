@@ -157,24 +157,31 @@ static __device__ __noinline__ int potrf_tile(float *G, int64_t ld, int nk, floa
     if (tid == 0) s_fail = 0;
     __syncthreads();
     if (tid < 32) {
+      // lane r keeps row r of the block in registers (rows/columns past pb form an identity),
+      // the pivot column is scaled in place and broadcast by shuffles for the rank-1 update
       const int r = tid;
+      float x[IB];
+#pragma unroll
+      for (int c = 0; c < IB; ++c) x[c] = (r < pb && c <= r) ? Ds[r * DS_LD + c] : (r == c ? 1.f : 0.f);
       int fail = 0;
-      for (int j = 0; j < pb; ++j) {
-        const float s = Ds[j * DS_LD + j];
-        if (!(s > 0.f)) { fail = p + j + 1; break; }
-        const float ljj = sqrtf(s);
-        __syncwarp();
-        if (r == j) Ds[j * DS_LD + j] = ljj;
-        if (r > j && r < pb) Ds[r * DS_LD + j] = Ds[r * DS_LD + j] / ljj;
-        __syncwarp();
-        if (r > j && r < pb) {
-          const float lrj = Ds[r * DS_LD + j];
-          for (int c = j + 1; c <= r; ++c) Ds[r * DS_LD + c] = fmaf(-lrj, Ds[c * DS_LD + j], Ds[r * DS_LD + c]);
+#pragma unroll
+      for (int j = 0; j < IB; ++j) {
+        const float s = __shfl_sync(0xffffffffu, x[j], j);
+        if (!fail && !(s > 0.f)) fail = p + j + 1;  // the same s on every lane
+        const float ljj = sqrtf(s > 0.f ? s : 1.f);
+        const float lrj = r == j ? ljj : (r > j ? x[j] / ljj : x[j]);
+        x[j] = lrj;
+#pragma unroll
+        for (int c = j + 1; c < IB; ++c) {
+          const float lcj = __shfl_sync(0xffffffffu, lrj, c);
+          if (r >= c) x[c] = fmaf(-lrj, lcj, x[c]);
         }
-        __syncwarp();
       }
+#pragma unroll
+      for (int c = 0; c < IB; ++c)
+        if (r < pb && c <= r) Ds[r * DS_LD + c] = x[c];
       if (r == 0) s_fail = fail;
-      if (!fail && r < pb) Rinv[r] = 1.f / Ds[r * DS_LD + r];
+      if (!fail && r < pb) Rinv[r] = 1.f / x[r];
     }
     __syncthreads();
     if (s_fail) return s_fail;

@@ -114,3 +114,34 @@ def batch_orders(count, lo=16, hi=512, seed=0):
     """Orders of a batch of matrices, uniform on [lo, hi]."""
     rng = np.random.default_rng(seed)
     return rng.integers(lo, hi + 1, size=count).astype(np.int32)
+
+
+def gram_spd_batch(orders, seed=0, device="cpu", dtype=torch.float64):
+    """A batch of Gram matrices A_m = sym(G G^T)/n_m + I (recipe of gram_spd) packed
+    column-major one after the other in one flat tensor. Matrices of equal order are drawn
+    and multiplied together. Returns (flat, offsets) with offsets[m] the element offset of
+    matrix m."""
+    device = torch.device(device)
+    orders = [int(n) for n in orders]
+    offsets, off = [], 0
+    for n in orders:
+        offsets.append(off)
+        off += n * n
+    flat = torch.empty(max(off, 1), dtype=dtype, device=device)
+    g = _gen(seed, device)
+    by_n = {}
+    for m, n in enumerate(orders):
+        by_n.setdefault(n, []).append(m)
+    for n in sorted(by_n):
+        idx = by_n[n]
+        if n == 0:
+            continue
+        G = torch.randn(len(idx), n, n, generator=g, device=device, dtype=torch.float32)
+        S = torch.bmm(G, G.transpose(1, 2)).to(torch.float64)
+        A = (S + S.transpose(1, 2)) * (0.5 / n)
+        A.diagonal(dim1=1, dim2=2).add_(1.0)
+        A = A.to(dtype)
+        for q, m in enumerate(idx):
+            # symmetric, so the row-major copy of A is also its column-major storage
+            flat[offsets[m]:offsets[m] + n * n].copy_(A[q].reshape(-1))
+    return flat, offsets
