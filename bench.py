@@ -410,15 +410,16 @@ def run_batched(args, chol, dev):
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=stream):
             step()
-        for _ in range(2):
-            graph.replay()
-        torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.batched_steps):
-            graph.replay()
-        e1.record(stream)
+        with torch.cuda.stream(stream):  # replay() launches on the current stream
+            for _ in range(2):
+                graph.replay()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(args.batched_steps):
+                graph.replay()
+            e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / args.batched_steps
         bad = int((work.info != 0).sum().item())

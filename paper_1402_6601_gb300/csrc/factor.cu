@@ -88,8 +88,12 @@ static size_t sched_smem_bytes(int T, int W) {
   return b;
 }
 
+constexpr int TilesF64_SMEM = TILE_SMEM_BYTES;
+constexpr int TilesF32_SMEM = f32::PANEL_SMEM_BYTES > f32::TILE_SMEM_BYTES ? f32::PANEL_SMEM_BYTES
+                                                                         : f32::TILE_SMEM_BYTES;
+
 static size_t factor_smem_bytes(int prec, int T, int W) {
-  const size_t tiles = prec == PREC_F64 ? (size_t)TILE_SMEM_BYTES : (size_t)f32::TILE_SMEM_BYTES;
+  const size_t tiles = prec == PREC_F64 ? (size_t)TilesF64_SMEM : (size_t)TilesF32_SMEM;
   return std::max(tiles, sched_smem_bytes(T, W));
 }
 
@@ -392,9 +396,13 @@ struct TilesF64 {
 };
 struct TilesF32 {
   using T = float;
-  static constexpr int SMEM = f32::TILE_SMEM_BYTES;
+  static constexpr int SMEM = f32::PANEL_SMEM_BYTES > f32::TILE_SMEM_BYTES ? f32::PANEL_SMEM_BYTES
+                                                                            : f32::TILE_SMEM_BYTES;
   static constexpr int MIN_BLOCKS = 1;  // the 8x8 register tiles need more than 128 registers
-  __device__ static int potrf(T *G, int64_t ld, int nk, T *s) { return f32::potrf_tile(G, ld, nk, s); }
+  // POTRF is the head of the critical path: tiles up to 256 are factored in shared memory
+  __device__ static int potrf(T *G, int64_t ld, int nk, T *s) {
+    return nk <= f32::PANEL_MAX_N ? f32::potrf_tile_smem(G, ld, nk, s) : f32::potrf_tile(G, ld, nk, s);
+  }
   __device__ static void trsm(T *B, int64_t ldb, const T *L, int64_t ldl, int mb, int nk, T *s) {
     f32::trsm_tile(B, ldb, L, ldl, mb, nk, s);
   }
@@ -571,7 +579,7 @@ static int launch_workers(const Resolved &r, const DeviceInfo &di) {
   if (di.sms <= 0) return 1024;
   std::call_once(g_attr_once, [] {
     cudaFuncSetAttribute(factor_kernel<TilesF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    cudaFuncSetAttribute(factor_kernel<TilesF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(factor_kernel<TilesF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   });
   const size_t smem = factor_smem_bytes(r.prec, r.T, 2 * di.sms);
   int per_sm = 0;

@@ -92,17 +92,25 @@ static __device__ __noinline__ void update_nt(float *C, int64_t ldc, const float
         __syncthreads();
         buf ^= 1;
       }
+      // all loads of C first, then the stores: interleaved, every read would wait for the
+      // previous store (possible aliasing) and the epilogue would cost 64 L2 round trips
+      float cv[8][8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int c = bn + (j < 4 ? ty * 4 + j : 64 + ty * 4 + (j - 4));
-        if (c >= N) continue;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const int r = bm + (i < 4 ? tx * 4 + i : 64 + tx * 4 + (i - 4));
-          if (r < M && (!lower || r >= c)) {
-            float *cp = C + (int64_t)c * ldc + r;
-            stcg(cp, ldcg(cp) - acc[i][j]);
-          }
+          cv[i][j] = (c < N && r < M && (!lower || r >= c)) ? ldcg(C + (int64_t)c * ldc + r) : 0.f;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int c = bn + (j < 4 ? ty * 4 + j : 64 + ty * 4 + (j - 4));
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int r = bm + (i < 4 ? tx * 4 + i : 64 + tx * 4 + (i - 4));
+          if (c < N && r < M && (!lower || r >= c)) stcg(C + (int64_t)c * ldc + r, cv[i][j] - acc[i][j]);
         }
       }
     }
@@ -225,6 +233,170 @@ static __device__ __noinline__ void trsm_tile(float *B, int64_t ldb, const float
                 smem);
   }
   __syncthreads();
+}
+
+// ---------------------------------------------------------------------------------------
+// Shared-memory resident POTRF for tiles of order <= PANEL_MAX_N. The diagonal tasks form
+// the factorization's critical path, and the blocked version above spends its time in
+// latency: after each 32-column step it re-reads and re-writes the trailing tile through L2.
+// Here the lower triangle of the tile is read once into shared memory as 32 x 32 blocks, the
+// right-looking factorization runs there (diagonal block in warp 0's registers, the rows
+// below solved one per thread, the trailing blocks updated with 4 x 8 register tiles per
+// lane), and the factor is written back once.
+
+constexpr int PANEL_MAX_N = 256;
+constexpr int NBLK_MAX = PANEL_MAX_N / IB;  // 8 block rows
+constexpr int SB_LD = IB + 4;               // column-major 32 x 32 block, 16-byte aligned columns
+constexpr int SB_FLOATS = IB * SB_LD;
+constexpr int PANEL_SMEM_BYTES = (NBLK_MAX * (NBLK_MAX + 1) / 2 * SB_FLOATS + IB) * 4;
+
+// lower block (i, j), i >= j, of the shared-memory tile
+__device__ __forceinline__ float *sblk(float *S, int i, int j) { return S + (i * (i + 1) / 2 + j) * SB_FLOATS; }
+
+// Factor the 32 x 32 block Db (column-major, ld SB_LD) in warp 0's registers, lane r holding
+// row r; rows and columns at or past pb are an identity. Writes L and Rinv = 1 / diag(L).
+// Returns 0 or the 1-based failing column offset by p. Warp 0 only.
+__device__ __forceinline__ int warp_diag_factor_cm(float *Db, float *Rinv, int pb, int p) {
+  const int r = threadIdx.x;
+  float x[IB];
+#pragma unroll
+  for (int c = 0; c < IB; ++c) x[c] = (r < pb && c <= r) ? Db[c * SB_LD + r] : (r == c ? 1.f : 0.f);
+  int fail = 0;
+#pragma unroll
+  for (int j = 0; j < IB; ++j) {
+    const float s = __shfl_sync(0xffffffffu, x[j], j);
+    if (!fail && !(s > 0.f)) fail = p + j + 1;  // the same s on every lane
+    const float ljj = sqrtf(s > 0.f ? s : 1.f);
+    const float lrj = r == j ? ljj : (r > j ? x[j] / ljj : x[j]);
+    x[j] = lrj;
+#pragma unroll
+    for (int c = j + 1; c < IB; ++c) {
+      const float lcj = __shfl_sync(0xffffffffu, lrj, c);
+      if (r >= c) x[c] = fmaf(-lrj, lcj, x[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < IB; ++c)
+    if (c <= r) Db[c * SB_LD + r] = x[c];
+  Rinv[r] = 1.f / x[r];
+  return fail;
+}
+
+// POTRF of the nk x nk tile G (nk <= PANEL_MAX_N) in shared memory; returns 0 or the failing
+// 1-based column. Called by all threads.
+static __device__ __noinline__ int potrf_tile_smem(float *G, int64_t ld, int nk, float *smem) {
+  float *S = smem;
+  float *Rinv = smem + NBLK_MAX * (NBLK_MAX + 1) / 2 * SB_FLOATS;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nblk = (nk + IB - 1) / IB;
+  const int nlow = nblk * (nblk + 1) / 2;
+  // whole-column vectors of 4 rows can be moved as float4 when every column start is aligned
+  const bool vec = ((reinterpret_cast<uintptr_t>(G) | (uintptr_t)(ld * 4)) & 15) == 0;
+  // load: element (r, c) of block (i, j) is A(32i + r, 32j + c); entries outside the tile form
+  // an identity, entries above the diagonal are zero
+  for (int e = tid; e < nlow * IB * 8; e += NT) {
+    const int q = e & 7, c = (e >> 3) & (IB - 1), b = e >> 8;
+    int i = 0;
+    while ((i + 1) * (i + 2) / 2 <= b) ++i;
+    const int j = b - i * (i + 1) / 2;
+    const int gr = IB * i + 4 * q, gc = IB * j + c;
+    float v[4];
+    if (vec && gr + 3 < nk && gc < nk && (i > j || 4 * q >= c)) {
+      const float4 t = __ldcg(reinterpret_cast<const float4 *>(G + (int64_t)gc * ld + gr));
+      v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = gr + u;
+        v[u] = (r < nk && gc < nk) ? (r >= gc ? ldcg(G + (int64_t)gc * ld + r) : 0.f) : (r == gc ? 1.f : 0.f);
+      }
+    }
+    *reinterpret_cast<float4 *>(S + b * SB_FLOATS + c * SB_LD + 4 * q) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+  if (tid == 0) s_fail = 0;
+  __syncthreads();
+  for (int j = 0; j < nblk; ++j) {
+    const int pb = min(IB, nk - IB * j);
+    if (warp == 0) {
+      const int f = warp_diag_factor_cm(sblk(S, j, j), Rinv, pb, IB * j);
+      if (lane == 0 && f) s_fail = f;
+    }
+    __syncthreads();
+    if (s_fail) return s_fail;
+    const float *D = sblk(S, j, j);
+    const int below = nblk - j - 1;
+    // rows of the blocks below the diagonal block: x D^T = b, one row per thread
+    if (tid < below * IB) {
+      float *P = sblk(S, j + 1 + (tid >> 5), j) + lane;
+      float x[IB];
+#pragma unroll
+      for (int c = 0; c < IB; ++c) x[c] = P[c * SB_LD];
+#pragma unroll
+      for (int c = 0; c < IB; ++c) {
+        x[c] = quot(x[c], D[c * SB_LD + c], Rinv[c]);
+#pragma unroll
+        for (int m = c + 1; m < IB; ++m) x[m] = fmaf(-x[c], D[c * SB_LD + m], x[m]);
+      }
+#pragma unroll
+      for (int c = 0; c < IB; ++c) P[c * SB_LD] = x[c];
+    }
+    __syncthreads();
+    // trailing blocks (i, m), j < m <= i < nblk: C -= L(i, j) L(m, j)^T, one block per warp
+    // at a time; lane: rows 4 rg .. 4 rg + 3, columns 8 cg .. 8 cg + 7
+    const int npair = below * (below + 1) / 2;
+    const int rg = lane & 7, cg = lane >> 3;
+    for (int t = warp; t < npair; t += NT / 32) {
+      int ii = 0;
+      while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
+      const int i = j + 1 + ii, m = j + 1 + (t - ii * (ii + 1) / 2);
+      const float *Ai = sblk(S, i, j) + 4 * rg;
+      const float *Bm = sblk(S, m, j) + 8 * cg;
+      float *C = sblk(S, i, m) + 8 * cg * SB_LD + 4 * rg;
+      float acc[4][8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const float4 v = *reinterpret_cast<const float4 *>(C + c * SB_LD);
+        acc[0][c] = v.x; acc[1][c] = v.y; acc[2][c] = v.z; acc[3][c] = v.w;
+      }
+#pragma unroll 8
+      for (int k = 0; k < IB; ++k) {
+        const float4 a = *reinterpret_cast<const float4 *>(Ai + k * SB_LD);
+        const float4 b0 = *reinterpret_cast<const float4 *>(Bm + k * SB_LD);
+        const float4 b1 = *reinterpret_cast<const float4 *>(Bm + k * SB_LD + 4);
+        const float av[4] = {a.x, a.y, a.z, a.w};
+        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int c = 0; c < 8; ++c) acc[u][c] = fmaf(-av[u], bv[c], acc[u][c]);
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        *reinterpret_cast<float4 *>(C + c * SB_LD) = make_float4(acc[0][c], acc[1][c], acc[2][c], acc[3][c]);
+    }
+    __syncthreads();
+  }
+  // write the factor back: the lower triangle of the tile only
+  for (int e = tid; e < nlow * IB * 8; e += NT) {
+    const int q = e & 7, c = (e >> 3) & (IB - 1), b = e >> 8;
+    int i = 0;
+    while ((i + 1) * (i + 2) / 2 <= b) ++i;
+    const int j = b - i * (i + 1) / 2;
+    const int gr = IB * i + 4 * q, gc = IB * j + c;
+    if (gc >= nk) continue;
+    const float4 t = *reinterpret_cast<const float4 *>(S + b * SB_FLOATS + c * SB_LD + 4 * q);
+    if (vec && gr + 3 < nk && (i > j || 4 * q >= c)) {
+      __stcg(reinterpret_cast<float4 *>(G + (int64_t)gc * ld + gr), t);
+    } else {
+      const float v[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (gr + u < nk && gr + u >= gc) stcg(G + (int64_t)gc * ld + gr + u, v[u]);
+    }
+  }
+  __syncthreads();
+  return 0;
 }
 
 }  // namespace f32

@@ -99,17 +99,25 @@ static __device__ __noinline__ void update_nt(double *C, int64_t ldc, const doub
         __syncthreads();
         buf ^= 1;
       }
+      // loads of C before any store, so that they overlap instead of each waiting for the
+      // previous (possibly aliasing) store
+      double cv[4][4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int c = bn + ty + 16 * j;
-        if (c >= N) continue;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int r = bm + tx + 16 * i;
-          if (r < M && (!lower || r >= c)) {
-            double *cp = C + (int64_t)c * ldc + r;
-            stcg(cp, ldcg(cp) - acc[i][j]);
-          }
+          cv[i][j] = (c < N && r < M && (!lower || r >= c)) ? ldcg(C + (int64_t)c * ldc + r) : 0.0;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = bn + ty + 16 * j;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int r = bm + tx + 16 * i;
+          if (c < N && r < M && (!lower || r >= c)) stcg(C + (int64_t)c * ldc + r, cv[i][j] - acc[i][j]);
         }
       }
     }

@@ -26,7 +26,8 @@ def _f32(chol, A_np):
     return chol.colmajor(torch.from_numpy(np.ascontiguousarray(A_np)).to("cuda", torch.float32))
 
 
-@pytest.mark.parametrize("n,nb,policy", [(600, 64, "heft"), (700, 128, "dada"), (1030, 256, "steal")])
+@pytest.mark.parametrize("n,nb,policy", [(600, 64, "heft"), (700, 128, "dada"), (1030, 256, "steal"),
+                                         (1024, 256, "dada")])
 def test_f32_integer_factor_bitwise(chol, n, nb, policy):
     L, A = synth.integer_factor(n, seed=n)
     Ad = _f32(chol, A)
