@@ -399,12 +399,13 @@ struct TilesF32 {
   static constexpr int SMEM = f32::PANEL_SMEM_BYTES > f32::TILE_SMEM_BYTES ? f32::PANEL_SMEM_BYTES
                                                                             : f32::TILE_SMEM_BYTES;
   static constexpr int MIN_BLOCKS = 1;  // the 8x8 register tiles need more than 128 registers
-  // POTRF is the head of the critical path: tiles up to 256 are factored in shared memory
+  // POTRF and TRSM lie on the critical path: for tiles up to 256 they run latency-lean bodies
   __device__ static int potrf(T *G, int64_t ld, int nk, T *s) {
     return nk <= f32::PANEL_MAX_N ? f32::potrf_tile_smem(G, ld, nk, s) : f32::potrf_tile(G, ld, nk, s);
   }
   __device__ static void trsm(T *B, int64_t ldb, const T *L, int64_t ldl, int mb, int nk, T *s) {
-    f32::trsm_tile(B, ldb, L, ldl, mb, nk, s);
+    if (nk <= f32::PANEL_MAX_N) f32::trsm_tile_rows(B, ldb, L, ldl, mb, nk, s);
+    else f32::trsm_tile(B, ldb, L, ldl, mb, nk, s);
   }
   __device__ static void update(T *C, int64_t ldc, const T *A, int64_t lda, const T *B, int64_t ldb, int M,
                                 int N, int K, bool lower, T *s) {

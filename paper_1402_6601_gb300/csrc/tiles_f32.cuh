@@ -256,6 +256,12 @@ __device__ __forceinline__ float *sblk(float *S, int i, int j) { return S + (i *
 // Factor the 32 x 32 block Db (column-major, ld SB_LD) in warp 0's registers, lane r holding
 // row r; rows and columns at or past pb are an identity. Writes L and Rinv = 1 / diag(L).
 // Returns 0 or the 1-based failing column offset by p. Warp 0 only.
+//
+// The loop is one dependent chain per column, so it is kept short: the square root and the
+// correctly rounded reciprocal square root are taken side by side from the pivot, the
+// column is scaled by a corrected quotient, and every lane runs the same unpredicated
+// update (lanes above the diagonal compute values in the upper triangle that are never read
+// or stored).
 __device__ __forceinline__ int warp_diag_factor_cm(float *Db, float *Rinv, int pb, int p) {
   const int r = threadIdx.x;
   float x[IB];
@@ -266,19 +272,21 @@ __device__ __forceinline__ int warp_diag_factor_cm(float *Db, float *Rinv, int p
   for (int j = 0; j < IB; ++j) {
     const float s = __shfl_sync(0xffffffffu, x[j], j);
     if (!fail && !(s > 0.f)) fail = p + j + 1;  // the same s on every lane
-    const float ljj = sqrtf(s > 0.f ? s : 1.f);
-    const float lrj = r == j ? ljj : (r > j ? x[j] / ljj : x[j]);
+    const float sp = s > 0.f ? s : 1.f;
+    const float ljj = sqrtf(sp);
+    const float rj = __frsqrt_rn(sp);
+    const float lrj = r == j ? ljj : quot(x[j], ljj, rj);
     x[j] = lrj;
 #pragma unroll
-    for (int c = j + 1; c < IB; ++c) {
-      const float lcj = __shfl_sync(0xffffffffu, lrj, c);
-      if (r >= c) x[c] = fmaf(-lrj, lcj, x[c]);
-    }
+    for (int c = j + 1; c < IB; ++c) x[c] = fmaf(-lrj, __shfl_sync(0xffffffffu, lrj, c), x[c]);
   }
 #pragma unroll
   for (int c = 0; c < IB; ++c)
     if (c <= r) Db[c * SB_LD + r] = x[c];
-  Rinv[r] = 1.f / x[r];
+  float d = x[0];
+#pragma unroll
+  for (int c = 1; c < IB; ++c) d = r == c ? x[c] : d;
+  Rinv[r] = __frcp_rn(d);
   return fail;
 }
 
@@ -335,8 +343,15 @@ static __device__ __noinline__ int potrf_tile_smem(float *G, int64_t ld, int nk,
 #pragma unroll
       for (int c = 0; c < IB; ++c) {
         x[c] = quot(x[c], D[c * SB_LD + c], Rinv[c]);
+        // column c of D below the diagonal, four rows per (broadcast) vector load
 #pragma unroll
-        for (int m = c + 1; m < IB; ++m) x[m] = fmaf(-x[c], D[c * SB_LD + m], x[m]);
+        for (int m4 = (c + 1) & ~3; m4 < IB; m4 += 4) {
+          const float4 d = *reinterpret_cast<const float4 *>(D + c * SB_LD + m4);
+          if (m4 > c) x[m4] = fmaf(-x[c], d.x, x[m4]);
+          if (m4 + 1 > c) x[m4 + 1] = fmaf(-x[c], d.y, x[m4 + 1]);
+          if (m4 + 2 > c) x[m4 + 2] = fmaf(-x[c], d.z, x[m4 + 2]);
+          x[m4 + 3] = fmaf(-x[c], d.w, x[m4 + 3]);
+        }
       }
 #pragma unroll
       for (int c = 0; c < IB; ++c) P[c * SB_LD] = x[c];
@@ -397,6 +412,73 @@ static __device__ __noinline__ int potrf_tile_smem(float *G, int64_t ld, int nk,
   }
   __syncthreads();
   return 0;
+}
+
+// TRSM X L^T = B in place (B: mb x nk, L: nk x nk lower, nk <= PANEL_MAX_N), left-looking
+// by 32-column blocks with one row of B per thread. For block j0 the thread keeps its 32
+// right-hand values in registers, applies the earlier columns of X (its own row, written by
+// itself in earlier blocks and read back from L2) against rows j0.. of L staged in shared
+// memory, then solves the 32 x 32 diagonal block in registers. The contraction is one long
+// register-resident stream per thread instead of block-wide updates with a 32-deep k, and
+// a column block costs one barrier pair.
+constexpr int TR_LD = IB + 4;
+constexpr int TRSM_ROWS_SMEM_BYTES = (PANEL_MAX_N * TR_LD + IB) * 4;
+
+static __device__ __noinline__ void trsm_tile_rows(float *B, int64_t ldb, const float *L, int64_t ldl, int mb,
+                                                   int nk, float *smem) {
+  float *Lp = smem;  // Lp[k * TR_LD + c] = L(j0 + c, k), zero above the diagonal, identity padding
+  float *Rinv = smem + PANEL_MAX_N * TR_LD;
+  const int tid = threadIdx.x;
+  for (int j0 = 0; j0 < nk; j0 += IB) {
+    const int jb = min(IB, nk - j0);
+    __syncthreads();  // the previous block is done with Lp
+    for (int e = tid; e < (j0 + IB) * IB; e += NT) {
+      const int c = e & (IB - 1), k = e >> 5;
+      Lp[k * TR_LD + c] =
+          (c < jb && k <= j0 + c) ? ldcg(L + (int64_t)k * ldl + j0 + c) : (k == j0 + c ? 1.f : 0.f);
+    }
+    if (tid < IB) Rinv[tid] = tid < jb ? __frcp_rn(ldcg(L + (int64_t)(j0 + tid) * ldl + j0 + tid)) : 1.f;
+    __syncthreads();
+    for (int r = tid; r < mb; r += NT) {
+      float acc[IB];
+#pragma unroll
+      for (int c = 0; c < IB; ++c) acc[c] = c < jb ? ldcg(B + (int64_t)(j0 + c) * ldb + r) : 0.f;
+      for (int k0 = 0; k0 < j0; k0 += 8) {
+        float xk[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) xk[u] = ldcg(B + (int64_t)(k0 + u) * ldb + r);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+#pragma unroll
+          for (int c4 = 0; c4 < IB; c4 += 4) {
+            const float4 l = *reinterpret_cast<const float4 *>(Lp + (k0 + u) * TR_LD + c4);
+            acc[c4] = fmaf(-xk[u], l.x, acc[c4]);
+            acc[c4 + 1] = fmaf(-xk[u], l.y, acc[c4 + 1]);
+            acc[c4 + 2] = fmaf(-xk[u], l.z, acc[c4 + 2]);
+            acc[c4 + 3] = fmaf(-xk[u], l.w, acc[c4 + 3]);
+          }
+        }
+      }
+      // x D^T = acc with D(c, m) = Lp[(j0 + m) * TR_LD + c]
+      const float *D = Lp + j0 * TR_LD;
+#pragma unroll
+      for (int m = 0; m < IB; ++m) {
+        acc[m] = quot(acc[m], D[m * TR_LD + m], Rinv[m]);
+#pragma unroll
+        for (int c4 = (m + 1) & ~3; c4 < IB; c4 += 4) {
+          const float4 d = *reinterpret_cast<const float4 *>(D + m * TR_LD + c4);
+          if (c4 > m) acc[c4] = fmaf(-acc[m], d.x, acc[c4]);
+          if (c4 + 1 > m) acc[c4 + 1] = fmaf(-acc[m], d.y, acc[c4 + 1]);
+          if (c4 + 2 > m) acc[c4 + 2] = fmaf(-acc[m], d.z, acc[c4 + 2]);
+          acc[c4 + 3] = fmaf(-acc[m], d.w, acc[c4 + 3]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < IB; ++c)
+        if (c < jb) stcg(B + (int64_t)(j0 + c) * ldb + r, acc[c]);
+    }
+  }
+  __syncthreads();
 }
 
 }  // namespace f32

@@ -4,7 +4,8 @@ FP32 factor: integer data stays exact in FP32 while every intermediate is an int
 2^24 (here |a_ij| <= 64 n), so L must come back bitwise; on Gram matrices (kappa <= 5) the
 FP32 factor must match the FP64 oracle within relative Frobenius 2e-5 (~ n u_32 growth).
 Refinement: the backward error must reach 1e-14 (the accuracy target of the FP64 path) on
-matrices with kappa = 1e6, and X must match the oracle's FP64 solution within kappa * 1e-15.
+matrices with kappa = 1e6, and X must match the oracle's FP64 solution within kappa * 1e-14
+(forward error <= kappa * backward error).
 """
 import numpy as np
 import pytest
@@ -62,8 +63,10 @@ def test_refine_reaches_fp64_backward_error(chol, n, nrhs, nb):
     assert eta <= 1e-14, (eta, int(iters.item()))
     assert float(berr.item()) <= 1e-14
     assert 1 <= int(iters.item()) <= 40
+    # refinement stops at backward error eta <= 1e-14, so the forward error is only bounded by
+    # kappa(A) * eta (the standard perturbation bound for A x = b): 1e6 * 1e-14
     Xref = oracle.solve(oracle.factor(A), B)
-    assert oracle.rel_frobenius(Xh, Xref) <= 1e6 * 1e-15
+    assert oracle.rel_frobenius(Xh, Xref) <= 1e6 * 1e-14
     # inputs untouched
     np.testing.assert_array_equal(Bd.cpu().numpy(), B)
     np.testing.assert_array_equal(Ad.cpu().numpy(), A)
