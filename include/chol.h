@@ -150,16 +150,35 @@ chol_status chol_trsm_sweep(int uplo_t, int n, int nrhs, const double *dL, int l
  * that factors A in FP32 and wins the accuracy back by iterative refinement whose residual
  * r = b - A x and update x += d run in FP64 (classical iterative refinement).
  */
-typedef enum { CHOL_F64 = 0, CHOL_F32 = 1, CHOL_BF16 = 2 } chol_precision;
+typedef enum {
+  CHOL_F64 = 0,    /* FP64 (DFMA) tile bodies */
+  CHOL_F32 = 1,    /* FP32 (FFMA) tile bodies */
+  CHOL_BF16 = 2,   /* FP32 storage; SYRK/GEMM tile updates on the tensor cores (tcgen05) with
+                      BF16 operands (8-bit significands) and FP32 accumulation; POTRF/TRSM FP32 */
+  CHOL_BF16X3 = 3  /* as CHOL_BF16, but each FP32 operand is split into three BF16 terms
+                      t0 + t1 + t2 and the six products t_i t_j (i + j <= 2) are accumulated
+                      in FP32: an FP32-accurate tile update on the tensor cores */
+} chol_precision;
 
 /* chol_factor on an FP32 matrix (same task graph, scheduler, options and workspace size). */
 chol_status chol_factor_f32(int n, float *dA, int lda, const chol_opts *opts, void *dWork,
                             size_t work_bytes, int *dInfo, void *stream);
 
+/* chol_factor_f32 with the tile bodies of `precision` (CHOL_F32, CHOL_BF16 or CHOL_BF16X3;
+ * others return CHOL_ERR_INVALID_ARG). Same workspace size. A wait of the tensor-core update
+ * that exceeds its 2 s limit ends the call with *dInfo = CHOL_INFO_TIMEOUT. */
+chol_status chol_factor_lowp(int precision, int n, float *dA, int lda, const chol_opts *opts, void *dWork,
+                             size_t work_bytes, int *dInfo, void *stream);
+
 /* Solve A X = B to a normwise backward error <= tol (Rigal-Gaches, infinity norm, maximised
- * over the right-hand sides) with a factor in `low_precision` (CHOL_F32; others return
- * CHOL_ERR_UNSUPPORTED) and at most max_iter refinement steps (the first low-precision
- * solve counts as one).
+ * over the right-hand sides) with a factor in `low_precision` (CHOL_F32, CHOL_BF16 or
+ * CHOL_BF16X3; others return CHOL_ERR_UNSUPPORTED) and at most max_iter refinement steps (the
+ * first low-precision solve counts as one). The BF16 forms factor the diagonally scaled
+ * matrix D^-1/2 A D^-1/2 (D = diag A, so every diagonal entry is 1 and every entry is in
+ * [-1, 1]) and unscale each correction. Classical refinement converges when kappa(A) times
+ * the factor's relative backward error is below 1: with plain BF16 operands (u = 2^-8) that
+ * holds only for well-conditioned A; the steps are then taken to max_iter and *dBerr reports
+ * the backward error reached.
  * dA    n x n FP64, lower triangle read (A is symmetric); not modified.
  * dB    n x nrhs FP64 (ldb), not modified; dX n x nrhs FP64 (ldx), overwritten by X.
  * opts  options of the low-precision factorization (tile size, policy, ...), may be NULL.

@@ -74,6 +74,7 @@ _SIGNATURES = {
     "chol_trsm_sweep": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _SZ, _P, _P]),
     "chol_solve_noalloc": (_I, [_I, _I, _P, _I, _P, _I, _P, _P]),
     "chol_factor_f32": (_I, [_I, _P, _I, _OPTS, _P, _SZ, _P, _P]),
+    "chol_factor_lowp": (_I, [_I, _I, _P, _I, _OPTS, _P, _SZ, _P, _P]),
     "chol_solve_refine_workspace_size": (_SZ, [_I, _I, _OPTS]),
     "chol_solve_refine": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _I, _D, _I, _OPTS, _P, _SZ, _P, _P, _P, _P]),
     "chol_backward_workspace_size": (_SZ, [_I]),
@@ -213,9 +214,17 @@ def factor(A, o=None, work=None, info=None, stream=None, check=False):
     return info, work
 
 
-def factor_f32(A, o=None, work=None, info=None, stream=None, check=False):
-    """FP32 tile Cholesky in place on a column-major float32 CUDA tensor."""
+# precisions of the low-precision factor (chol_precision)
+F64, F32, BF16, BF16X3 = 0, 1, 2, 3
+_PREC = {"f32": F32, "bf16": BF16, "bf16x3": BF16X3, F32: F32, BF16: BF16, BF16X3: BF16X3}
+
+
+def factor_f32(A, o=None, work=None, info=None, stream=None, check=False, precision="f32"):
+    """FP32-storage tile Cholesky in place on a column-major float32 CUDA tensor. precision:
+    "f32" (FFMA tile bodies), "bf16" (tensor-core SYRK/GEMM with BF16 operands, FP32
+    accumulation) or "bf16x3" (three BF16 operand terms: FP32-accurate tensor-core updates)."""
     o = o or opts()
+    prec = _PREC[precision]
     n = A.shape[0]
     if not (A.is_cuda and A.dtype == torch.float32 and A.dim() == 2 and A.shape[1] == n):
         raise ValueError("A must be a square float32 CUDA tensor")
@@ -226,8 +235,8 @@ def factor_f32(A, o=None, work=None, info=None, stream=None, check=False):
         work = _workspace(workspace_size(n, o), A.device)
     if info is None:
         info = torch.zeros(1, dtype=torch.int32, device=A.device)
-    _check(lib.chol_factor_f32(n, A.data_ptr(), lda, ctypes.byref(o), work.data_ptr(), work.numel(),
-                               info.data_ptr(), _stream(stream)), "chol_factor_f32")
+    _check(lib.chol_factor_lowp(prec, n, A.data_ptr(), lda, ctypes.byref(o), work.data_ptr(), work.numel(),
+                                info.data_ptr(), _stream(stream)), "chol_factor_lowp")
     if check and int(info.item()) != 0:
         raise CholeskyError("chol_factor_f32: info = %d" % int(info.item()))
     return info, work
@@ -238,10 +247,11 @@ def refine_workspace_size(n, nrhs, o=None):
     return int(lib.chol_solve_refine_workspace_size(n, nrhs, ctypes.byref(o)))
 
 
-def solve_refine(A, B, X=None, tol=1e-14, max_iter=30, o=None, work=None, stream=None):
-    """Mixed-precision solve (FP32 factor, FP64 refinement). Returns (X, info, iters, berr)
-    as device tensors (no synchronisation)."""
+def solve_refine(A, B, X=None, tol=1e-14, max_iter=30, o=None, work=None, stream=None, precision="f32"):
+    """Mixed-precision solve (low-precision factor: "f32", "bf16" or "bf16x3"; FP64
+    refinement). Returns (X, info, iters, berr) as device tensors (no synchronisation)."""
     o = o or opts()
+    prec = _PREC[precision]
     n = A.shape[0]
     lda = _check_matrix(A, "A")
     ldb = _check_matrix(B, "B")
@@ -254,7 +264,7 @@ def solve_refine(A, B, X=None, tol=1e-14, max_iter=30, o=None, work=None, stream
     info = torch.zeros(1, dtype=torch.int32, device=A.device)
     iters = torch.zeros(1, dtype=torch.int32, device=A.device)
     berr = torch.zeros(1, dtype=torch.float64, device=A.device)
-    _check(lib.chol_solve_refine(n, nrhs, A.data_ptr(), lda, B.data_ptr(), ldb, X.data_ptr(), ldx, 1, tol,
+    _check(lib.chol_solve_refine(n, nrhs, A.data_ptr(), lda, B.data_ptr(), ldb, X.data_ptr(), ldx, prec, tol,
                                  max_iter, ctypes.byref(o), work.data_ptr(), work.numel(), info.data_ptr(),
                                  iters.data_ptr(), berr.data_ptr(), _stream(stream)), "chol_solve_refine")
     return X, info, iters, berr

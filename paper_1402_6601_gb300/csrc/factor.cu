@@ -28,6 +28,7 @@
 #include "internal.cuh"
 #include "sched.cuh"
 #include "tiles_f32.cuh"
+#include "tiles_tc.cuh"
 #include "tiles_f64.cuh"
 
 namespace chol {
@@ -88,14 +89,7 @@ static size_t sched_smem_bytes(int T, int W) {
   return b;
 }
 
-constexpr int TilesF64_SMEM = TILE_SMEM_BYTES;
-constexpr int TilesF32_SMEM = f32::PANEL_SMEM_BYTES > f32::TILE_SMEM_BYTES ? f32::PANEL_SMEM_BYTES
-                                                                         : f32::TILE_SMEM_BYTES;
 
-static size_t factor_smem_bytes(int prec, int T, int W) {
-  const size_t tiles = prec == PREC_F64 ? (size_t)TilesF64_SMEM : (size_t)TilesF32_SMEM;
-  return std::max(tiles, sched_smem_bytes(T, W));
-}
 
 static Layout make_layout(int n, const Resolved &r, int W) {
   Layout L;
@@ -389,10 +383,13 @@ struct TilesF64 {
   __device__ static void trsm(T *B, int64_t ldb, const T *L, int64_t ldl, int mb, int nk, T *s) {
     trsm_tile(B, ldb, L, ldl, mb, nk, s);
   }
-  __device__ static void update(T *C, int64_t ldc, const T *A, int64_t lda, const T *B, int64_t ldb, int M,
-                                int N, int K, bool lower, T *s) {
+  __device__ static int update(T *C, int64_t ldc, const T *A, int64_t lda, const T *B, int64_t ldb, int M,
+                               int N, int K, bool lower, T *s) {
     update_nt(C, ldc, A, lda, B, ldb, M, N, K, lower, s);
+    return 0;
   }
+  __device__ static void begin() {}
+  __device__ static void end() {}
 };
 struct TilesF32 {
   using T = float;
@@ -407,10 +404,32 @@ struct TilesF32 {
     if (nk <= f32::PANEL_MAX_N) f32::trsm_tile_rows(B, ldb, L, ldl, mb, nk, s);
     else f32::trsm_tile(B, ldb, L, ldl, mb, nk, s);
   }
-  __device__ static void update(T *C, int64_t ldc, const T *A, int64_t lda, const T *B, int64_t ldb, int M,
-                                int N, int K, bool lower, T *s) {
+  __device__ static int update(T *C, int64_t ldc, const T *A, int64_t lda, const T *B, int64_t ldb, int M,
+                               int N, int K, bool lower, T *s) {
     f32::update_nt(C, ldc, A, lda, B, ldb, M, N, K, lower, s);
+    return 0;
   }
+  __device__ static void begin() {}
+  __device__ static void end() {}
+};
+// FP32 storage and FP32 POTRF/TRSM; SYRK/GEMM on the tensor cores with NTERM BF16 operand
+// terms. The accumulators (all 512 TMEM columns) are held by the worker for the whole launch.
+template <int NTERM>
+struct TilesTC : TilesF32 {
+  static constexpr int SMEM = tc::Cfg<NTERM>::SMEM > TilesF32::SMEM ? tc::Cfg<NTERM>::SMEM : TilesF32::SMEM;
+  // one worker per SM: a second one would wait in tcgen05.alloc for columns the first holds
+  static_assert(2 * SMEM > 228 * 1024, "tensor-core workers must not share an SM");
+  __device__ static tc::State &state() {
+    __shared__ tc::State st;
+    return st;
+  }
+  __device__ static int update(T *C, int64_t ldc, const T *A, int64_t lda, const T *B, int64_t ldb, int M,
+                               int N, int K, bool lower, T *s) {
+    return tc::update_nt<NTERM>(C, ldc, A, lda, B, ldb, M, N, K, lower, reinterpret_cast<unsigned char *>(s),
+                                state());
+  }
+  __device__ static void begin() { tc::begin(state()); }
+  __device__ static void end() { tc::end(state()); }
 };
 
 // Run one tile task with the whole block. Returns 0 or a 1-based failing global column.
@@ -426,14 +445,18 @@ __device__ int run_task(const FactorArgs &a, const TaskDesc &d, typename P::T *s
       P::trsm(tile_ptr<T>(a, d.i, d.k), a.lda, tile_ptr<T>(a, d.k, d.k), a.lda, tile_dim(a, d.i),
               tile_dim(a, d.k), smem);
       return 0;
-    case K_SYRK:
-      P::update(tile_ptr<T>(a, d.i, d.i), a.lda, tile_ptr<T>(a, d.i, d.k), a.lda, tile_ptr<T>(a, d.i, d.k),
-                a.lda, tile_dim(a, d.i), tile_dim(a, d.i), tile_dim(a, d.k), true, smem);
-      return 0;
+    case K_SYRK:  // a nonzero return is an expired wait inside the tile update
+      return P::update(tile_ptr<T>(a, d.i, d.i), a.lda, tile_ptr<T>(a, d.i, d.k), a.lda,
+                       tile_ptr<T>(a, d.i, d.k), a.lda, tile_dim(a, d.i), tile_dim(a, d.i), tile_dim(a, d.k),
+                       true, smem)
+                 ? CHOL_INFO_TIMEOUT
+                 : 0;
     default:
-      P::update(tile_ptr<T>(a, d.i, d.j), a.lda, tile_ptr<T>(a, d.i, d.k), a.lda, tile_ptr<T>(a, d.j, d.k),
-                a.lda, tile_dim(a, d.i), tile_dim(a, d.j), tile_dim(a, d.k), false, smem);
-      return 0;
+      return P::update(tile_ptr<T>(a, d.i, d.j), a.lda, tile_ptr<T>(a, d.i, d.k), a.lda,
+                       tile_ptr<T>(a, d.j, d.k), a.lda, tile_dim(a, d.i), tile_dim(a, d.j), tile_dim(a, d.k),
+                       false, smem)
+                 ? CHOL_INFO_TIMEOUT
+                 : 0;
   }
 }
 
@@ -447,6 +470,7 @@ __global__ void __launch_bounds__(NT, P::MIN_BLOCKS) factor_kernel(const __grid_
   const int wid = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t rng = 0x9E3779B9u ^ ((uint32_t)wid * 0x85EBCA6Bu + 1u);
+  P::begin();
   if (wid == 0 && threadIdx.x == 0) {
     const uint32_t key = a.queue_order == 1 ? 0xFFFFFFFFu : prio_key(a.bl[0]);
     atomicAdd(&a.qcost[0], (unsigned long long)a.cost[K_POTRF]);
@@ -493,6 +517,7 @@ __global__ void __launch_bounds__(NT, P::MIN_BLOCKS) factor_kernel(const __grid_
       }
     }
   }
+  P::end();
 }
 
 __global__ void init_kernel(int T, int64_t ntasks, int *cnt, int *owner, int64_t hold_task) {
@@ -532,6 +557,26 @@ __global__ void copy_info_kernel(const Ctrl *ctrl, int *dInfo) {
 
 static std::once_flag g_attr_once;
 
+static size_t tile_smem_bytes(int prec) {
+  switch (prec) {
+    case PREC_F64: return TilesF64::SMEM;
+    case PREC_F32: return TilesF32::SMEM;
+    case PREC_BF16: return TilesTC<1>::SMEM;
+    default: return TilesTC<3>::SMEM;
+  }
+}
+
+static size_t factor_smem_bytes(int prec, int T, int W) { return std::max(tile_smem_bytes(prec), sched_smem_bytes(T, W)); }
+
+static const void *kernel_for(int prec) {
+  switch (prec) {
+    case PREC_F64: return (const void *)factor_kernel<TilesF64>;
+    case PREC_F32: return (const void *)factor_kernel<TilesF32>;
+    case PREC_BF16: return (const void *)factor_kernel<TilesTC<1>>;
+    default: return (const void *)factor_kernel<TilesTC<3>>;
+  }
+}
+
 static bool resolve(int n, const chol_opts *opts, Resolved &r, int prec = PREC_F64) {
   chol_opts o;
   chol_opts_default(&o);
@@ -554,9 +599,10 @@ static bool resolve(int n, const chol_opts *opts, Resolved &r, int prec = PREC_F
   r.max_iter = o.dada_max_iter > 0 ? o.dada_max_iter : 16;
   r.eps = o.dada_eps > 0.0 ? o.dada_eps : 0.01;
   const double nb = (double)r.nb;
-  // predicted rate per worker in GFLOP/s (= flop per ns): FP64 DFMA ~7.5 per SM, FP32 FFMA
-  // tile bodies ~300 per SM
-  const double rate = (prec == PREC_F64 ? 7.5 : 300.0) / (double)r.wps;
+  // predicted rate per worker (GFLOP/s = flop per ns): FP64 DFMA ~7.5 per SM, FP32 FFMA tile
+  // bodies ~300, tensor-core updates ~700 (one BF16 term) and ~500 (three terms)
+  const double per_sm = prec == PREC_F64 ? 7.5 : prec == PREC_F32 ? 300.0 : prec == PREC_BF16 ? 700.0 : 500.0;
+  const double rate = per_sm / (double)r.wps;
   const double flops[4] = {nb * nb * nb / 3.0, nb * nb * nb, nb * nb * nb, 2.0 * nb * nb * nb};
   for (int k = 0; k < 4; ++k) {
     if (o.cost_ns[k] < 0) return false;
@@ -581,10 +627,12 @@ static int launch_workers(const Resolved &r, const DeviceInfo &di) {
   std::call_once(g_attr_once, [] {
     cudaFuncSetAttribute(factor_kernel<TilesF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     cudaFuncSetAttribute(factor_kernel<TilesF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(factor_kernel<TilesTC<1>>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(factor_kernel<TilesTC<3>>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   });
   const size_t smem = factor_smem_bytes(r.prec, r.T, 2 * di.sms);
   int per_sm = 0;
-  const void *fn = r.prec == PREC_F64 ? (const void *)factor_kernel<TilesF64> : (const void *)factor_kernel<TilesF32>;
+  const void *fn = kernel_for(r.prec);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, smem) != cudaSuccess)
     per_sm = 1;
   per_sm = std::max(1, std::min(per_sm, r.wps));
@@ -600,7 +648,7 @@ using namespace chol;
 extern "C" size_t chol_factor_workspace_size(int n, const chol_opts *opts) {
   // the same workspace serves both precisions of the factor
   size_t best = 0;
-  for (int prec = PREC_F64; prec <= PREC_F32; ++prec) {
+  for (int prec = PREC_F64; prec <= PREC_BF16X3; ++prec) {
     Resolved r;
     if (n < 0 || !resolve(n, opts, r, prec)) return 0;
     const DeviceInfo di = current_device_info();
@@ -683,7 +731,7 @@ chol_status factor_impl(int prec, int n, void *dA, int lda, const chol_opts *opt
   }
   const size_t smem = factor_smem_bytes(prec, r.T, W);
   void *args[] = {(void *)&a};
-  const void *fn = prec == PREC_F64 ? (const void *)factor_kernel<TilesF64> : (const void *)factor_kernel<TilesF32>;
+  const void *fn = kernel_for(prec);
   CHOL_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(W), dim3(NT), args, smem, s));
   copy_info_kernel<<<1, 32, 0, s>>>(a.ctrl, dInfo);
   CHOL_CUDA_TRY(cudaGetLastError());
@@ -695,6 +743,16 @@ chol_status factor_impl(int prec, int n, void *dA, int lda, const chol_opts *opt
 extern "C" chol_status chol_factor(int n, double *dA, int lda, const chol_opts *opts, void *dWork,
                                    size_t work_bytes, int *dInfo, void *stream) {
   return factor_impl(PREC_F64, n, dA, lda, opts, dWork, work_bytes, dInfo, stream);
+}
+
+extern "C" chol_status chol_factor_lowp(int precision, int n, float *dA, int lda, const chol_opts *opts,
+                                        void *dWork, size_t work_bytes, int *dInfo, void *stream) {
+  const int prec = precision == CHOL_F32 ? PREC_F32
+                   : precision == CHOL_BF16 ? PREC_BF16
+                   : precision == CHOL_BF16X3 ? PREC_BF16X3
+                                              : -1;
+  if (prec < 0) return CHOL_ERR_INVALID_ARG;
+  return factor_impl(prec, n, dA, lda, opts, dWork, work_bytes, dInfo, stream);
 }
 
 extern "C" chol_status chol_factor_f32(int n, float *dA, int lda, const chol_opts *opts, void *dWork,

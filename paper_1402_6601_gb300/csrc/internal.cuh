@@ -6,7 +6,9 @@
 
 namespace chol {
 
-enum { PREC_F64 = 0, PREC_F32 = 1 };
+// tile bodies of the factor: FP64 DFMA, FP32 FFMA, FP32 with tensor-core BF16 updates (one or
+// three operand terms)
+enum { PREC_F64 = 0, PREC_F32 = 1, PREC_BF16 = 2, PREC_BF16X3 = 3 };
 
 // Tile Cholesky of the n x n matrix at dA (double for PREC_F64, float for PREC_F32).
 chol_status factor_impl(int prec, int n, void *dA, int lda, const chol_opts *opts, void *dWork,

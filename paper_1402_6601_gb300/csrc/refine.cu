@@ -1,4 +1,5 @@
-// Mixed-precision solve: FP32 tile Cholesky of A, then iterative refinement whose residual
+// Mixed-precision solve: low-precision tile Cholesky of A (FP32 FFMA, or FP32 with tensor-core
+// BF16 updates of the diagonally scaled matrix), then iterative refinement whose residual
 // r = b - A x and update x += d run in FP64 (classical iterative refinement: each step
 // solves A d = r with the low-precision factor). Not in the paper; it reuses the paper's
 // factorization (same task graph, scheduler and policies) at a lower precision.
@@ -37,11 +38,23 @@ __device__ __forceinline__ void atomic_max_nonneg(double *p, double v) {
   atomicMax(reinterpret_cast<unsigned long long *>(p), (unsigned long long)__double_as_longlong(v));
 }
 
-__global__ void convert_lower_kernel(const double *A, int64_t lda, float *A32, int64_t lda32, int n) {
+// With `scale` (nullable): A32 = D^-1/2 A D^-1/2, scale_i = 1 / sqrt(a_ii) (1 where a_ii <= 0,
+// which the factor then reports), computed in FP64 before rounding.
+__global__ void convert_lower_kernel(const double *A, int64_t lda, float *A32, int64_t lda32, int n,
+                                     const double *scale) {
   const int64_t total = lda32 * (int64_t)n;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = e / lda32, i = e - j * lda32;
-    A32[e] = (i >= j && i < n) ? (float)A[j * lda + i] : 0.f;
+    double v = (i >= j && i < n) ? A[j * lda + i] : 0.0;
+    if (scale && i < n) v *= scale[i] * scale[j];
+    A32[e] = (float)v;
+  }
+}
+
+__global__ void diag_scale_kernel(const double *A, int64_t lda, int n, double *scale) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double d = A[(int64_t)i * lda + i];
+    scale[i] = d > 0.0 ? 1.0 / sqrt(d) : 1.0;
   }
 }
 
@@ -130,22 +143,27 @@ __global__ void __launch_bounds__(256) symm_residual_kernel(const double *A, int
   }
 }
 
+// R32 = float(D^-1/2 R) (scale nullable: no scaling)
 __global__ void to_f32_kernel(const double *R, int64_t ldr, float *R32, int64_t ld32, int n, int nrhs,
-                              const int *skip) {
+                              const double *scale, const int *skip) {
   if (skip && ld_volatile(skip)) return;
   const int64_t total = (int64_t)n * nrhs;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = e / n, i = e - c * n;
-    R32[c * ld32 + i] = (float)R[c * ldr + i];
+    const double r = R[c * ldr + i];
+    R32[c * ld32 + i] = (float)(scale ? r * scale[i] : r);
   }
 }
 
-__global__ void axpy_kernel(double *X, int64_t ldx, const float *D, int64_t ldd, int n, int nrhs, const int *skip) {
+// X += D^-1/2 double(D32) (scale nullable)
+__global__ void axpy_kernel(double *X, int64_t ldx, const float *D, int64_t ldd, int n, int nrhs,
+                            const double *scale, const int *skip) {
   if (skip && ld_volatile(skip)) return;
   const int64_t total = (int64_t)n * nrhs;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = e / n, i = e - c * n;
-    X[c * ldx + i] += (double)D[c * ldd + i];
+    const double d = (double)D[c * ldd + i];
+    X[c * ldx + i] += scale ? d * scale[i] : d;
   }
 }
 
@@ -216,7 +234,7 @@ __global__ void refine_out_kernel(const RefineCtrl *ctrl, int *dIters, double *d
 }
 
 struct RefineLayout {
-  size_t ctrl, a32, fwork, r, r32, swork, eta, finfo, total, fbytes, sbytes;
+  size_t ctrl, a32, fwork, r, r32, swork, eta, finfo, scale, total, fbytes, sbytes;
   int64_t lda32, ld32;
 };
 
@@ -231,6 +249,7 @@ static RefineLayout refine_layout(int n, int nrhs, const chol_opts *opts) {
   L.fbytes = chol_factor_workspace_size(n, opts);
   L.fwork = o; o += align_up(L.fbytes, 256);
   L.r = o; o += align_up((size_t)n * std::max(nrhs, 1) * 8, 256);
+  L.scale = o; o += align_up((size_t)std::max(n, 1) * 8, 256);
   L.r32 = o; o += align_up((size_t)L.ld32 * std::max(nrhs, 1) * 4, 256);
   L.sbytes = solve_workspace_bytes(n, nrhs);
   L.swork = o; o += align_up(L.sbytes, 256);
@@ -254,7 +273,11 @@ extern "C" chol_status chol_solve_refine(int n, int nrhs, const double *dA, int 
                                          const chol_opts *opts, void *dWork, size_t work_bytes, int *dInfo,
                                          int *dIters, double *dBerr, void *stream) {
   if (n < 0 || nrhs < 0 || !dInfo || !(tol >= 0.0) || max_iter < 1 || max_iter > 1000) return CHOL_ERR_INVALID_ARG;
-  if (low_precision != CHOL_F32) return CHOL_ERR_UNSUPPORTED;
+  const int prec = low_precision == CHOL_F32 ? PREC_F32
+                   : low_precision == CHOL_BF16 ? PREC_BF16
+                   : low_precision == CHOL_BF16X3 ? PREC_BF16X3
+                                                  : -1;
+  if (prec < 0) return CHOL_ERR_UNSUPPORTED;
   if (lda < std::max(1, n) || ldb < std::max(1, n) || ldx < std::max(1, n)) return CHOL_ERR_INVALID_ARG;
   if (n > 0 && (!dA || (nrhs > 0 && (!dB || !dX)))) return CHOL_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
@@ -279,10 +302,12 @@ extern "C" chol_status chol_solve_refine(int n, int nrhs, const double *dA, int 
   const int *skip = &ctrl->done;
   const int eblocks = di.sms * 8;
 
-  // low-precision factor
-  convert_lower_kernel<<<eblocks, 256, 0, s>>>(dA, lda, A32, L.lda32, n);
+  // low-precision factor (of the diagonally scaled matrix for the BF16 forms)
+  double *scale = prec == PREC_F32 ? nullptr : reinterpret_cast<double *>(ws + L.scale);
+  if (scale) diag_scale_kernel<<<(n + 255) / 256, 256, 0, s>>>(dA, lda, n, scale);
+  convert_lower_kernel<<<eblocks, 256, 0, s>>>(dA, lda, A32, L.lda32, n, scale);
   CHOL_CUDA_TRY(cudaGetLastError());
-  chol_status st = factor_impl(PREC_F32, n, A32, (int)L.lda32, opts, ws + L.fwork, L.fbytes, finfo, stream);
+  chol_status st = factor_impl(prec, n, A32, (int)L.lda32, opts, ws + L.fwork, L.fbytes, finfo, stream);
   if (st != CHOL_OK) return st;
   CHOL_CUDA_TRY(cudaMemcpyAsync(dInfo, finfo, sizeof(int), cudaMemcpyDeviceToDevice, s));
   refine_init_kernel<<<1, 32, 0, s>>>(ctrl, finfo);
@@ -295,11 +320,11 @@ extern "C" chol_status chol_solve_refine(int n, int nrhs, const double *dA, int 
                                   cudaMemcpyDeviceToDevice, s));
   const dim3 rgrid((n + RB - 1) / RB, (nrhs + RG - 1) / RG);
   for (int it = 0; it < max_iter; ++it) {
-    to_f32_kernel<<<eblocks, 256, 0, s>>>(R, n, R32, L.ld32, n, nrhs, skip);
+    to_f32_kernel<<<eblocks, 256, 0, s>>>(R, n, R32, L.ld32, n, nrhs, scale, skip);
     CHOL_CUDA_TRY(cudaGetLastError());
     st = solve_f32(n, nrhs, A32, (int)L.lda32, R32, (int)L.ld32, ws + L.swork, skip, s);
     if (st != CHOL_OK) return st;
-    axpy_kernel<<<eblocks, 256, 0, s>>>(dX, ldx, R32, L.ld32, n, nrhs, skip);
+    axpy_kernel<<<eblocks, 256, 0, s>>>(dX, ldx, R32, L.ld32, n, nrhs, scale, skip);
     const int cpt = cpt_for(std::min(nrhs, RG));
     if (cpt == 8) symm_residual_kernel<8><<<rgrid, 256, 0, s>>>(dA, lda, dX, ldx, dB, ldb, R, n, n, nrhs, skip);
     else if (cpt == 4) symm_residual_kernel<4><<<rgrid, 256, 0, s>>>(dA, lda, dX, ldx, dB, ldb, R, n, n, nrhs, skip);

@@ -4,8 +4,8 @@ FP32 factor: integer data stays exact in FP32 while every intermediate is an int
 2^24 (here |a_ij| <= 64 n), so L must come back bitwise; on Gram matrices (kappa <= 5) the
 FP32 factor must match the FP64 oracle within relative Frobenius 2e-5 (~ n u_32 growth).
 Refinement: the backward error must reach 1e-14 (the accuracy target of the FP64 path) on
-matrices with kappa = 1e6, and X must match the oracle's FP64 solution within kappa * 1e-14
-(forward error <= kappa * backward error).
+matrices with kappa = 1e6, and X must match the oracle's FP64 solution within the forward
+error bound 2 kappa_inf eta / (1 - kappa_inf eta) that the backward errors of both imply.
 """
 import numpy as np
 import pytest
@@ -25,6 +25,20 @@ def chol():
 
 def _f32(chol, A_np):
     return chol.colmajor(torch.from_numpy(np.ascontiguousarray(A_np)).to("cuda", torch.float32))
+
+
+def _assert_forward_error(A, X, B, Xref):
+    """Column-wise forward error against the perturbation bound of a normwise (Rigal-Gaches)
+    backward error eta: ||x - x*||_inf / ||x*||_inf <= 2 kappa_inf eta / (1 - kappa_inf eta)
+    (Higham, Accuracy and Stability, Thm 7.2), kappa_inf = ||A||_inf ||A^-1||_inf computed
+    here; Xref (the oracle's FP64 solution) carries its own error, bounded the same way."""
+    kinf = np.linalg.norm(A, np.inf) * np.linalg.norm(np.linalg.inv(A), np.inf)
+    for c in range(B.shape[1]):
+        eta = oracle.backward_error(A, X[:, c:c + 1], B[:, c:c + 1])
+        eta_ref = oracle.backward_error(A, Xref[:, c:c + 1], B[:, c:c + 1])
+        bound = sum(2 * kinf * e / (1 - kinf * e) for e in (eta, eta_ref))
+        err = np.abs(X[:, c] - Xref[:, c]).max() / np.abs(Xref[:, c]).max()
+        assert err <= bound, (c, err, bound)
 
 
 @pytest.mark.parametrize("n,nb,policy", [(600, 64, "heft"), (700, 128, "dada"), (1030, 256, "steal"),
@@ -63,10 +77,9 @@ def test_refine_reaches_fp64_backward_error(chol, n, nrhs, nb):
     assert eta <= 1e-14, (eta, int(iters.item()))
     assert float(berr.item()) <= 1e-14
     assert 1 <= int(iters.item()) <= 40
-    # refinement stops at backward error eta <= 1e-14, so the forward error is only bounded by
-    # kappa(A) * eta (the standard perturbation bound for A x = b): 1e6 * 1e-14
-    Xref = oracle.solve(oracle.factor(A), B)
-    assert oracle.rel_frobenius(Xh, Xref) <= 1e6 * 1e-14
+    # refinement stops at backward error eta <= 1e-14: the forward error is bounded through
+    # the condition number
+    _assert_forward_error(A, Xh, B, oracle.solve(oracle.factor(A), B))
     # inputs untouched
     np.testing.assert_array_equal(Bd.cpu().numpy(), B)
     np.testing.assert_array_equal(Ad.cpu().numpy(), A)
@@ -84,3 +97,74 @@ def test_refine_reports_indefinite(chol):
     assert int(info.item()) == 151
     assert np.isinf(float(berr.item()))
     assert int(iters.item()) == 0
+
+
+# ---- tensor-core forms of the low-precision factor (tcgen05, BF16 operands, FP32 accumulation)
+
+@pytest.mark.parametrize("precision", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("n,nb,policy", [(600, 64, "heft"), (1030, 256, "dada"), (1024, 256, "heft")])
+def test_tc_integer_factor_bitwise(chol, precision, n, nb, policy):
+    # the update operands are entries of L (integers in [-8, 8]: exact in one BF16 term) and
+    # every partial sum is an integer below 2^24, so both forms must return L bitwise
+    L, A = synth.integer_factor(n, seed=n + 1)
+    Ad = _f32(chol, A)
+    info, _ = chol.factor_f32(Ad, chol.opts(nb=nb, policy=policy), precision=precision)
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    np.testing.assert_array_equal(np.tril(Ad.cpu().numpy().astype(np.float64)), L)
+
+
+@pytest.mark.parametrize("n,nb", [(1024, 128), (1000, 256), (333, 64)])
+def test_bf16x3_factor_parity(chol, n, nb):
+    # three BF16 terms carry all 24 bits of an FP32 operand: FP32-level agreement
+    A = synth.gram_spd(n, seed=n).numpy()
+    Ad = _f32(chol, A)
+    info, _ = chol.factor_f32(Ad, chol.opts(nb=nb), precision="bf16x3")
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    rel = oracle.rel_frobenius(np.tril(Ad.cpu().numpy().astype(np.float64)), oracle.factor(A))
+    assert rel <= 2e-5
+
+
+@pytest.mark.parametrize("n,nb", [(1024, 128), (1000, 256)])
+def test_bf16_factor_parity(chol, n, nb):
+    # one BF16 term: each update operand carries a relative error <= u = 2^-9, so the Schur
+    # complements, and with kappa(A) <= 5 the factor, are off by a few u times sqrt(growth)
+    A = synth.gram_spd(n, seed=n).numpy()
+    Ad = _f32(chol, A)
+    info, _ = chol.factor_f32(Ad, chol.opts(nb=nb), precision="bf16")
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    rel = oracle.rel_frobenius(np.tril(Ad.cpu().numpy().astype(np.float64)), oracle.factor(A))
+    assert 1e-6 < rel <= 16 * 2.0 ** -9, rel
+
+
+@pytest.mark.parametrize("n,nrhs,nb", [(1024, 4, 128), (777, 16, 256)])
+def test_refine_bf16x3_reaches_fp64_backward_error(chol, n, nrhs, nb):
+    A = synth.householder_spd(n, seed=3, cond=1e6).numpy()
+    B = synth.rhs(n, nrhs, seed=4).numpy()
+    Ad = chol.colmajor(torch.from_numpy(A).to("cuda"))
+    Bd = chol.colmajor(torch.from_numpy(B).to("cuda"))
+    X, info, iters, berr = chol.solve_refine(Ad, Bd, tol=1e-14, max_iter=40, o=chol.opts(nb=nb),
+                                             precision="bf16x3")
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    Xh = X.cpu().numpy()
+    assert oracle.backward_error(A, Xh, B) <= 1e-14
+    assert float(berr.item()) <= 1e-14
+    _assert_forward_error(A, Xh, B, oracle.solve(oracle.factor(A), B))
+
+
+def test_refine_bf16_well_conditioned(chol):
+    # plain BF16 operands: refinement contracts when kappa(A) u_bf16 < 1 (Gram, kappa <= 5)
+    n, nrhs = 1024, 4
+    A = synth.gram_spd(n, seed=5).numpy()
+    B = synth.rhs(n, nrhs, seed=6).numpy()
+    Ad = chol.colmajor(torch.from_numpy(A).to("cuda"))
+    Bd = chol.colmajor(torch.from_numpy(B).to("cuda"))
+    X, info, iters, berr = chol.solve_refine(Ad, Bd, tol=1e-14, max_iter=40, o=chol.opts(nb=128),
+                                             precision="bf16")
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    assert oracle.backward_error(A, X.cpu().numpy(), B) <= 1e-14
+    assert int(iters.item()) >= 2  # a BF16 factor alone cannot reach it
