@@ -318,9 +318,11 @@ def _backward_error(A, X, B):
 
 def run_mixed(args, chol, dev):
     """The mixed-precision configuration: A = Q diag(lambda) Q^T with kappa = 1e6 (32
-    Householder reflectors), 16 RHS. FP64 factor + solve against FP32 factor + FP64
-    iterative refinement to the same backward error (1e-14); both timed with CUDA events
-    over --mixed-steps steps after one warm-up step each."""
+    Householder reflectors), 16 RHS. FP64 factor + solve against a low-precision factor + FP64
+    iterative refinement to the same backward error (1e-14), for each low-precision form
+    (FP32 FFMA, three-term BF16 on tensor cores, plain BF16 on tensor cores); all timed with
+    CUDA events over --mixed-steps steps after one warm-up step each. The headline numbers
+    are those of the fastest form that reaches the target."""
     import torch
     import synth
     n, nrhs = args.mixed_n, args.mixed_nrhs
@@ -342,8 +344,9 @@ def run_mixed(args, chol, dev):
         chol.factor(W, o, work=work, info=info, stream=stream)
         chol.solve(W, Bw, work=sw, info=info, stream=stream)
 
-    def mixed_step():
-        return chol.solve_refine(A, B, X=X, tol=1e-14, max_iter=30, o=o, work=rwork, stream=stream)
+    def mixed_step(prec, A_, B_):
+        return chol.solve_refine(A_, B_, X=X, tol=1e-14, max_iter=30, o=o, work=rwork, stream=stream,
+                                 precision=prec)
 
     def timed(fn):
         fn()
@@ -360,17 +363,46 @@ def run_mixed(args, chol, dev):
 
     t64, _ = timed(fp64_step)
     e64 = _backward_error(A, Bw, B)
-    tmx, out = timed(mixed_step)
-    _, minfo, iters, berr = out
-    emx = _backward_error(A, X, B)
-    rel = float(torch.linalg.norm(X - Bw) / torch.linalg.norm(Bw))
+    low = {"f32": "FP32 (FFMA) tile bodies",
+           "bf16x3": "FP32 storage, SYRK/GEMM on tcgen05 with three BF16 operand terms (FP32-accurate), "
+                     "diagonal scaling",
+           "bf16": "FP32 storage, SYRK/GEMM on tcgen05 with one BF16 operand term, diagonal scaling"}
+    variants = {}
+    for prec in ("f32", "bf16x3", "bf16"):
+        tmx, out = timed(lambda: mixed_step(prec, A, B))
+        _, minfo, iters, berr = out
+        finfo = int(minfo.item())
+        emx = _backward_error(A, X, B) if finfo == 0 else float("inf")
+        reached = bool(finfo == 0 and emx <= 1e-14)
+        v = {"low_precision": low[prec], "ms": round(tmx, 2),
+             "speedup": round(t64 / tmx, 2) if reached else None,  # only at the same backward error
+             "iterations": int(iters.item()), "info": finfo,
+             "backward_error": emx, "reported_backward_error": float(berr.item()),
+             "reached_target": reached}
+        if finfo == 0:
+            v["x_rel_diff_vs_fp64"] = float(torch.linalg.norm(X - Bw) / torch.linalg.norm(Bw))
+        else:
+            v["note"] = ("the factor breaks down (info = %d: a pivot is not positive in this precision); "
+                         "kappa(A) u_bf16 >> 1" % finfo)
+        variants[prec] = v
+    # plain BF16 on a well-conditioned matrix of the same order (A = sym(G G^T)/n + I), for context
+    Ag = chol.colmajor(synth.gram_spd(n, seed=args.seed + 3, device=dev))
+    tg, out = timed(lambda: mixed_step("bf16", Ag, B))
+    _, ginfo, giters, gberr = out
+    variants["bf16_well_conditioned"] = {
+        "workload": "n=%d, %d RHS, A = sym(G G^T)/n + I (kappa <= 5)" % (n, nrhs), "ms": round(tg, 2),
+        "iterations": int(giters.item()), "info": int(ginfo.item()),
+        "backward_error": _backward_error(Ag, X, B) if int(ginfo.item()) == 0 else float("inf")}
+    ok = [p for p in ("f32", "bf16x3") if variants[p]["reached_target"]]
+    best = min(ok, key=lambda p: variants[p]["ms"]) if ok else "f32"
+    b = variants[best]
     return {"workload": "n=%d, %d RHS, A = Q diag(lambda) Q^T, lambda geometric 1..1e6 (32 Householder "
                         "reflectors), tile 256, HEFT" % (n, nrhs),
-            "fp64_ms": round(t64, 2), "mixed_ms": round(tmx, 2), "speedup": round(t64 / tmx, 2),
-            "low_precision": "f32 (FFMA) factor, FP64 residual and update",
-            "target_backward_error": 1e-14, "fp64_backward_error": e64, "mixed_backward_error": emx,
-            "mixed_reported_backward_error": float(berr.item()), "iterations": int(iters.item()),
-            "info": int(minfo.item()), "x_rel_diff_vs_fp64": rel}
+            "fp64_ms": round(t64, 2), "mixed_ms": b["ms"], "speedup": b["speedup"], "best": best,
+            "low_precision": b["low_precision"] + "; FP64 residual and update",
+            "target_backward_error": 1e-14, "fp64_backward_error": e64, "mixed_backward_error": b["backward_error"],
+            "mixed_reported_backward_error": b["reported_backward_error"], "iterations": b["iterations"],
+            "info": b["info"], "x_rel_diff_vs_fp64": b.get("x_rel_diff_vs_fp64"), "variants": variants}
 
 
 def run_batched(args, chol, dev):

@@ -130,7 +130,7 @@ chol_status chol_solve(int n, int nrhs, const double *dL, int lda, double *dB, i
  * workspace chol_solve needs. Arguments and results are those of chol_solve.
  *  - The workspace is a fixed 256 KiB array of this library in device global memory
  *    (each GPU that loads the library holds it until the process exits). Problems whose
- *    chol_solve_workspace_size(n, nrhs) exceeds 256 KiB -- ceil(n/32) * ceil(nrhs/64) >
+ *    chol_solve_workspace_size(n, nrhs) exceeds 256 KiB -- ceil(n/32) * ceil(nrhs/32) >
  *    32704 -- are rejected with CHOL_ERR_UNSUPPORTED before anything is launched.
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
  *    with that device current; make that first call before any stream capture.

@@ -1,12 +1,19 @@
 // Forward and back substitution with the Cholesky factor, L Y = B then L^T X = Y.
 //
-// The right-hand sides are cut into 32-row blocks r and groups g of up to 64 columns. One
+// The right-hand sides are cut into 32-row blocks r and groups g of up to 32 columns. One
 // thread block handles one item (r, g) at a time: it accumulates B_r - sum_m L_rm Y_m over
-// the blocks m already solved (forward; L_mr^T X_m over m > r backward), waiting on each
-// m's ready flag, then solves the 32 x 32 diagonal block and publishes Y_r. Items are
-// claimed from an atomic counter in solve order, so every item waits only on items that
-// were claimed earlier and are held by running blocks: the sweep always progresses, with
-// or without co-residency. Waits are bounded (timeout -> CHOL_INFO_TIMEOUT in *dInfo).
+// the blocks m already solved (forward; L_mr^T X_m over m > r backward), then solves its
+// 32 x 32 diagonal block and publishes Y_r with a ready flag. Items are claimed from an
+// atomic counter in solve order, so every item waits only on items that were claimed earlier
+// and are held by running blocks: the sweep always progresses, with or without co-residency.
+//
+// Inside an item the eight warps split the blocks m (warp w takes m = w, w + 8, ... in the
+// order the sweep produces them) and work independently: a warp loads its L block, waits for
+// its m's flag (one lane polls, bounded), stages Y_m in its own shared-memory rows and
+// accumulates into registers (lane = row of the item, one register per right-hand side). The
+// block synchronises once per item, to add the eight partial sums; the chain from one block
+// row to the next is therefore one L2 round trip for Y, one warp's 32 x 32 product, the sum
+// and the diagonal solve. Waits are bounded (timeout -> CHOL_INFO_TIMEOUT in *dInfo).
 //
 // The kernel is instantiated for FP64 (chol_solve) and FP32 (the low-precision solves of
 // the mixed-precision refinement). In FP64 both sweeps are bound by the FP64 pipe (n^2 nrhs
@@ -14,16 +21,16 @@
 #include <algorithm>
 #include <mutex>
 #include "common.cuh"
-#include "blockacc.cuh"
 #include "internal.cuh"
 
 namespace chol {
 
 constexpr int SB = 32;   // rows per block
-constexpr int SG = 64;   // right-hand sides per group
+constexpr int SG = 32;   // right-hand sides per group (one accumulator register per lane each)
 constexpr int SNT = 256;
+constexpr int SNW = SNT / 32;
 constexpr int SLD = SB + 1;
-constexpr int SOLVE_EXCL_SMEM = 120 * 1024;  // unused bytes that keep the SM to one block
+constexpr int SOLVE_EXCL_SMEM = 120 * 1024;  // at least this much, so an SM holds one block
 
 struct SolveCtrl {
   unsigned int next_item;
@@ -56,20 +63,54 @@ __device__ __forceinline__ T squot(T b, T d, T r) {
   return fma(e, r, x);
 }
 
-template <class T, int CPT>
+// shared memory of solve_kernel<T, NC>, in elements of T
+template <class T, int NC>
+struct SolveSmem {
+  static constexpr int V = 16 / (int)sizeof(T) < NC ? 16 / (int)sizeof(T) : NC;  // vector width
+  static constexpr int YLD = NC + 16 / (int)sizeof(T);  // row stride: 16-byte rows, no conflicts
+  static constexpr size_t YW = (size_t)SNW * SB * YLD;  // per-warp Y_m rows, later partial sums
+  static constexpr size_t LT = (size_t)SNW * SB * SLD;  // per-warp transposed L block (backward)
+  static constexpr size_t YS = (size_t)SB * YLD;        // the item's block before the diagonal solve
+  static constexpr size_t LD = (size_t)SB * SLD + SB;   // diagonal block and its reciprocals
+  static constexpr size_t NEED = (YW + LT + YS + LD) * sizeof(T);
+  static constexpr size_t BYTES = NEED > (size_t)SOLVE_EXCL_SMEM ? NEED : (size_t)SOLVE_EXCL_SMEM;
+};
+
+template <class T, int V>
+struct VecOf;
+template <> struct VecOf<float, 4> { using type = float4; };
+template <> struct VecOf<float, 2> { using type = float2; };
+template <> struct VecOf<float, 1> { using type = float; };
+template <> struct VecOf<double, 2> { using type = double2; };
+template <> struct VecOf<double, 1> { using type = double; };
+
+template <class T, int V>
+__device__ __forceinline__ void vload(const T *p, T (&v)[V]) {
+  using VT = typename VecOf<T, V>::type;
+  const VT x = *reinterpret_cast<const VT *>(p);
+  const T *e = reinterpret_cast<const T *>(&x);
+#pragma unroll
+  for (int u = 0; u < V; ++u) v[u] = e[u];
+}
+
+template <class T, int NC>
 __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ SolveArgs a) {
-  __shared__ T Ls[SB * SLD];  // off-diagonal block of the current step
-  __shared__ T Ld[SB * SLD];  // diagonal block of the item (prefetched)
-  __shared__ T Ys[SB * SG];
-  __shared__ T Red[SB * SG];  // k-slice partial sums
-  __shared__ T Rs[SB];        // reciprocals of the diagonal
+  using S = SolveSmem<T, NC>;
+  constexpr int V = S::V, YLD = S::YLD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *Yw = reinterpret_cast<T *>(smem_raw);
+  T *Lt = Yw + S::YW;
+  T *Ys = Lt + S::LT;
+  T *Ld = Ys + S::YS;
+  T *Rs = Ld + SB * SLD;
   __shared__ long long s_item;
   __shared__ int s_abort;
   const T *L = static_cast<const T *>(a.L);
   T *B = static_cast<T *>(a.B);
   if (a.skip && ld_volatile(a.skip)) return;
-  const int tid = threadIdx.x;
-  const int rr = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  T *yw = Yw + (size_t)warp * SB * YLD;
+  T *lt = Lt + (size_t)warp * SB * SLD;
   while (true) {
     if (tid == 0) {
       s_abort = ld_volatile(&a.ctrl->abort) || (a.prev_abort && ld_volatile(a.prev_abort));
@@ -83,48 +124,55 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
     const int r = a.trans ? a.nrb - 1 - ord : ord;
     const int r0 = r * SB, rows = min(SB, a.n - r0);
     const int c0 = g * SG, cols = min(SG, a.nrhs - c0);
-    const Slices<CPT> sl(cols, warp);
     // the diagonal block and its reciprocals do not depend on other items: load them now,
-    // off the chain of waits. Rows past the end of the matrix get an identity block, so
-    // the substitution runs over a fixed 32 rows with register-resident data.
+    // off the chain of waits. Rows past the end of the matrix get an identity block, so the
+    // substitution runs over a fixed 32 rows with register-resident data.
     for (int e = tid; e < SB * SB; e += SNT) {
       const int i = e & 31, j = e >> 5;
       Ld[i * SLD + j] = (i < rows && j < rows && i >= j) ? __ldcg(L + (int64_t)(r0 + j) * a.lda + r0 + i)
                                                           : (i == j ? T(1) : T(0));
     }
     if (tid < SB) Rs[tid] = tid < rows ? T(1) / __ldcg(L + (int64_t)(r0 + tid) * a.lda + r0 + tid) : T(1);
-    T acc[CPT];
+    // this thread's entries of B_r for the final sum, loaded now (off the chain)
+    constexpr int BPT = (SB * NC + SNT - 1) / SNT;
+    T bv[BPT];
 #pragma unroll
-    for (int q = 0; q < CPT; ++q) {
-      const int c = sl.col(q);
-      acc[q] = (sl.kslice == 0 && rr < rows && c < cols) ? __ldcg(B + (int64_t)(c0 + c) * a.ldb + r0 + rr) : T(0);
+    for (int u = 0; u < BPT; ++u) {
+      const int e = tid + u * SNT, i = e & (SB - 1), q = e >> 5;
+      bv[u] = (e < SB * NC && i < rows && q < cols) ? __ldcg(B + (int64_t)(c0 + q) * a.ldb + r0 + i) : T(0);
     }
-    // blocks are consumed in the order the sweep produces them (forward: 0, 1, ...;
-    // backward: nrb-1, nrb-2, ...), so an item only waits on the newest block it needs
+    // warp-parallel accumulation over the solved blocks
+    T acc[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) acc[q] = T(0);
     const int nsteps = a.trans ? a.nrb - 1 - r : r;
-    for (int step = 0; step < nsteps; ++step) {
+    int wab = 0;
+    for (int step = warp; step < nsteps; step += SNW) {
       const int m = a.trans ? a.nrb - 1 - step : step;
       const int m0 = m * SB, mrows = min(SB, a.n - m0);
-      // L block into Ls as Ls[row of the r block][k] (forward: L_rm; backward: L_mr^T)
-      for (int e = tid; e < SB * SB; e += SNT) {
-        const int i = e & 31, j = e >> 5;
-        if (!a.trans) {  // element (r0+i, m0+j)
-          Ls[i * SLD + j] = (i < rows && j < mrows) ? __ldcg(L + (int64_t)(m0 + j) * a.lda + r0 + i) : T(0);
-        } else {         // element (m0+i, r0+j) stored at [j][i]
-          Ls[j * SLD + i] = (i < mrows && j < rows) ? __ldcg(L + (int64_t)(r0 + j) * a.lda + m0 + i) : T(0);
-        }
+      // L block, issued before the wait. Forward: lane = row of the item, lr[k] = L_rm(lane, k).
+      // Backward: lane = row k of block m, lr[i] = L_mr(lane, i), staged transposed below.
+      T lr[SB];
+      if (!a.trans) {
+#pragma unroll
+        for (int k = 0; k < SB; ++k)
+          lr[k] = (lane < rows && k < mrows) ? __ldcg(L + (int64_t)(m0 + k) * a.lda + r0 + lane) : T(0);
+      } else {
+#pragma unroll
+        for (int i = 0; i < SB; ++i)
+          lr[i] = (lane < mrows && i < rows) ? __ldcg(L + (int64_t)(r0 + i) * a.lda + m0 + lane) : T(0);
       }
       // wait until block m of this group is solved
-      if (tid == 0) {
+      if (lane == 0) {
         const uint64_t t0 = globaltimer_ns();
         int64_t spins = 0;
         unsigned slp = 32;
         while (ld_volatile(&a.flags[(int64_t)m * a.ngroups + g]) == 0) {
-          if (ld_volatile(&a.ctrl->abort)) { s_abort = 1; break; }
+          if (ld_volatile(&a.ctrl->abort)) { wab = 1; break; }
           if (globaltimer_ns() - t0 > (uint64_t)a.timeout_ns || ++spins > (a.timeout_ns >> 7) + 100000) {
             atomicCAS(&a.ctrl->info, 0, CHOL_INFO_TIMEOUT);
             atomicExch(&a.ctrl->abort, 1);
-            s_abort = 1;
+            wab = 1;
             break;
           }
           __nanosleep(slp);
@@ -132,25 +180,54 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
         }
         __threadfence();
       }
-      __syncthreads();
-      if (s_abort) break;
-      for (int e = tid; e < SB * SG; e += SNT) {
-        const int k = e & 31, c = e >> 5;
-        Ys[k * SG + c] = (k < mrows && c < cols) ? __ldcg(B + (int64_t)(c0 + c) * a.ldb + m0 + k) : T(0);
+      __syncwarp();
+      wab = __shfl_sync(0xffffffffu, wab, 0);
+      if (wab) break;
+      // Y block m: lane k stages row k
+#pragma unroll
+      for (int q = 0; q < NC; ++q)
+        yw[lane * YLD + q] = (lane < mrows && q < cols) ? __ldcg(B + (int64_t)(c0 + q) * a.ldb + m0 + lane) : T(0);
+      if (a.trans) {
+#pragma unroll
+        for (int i = 0; i < SB; ++i) lt[lane * SLD + i] = lr[i];
       }
-      __syncthreads();
-      acc_step<T, CPT>(acc, Ls, SLD, Ys, SG, rr, sl);
-      __syncthreads();
+      __syncwarp();
+#pragma unroll
+      for (int k = 0; k < SB; ++k) {
+        const T l = a.trans ? lt[k * SLD + lane] : lr[k];
+#pragma unroll
+        for (int q = 0; q < NC; q += V) {
+          T y[V];
+          vload<T, V>(yw + k * YLD + q, y);
+#pragma unroll
+          for (int u = 0; u < V; ++u) acc[q + u] = fma(l, y[u], acc[q + u]);
+        }
+      }
+      __syncwarp();
     }
+    if (wab && lane == 0) s_abort = 1;
+    // the eight partial sums: into the warps' rows, then B_r minus their sum into Ys
+#pragma unroll
+    for (int q = 0; q < NC; ++q) yw[lane * YLD + q] = acc[q];
+    __syncthreads();
     if (s_abort) break;
-    acc_finish<T, CPT>(acc, Ys, SG, Red, rr, cols, sl);
-    // diagonal block: one thread per right-hand side runs the substitution, so every FP64
-    // instruction of the block does useful work (the FP64 pipe, not latency, bounds it)
+#pragma unroll
+    for (int u = 0; u < BPT; ++u) {
+      const int e = tid + u * SNT, i = e & (SB - 1), q = e >> 5;
+      if (e < SB * NC) {
+        T sum = T(0);
+#pragma unroll
+        for (int w = 0; w < SNW; ++w) sum += Yw[(size_t)w * SB * YLD + i * YLD + q];
+        Ys[i * YLD + q] = bv[u] - sum;
+      }
+    }
+    __syncthreads();
+    // diagonal block: one thread per right-hand side runs the substitution
     if (tid < cols) {
       const int c = tid;
       T x[SB];
 #pragma unroll
-      for (int i = 0; i < SB; ++i) x[i] = Ys[i * SG + c];
+      for (int i = 0; i < SB; ++i) x[i] = Ys[i * YLD + c];
       // right-looking: once x_k is known every later row is updated at once, so each x_k
       // is one quotient and one multiply-add after x_{k-1}
       if (!a.trans) {
@@ -192,15 +269,16 @@ static size_t solve_ws(int n, int nrhs) { return 512 + 2 * flags_bytes(n, nrhs);
 
 size_t solve_workspace_bytes(int n, int nrhs) { return solve_ws(n, nrhs); }
 
-template <class T, int CPT>
+template <class T, int NC>
 static cudaError_t launch_solve(const SolveArgs &a, int grid, cudaStream_t s) {
   // one block per SM: the dynamic shared memory request (more than half an SM's) makes a
   // second block impossible
+  constexpr size_t bytes = SolveSmem<T, NC>::BYTES;
   static std::once_flag once;
   std::call_once(once, [] {
-    cudaFuncSetAttribute(solve_kernel<T, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_EXCL_SMEM);
+    cudaFuncSetAttribute(solve_kernel<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   });
-  solve_kernel<T, CPT><<<grid, SNT, SOLVE_EXCL_SMEM, s>>>(a);
+  solve_kernel<T, NC><<<grid, SNT, bytes, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -227,12 +305,15 @@ static chol_status launch_sweep(int trans, int slot, int n, int nrhs, const T *d
   // of an SM's) makes a second block impossible.
   const DeviceInfo di = current_device_info();
   const int64_t grid = std::min<int64_t>(a.nitems, (int64_t)std::max(1, di.sms));
-  const int cpt = cpt_for(std::min(nrhs, SG));
+  // accumulator registers per lane: the smallest power of two that holds a group
+  const int w = std::min(nrhs, SG);
   cudaError_t e;
-  if (cpt == 8) e = launch_solve<T, 8>(a, (int)grid, s);
-  else if (cpt == 4) e = launch_solve<T, 4>(a, (int)grid, s);
-  else if (cpt == 2) e = launch_solve<T, 2>(a, (int)grid, s);
-  else e = launch_solve<T, 1>(a, (int)grid, s);
+  if (w <= 1) e = launch_solve<T, 1>(a, (int)grid, s);
+  else if (w <= 2) e = launch_solve<T, 2>(a, (int)grid, s);
+  else if (w <= 4) e = launch_solve<T, 4>(a, (int)grid, s);
+  else if (w <= 8) e = launch_solve<T, 8>(a, (int)grid, s);
+  else if (w <= 16) e = launch_solve<T, 16>(a, (int)grid, s);
+  else e = launch_solve<T, 32>(a, (int)grid, s);
   CHOL_CUDA_TRY(e);
   return CHOL_OK;
 }

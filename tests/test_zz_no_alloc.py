@@ -57,7 +57,7 @@ def test_noalloc_solve_matches_solve_on_two_calls(n, nrhs):
 
 def test_noalloc_rejects_problems_beyond_its_array():
     chol, f = _fn()
-    # ceil(n/32) * ceil(nrhs/64) above 32704 does not fit; rejected before any launch
+    # ceil(n/32) * ceil(nrhs/32) above 32704 does not fit; rejected before any launch
     st = f(32705 * 32, 1, None, 32705 * 32, None, 32705 * 32, None, None)
     assert st == -5
     st = f(-1, 1, None, 1, None, 1, None, None)
