@@ -63,6 +63,11 @@ def parse():
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--batch", type=int, default=10000)
     p.add_argument("--batched-steps", type=int, default=3)
+    p.add_argument("--no-adjoint", action="store_true")
+    p.add_argument("--adj-n", type=int, default=1024)
+    p.add_argument("--adj-batch", type=int, default=64)
+    p.add_argument("--adj-steps", type=int, default=2)
+    p.add_argument("--adj-streams", type=int, default=8)
     return p.parse_args()
 
 
@@ -288,6 +293,9 @@ def main():
     batched = None
     if not args.no_batched and rank == 0:
         batched = run_batched(args, chol, dev)
+    adjoint = None
+    if not args.no_adjoint and rank == 0:
+        adjoint = run_adjoint(args, chol, dev)
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         cpu = cpu_baseline(args)
@@ -301,6 +309,7 @@ def main():
             "config": workload_config(args),
             "factor_ms": round(fac_avg, 2), "solve_backward_error": berr,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "mixed_precision": mixed, "batched": batched,
+            "adjoint": adjoint,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
                        "reasons": clk.get("reasons"), "samples": clk.get("samples"),
@@ -470,6 +479,80 @@ def run_batched(args, chol, dev):
         del src, work, flat, rhs, graph
         torch.cuda.empty_cache()
     return out
+
+
+def run_adjoint(args, chol, dev):
+    """The differentiation configuration: --adj-batch FP64 SPD matrices of order --adj-n
+    (A = sym(G G^T)/n + I), loss = sum(w * x) with x = A^-1 b and w, b ~ N(0,1). One step =
+    for every matrix the forward pass (factor + solve) and the backward pass (solve adjoint,
+    then Cholesky adjoint) through the library's entry points, timed with CUDA events. The
+    matrices are independent: they go round-robin to --adj-streams streams, and each factor
+    runs with 32 workers (a tile-128 factor of order 1024 has at most 28 ready tasks), so
+    several factorizations share the GPU. Flops per matrix: n^3/3 + 2n^2 forward; backward
+    n^3/3 for L^T Lbar on the lower tiles, 2n^3 for the two triangular solves with n
+    right-hand sides, O(n^2) for the rest."""
+    import torch
+    import synth
+    n, m, ns = args.adj_n, args.adj_batch, max(1, args.adj_streams)
+    As = [chol.colmajor(synth.gram_spd(n, seed=args.seed + 100 + i, device=dev)) for i in range(m)]
+    bw = synth.rhs(n, 2 * m, seed=args.seed + 11, device=dev)
+    bs = [chol.colmajor(bw[:, i:i + 1]) for i in range(m)]
+    ws = [chol.colmajor(bw[:, m + i:m + i + 1]) for i in range(m)]
+    o = chol.opts(nb=128, num_workers=32)
+    main = torch.cuda.current_stream(dev)
+    streams = [torch.cuda.Stream(dev) for _ in range(ns)]
+    Fs = [torch.empty_like(As[0]) for _ in range(ns)]
+    Xs = [torch.empty_like(bs[0]) for _ in range(ns)]
+    fworks = [torch.empty(chol.workspace_size(n, o), dtype=torch.uint8, device=dev) for _ in range(ns)]
+    sworks = [torch.empty(chol.solve_workspace_size(n, 1), dtype=torch.uint8, device=dev) for _ in range(ns)]
+    infos = [torch.zeros(1, dtype=torch.int32, device=dev) for _ in range(ns)]
+    grads = [None] * m
+
+    def step():
+        start = torch.cuda.Event()
+        start.record(main)
+        for st in streams:
+            st.wait_event(start)
+        for i in range(m):
+            k = i % ns
+            st, F, X = streams[k], Fs[k], Xs[k]
+            with torch.cuda.stream(st):
+                F.copy_(As[i])
+                X.copy_(bs[i])
+                chol.factor(F, o, work=fworks[k], info=infos[k], stream=st)
+                chol.solve(F, X, work=sworks[k], info=infos[k], stream=st)
+                _, Lbar = chol.solve_backward(F, X, ws[i], stream=st)
+                grads[i] = chol.cholesky_backward(F, Lbar, stream=st)
+        for st in streams:
+            done = torch.cuda.Event()
+            done.record(st)
+            main.wait_event(done)
+
+    step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(main)
+    for _ in range(args.adj_steps):
+        step()
+    e1.record(main)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.adj_steps
+    flops = m * (n ** 3 / 3.0 + 2.0 * n * n + n ** 3 / 3.0 + 2.0 * n ** 3)
+    bad = sum(int(x.item()) != 0 for x in infos)
+    # check (outside the timed region): Abar = -(lam x^T + x lam^T)/2 with lam = A^-1 w
+    worst = 0.0
+    for i in (0, m // 2, m - 1):
+        x = torch.linalg.solve(As[i], bs[i])
+        lam = torch.linalg.solve(As[i], ws[i])
+        ref = -0.5 * (lam @ x.T + x @ lam.T)
+        worst = max(worst, float(torch.linalg.norm(grads[i] - ref) / torch.linalg.norm(ref)))
+    return {"workload": "%d FP64 SPD matrices n=%d (A = sym(G G^T)/n + I), loss = sum(w * x), x = A^-1 b; "
+                        "forward factor + solve and backward solve + Cholesky adjoints per matrix, tile 128, "
+                        "%d streams, 32 factor workers per matrix" % (m, n, ns),
+            "ms": round(ms, 2), "ms_per_matrix": round(ms / m, 3), "flops_per_step": flops,
+            "gflops": round(flops / ms / 1e6, 1), "frac_of_fp64_peak": round(flops / ms / 1e6 / FP64_PEAK_GFLOPS, 4),
+            "nonzero_info": bad, "grad_rel_diff_vs_closed_form": worst}
 
 
 def run_e2e(args, chol, A0, B0, o, dev):
