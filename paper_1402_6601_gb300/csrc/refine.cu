@@ -9,8 +9,8 @@
 // whole solve is one asynchronous sequence of launches on the caller's stream.
 //
 // Kernels (FP64 parts are bound by the FP64 pipe, like the factor):
-//   convert_lower   A (FP64, lower) -> A32 (FP32), rows padded with zeros
-//   norm kernels    ||A||_inf from the lower triangle (symmetric), once
+//   convert_lower   A (FP64, lower) -> A32 (FP32), with the absolute row sums of the
+//                   symmetric A; norm_max turns them into ||A||_inf
 //   symm_residual   R = B - A X, A symmetric from its lower triangle, one block per 32 rows
 //   to_f32 / axpy   R32 = float(R); X += double(D32)
 //   berr            eta = max_c ||r_c||_inf / (||A||_inf ||x_c||_inf + ||b_c||_inf)
@@ -38,16 +38,61 @@ __device__ __forceinline__ void atomic_max_nonneg(double *p, double v) {
   atomicMax(reinterpret_cast<unsigned long long *>(p), (unsigned long long)__double_as_longlong(v));
 }
 
-// With `scale` (nullable): A32 = D^-1/2 A D^-1/2, scale_i = 1 / sqrt(a_ii) (1 where a_ii <= 0,
-// which the factor then reports), computed in FP64 before rounding.
-__global__ void convert_lower_kernel(const double *A, int64_t lda, float *A32, int64_t lda32, int n,
-                                     const double *scale) {
-  const int64_t total = lda32 * (int64_t)n;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = e / lda32, i = e - j * lda32;
-    double v = (i >= j && i < n) ? A[j * lda + i] : 0.0;
-    if (scale && i < n) v *= scale[i] * scale[j];
-    A32[e] = (float)v;
+// One 32 x 32 tile (I, J), I >= J, of the lower triangle per block (32 x 8 threads): A32 =
+// float(A) (with `scale`, nullable: D^-1/2 A D^-1/2, scale_i = 1 / sqrt(a_ii), 1 where
+// a_ii <= 0, applied in FP64 before rounding), and the absolute row sums of the symmetric A
+// accumulated into rsum: |a_ij| counts for row i and, below the diagonal, for row j. The sums
+// are FP32 (the norm only scales the backward error, and FP64 adds would run on the FP64
+// pipe); entries above the diagonal of A32 are not written (nothing reads them).
+__global__ void __launch_bounds__(256) convert_lower_kernel(const double *A, int64_t lda, float *A32, int64_t lda32,
+                                                            int n, const double *scale, float *rsum) {
+  const int I = blockIdx.x, J = blockIdx.y;
+  if (J > I) return;
+  __shared__ float rs[8][33], cs[32];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int i = I * 32 + tx;
+  float rsum_i = 0.f;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int jl = ty + 8 * u, j = J * 32 + jl;
+    double v = 0.0;
+    if (i < n && j < n && i >= j) {
+      v = A[(int64_t)j * lda + i];
+      A32[(int64_t)j * lda32 + i] = (float)(scale ? v * scale[i] * scale[j] : v);
+    }
+    const float av = fabsf((float)v);
+    rsum_i += av;
+    // column j's entries below the diagonal count for row j (warp sum over the 32 rows)
+    float c = i > j ? av : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (tx == 0) cs[jl] = c;
+  }
+  rs[ty][tx] = rsum_i;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float t = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += rs[k][threadIdx.x];
+    if (I * 32 + threadIdx.x < n) atomicAdd(&rsum[I * 32 + threadIdx.x], t);
+    if (J * 32 + threadIdx.x < n) atomicAdd(&rsum[J * 32 + threadIdx.x], cs[threadIdx.x]);
+  }
+}
+
+// ||A||_inf = max_i rsum_i (one block)
+__global__ void norm_max_kernel(const float *rsum, int n, RefineCtrl *ctrl) {
+  __shared__ float w[32];
+  float m = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, rsum[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? w[threadIdx.x] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) ctrl->normA = (double)m;
   }
 }
 
@@ -58,57 +103,37 @@ __global__ void diag_scale_kernel(const double *A, int64_t lda, int n, double *s
   }
 }
 
-// Load block (I, J) of the symmetric A from its lower triangle into As[row in I][col in J]:
-// (I, J) itself for J < I, (J, I)^T for J > I, the symmetric diagonal block for J = I.
-__device__ __forceinline__ void load_sym_block(const double *A, int64_t lda, int I, int J, int n, double *As) {
+// Block (I, J) of the symmetric A from its lower triangle, as As[row in I][col in J]: (I, J)
+// itself for J < I, (J, I)^T for J > I (read along its columns, contiguous), the symmetric
+// diagonal block for J = I. sym_value gives element e (a = e mod 32, b = e / 32) of that read
+// and sym_slot the As slot it goes to.
+__device__ __forceinline__ double sym_value(const double *A, int64_t lda, int I, int J, int n, int e) {
   const int I0 = I * RB, J0 = J * RB, rows = min(RB, n - I0), jc = min(RB, n - J0);
-  for (int e = threadIdx.x; e < RB * RB; e += blockDim.x) {
-    const int a = e & 31, b = e >> 5;
-    double v = 0.0;
-    if (J < I) {          // As[a][b] = A(I0+a, J0+b)
-      if (a < rows && b < jc) v = A[(int64_t)(J0 + b) * lda + I0 + a];
-      As[a * RLD + b] = v;
-    } else if (J > I) {   // As[b][a] = A(J0+a, I0+b), read along a (contiguous)
-      if (a < jc && b < rows) v = A[(int64_t)(I0 + b) * lda + J0 + a];
-      As[b * RLD + a] = v;
-    } else {
-      if (a < rows && b < rows) v = a >= b ? A[(int64_t)(I0 + b) * lda + I0 + a] : A[(int64_t)(I0 + a) * lda + I0 + b];
-      As[a * RLD + b] = v;
-    }
-  }
+  const int a = e & 31, b = e >> 5;
+  if (J < I) return (a < rows && b < jc) ? __ldcg(A + (int64_t)(J0 + b) * lda + I0 + a) : 0.0;
+  if (J > I) return (a < jc && b < rows) ? __ldcg(A + (int64_t)(I0 + b) * lda + J0 + a) : 0.0;
+  if (a >= rows || b >= rows) return 0.0;
+  return a >= b ? __ldcg(A + (int64_t)(I0 + b) * lda + I0 + a) : __ldcg(A + (int64_t)(I0 + a) * lda + I0 + b);
+}
+__device__ __forceinline__ int sym_slot(int I, int J, int e) {
+  const int a = e & 31, b = e >> 5;
+  return J > I ? b * RLD + a : a * RLD + b;
 }
 
-// ||A||_inf = max_i sum_j |a_ij| of the symmetric A; one block per 32 rows
-__global__ void __launch_bounds__(256) rownorm_kernel(const double *A, int64_t lda, int n, RefineCtrl *ctrl) {
-  __shared__ double As[RB * RLD];
-  __shared__ double part[8][RB];
-  const int nrb = (n + RB - 1) / RB;
-  const int I = blockIdx.x;
-  const int tid = threadIdx.x, rr = tid & 31, cs = tid >> 5;
-  double s = 0.0;
-  for (int J = 0; J < nrb; ++J) {
-    load_sym_block(A, lda, I, J, n, As);
-    __syncthreads();
-#pragma unroll
-    for (int t = 0; t < 4; ++t) s += fabs(As[rr * RLD + cs + 8 * t]);
-    __syncthreads();
-  }
-  part[cs][rr] = s;
-  __syncthreads();
-  if (tid < RB && I * RB + tid < n) {
-    double t = 0.0;
-    for (int c = 0; c < 8; ++c) t += part[c][tid];
-    atomic_max_nonneg(&ctrl->normA, t);
-  }
-}
-
-// R = B - A X (FP64). Block (I, g): rows I*32.., columns g*64..; the 32 x 32 blocks of the
-// symmetric A come from its lower triangle (load_sym_block); the threads share the
-// products as described in blockacc.cuh.
+// R = B - A X (FP64). Block (I, g): rows I*32.., columns g*64..; the threads share the products
+// as described in blockacc.cuh. The blocks of A and X for step J + 1 are loaded into registers
+// while step J is multiplied, so the FP64 pipe does not wait for L2 between steps.
+//
+// The J range of a block row is cut into gridDim.z segments so that the grid has many more
+// blocks than the SMs hold at once (a block row per block left a ~20 % imbalance between SMs
+// holding three and four of them): segment s covers its share of J, starts from B when s = 0
+// and from 0 otherwise, and writes its partial sums to R + s * pstride; sum_partials_kernel
+// adds the segments in a fixed order (deterministic). With one segment R is written directly.
 template <int CPT>
-__global__ void __launch_bounds__(256) symm_residual_kernel(const double *A, int64_t lda, const double *X,
+__global__ void __launch_bounds__(256, 4) symm_residual_kernel(const double *A, int64_t lda, const double *X,
                                                             int64_t ldx, const double *B, int64_t ldb, double *R,
-                                                            int64_t ldr, int n, int nrhs, const int *skip) {
+                                                            int64_t ldr, int64_t pstride, int n, int nrhs,
+                                                            const int *skip) {
   __shared__ double As[RB * RLD];
   __shared__ double Xs[RB * RG];
   __shared__ double Red[RB * RG];
@@ -119,20 +144,38 @@ __global__ void __launch_bounds__(256) symm_residual_kernel(const double *A, int
   const int c0 = g * RG, cols = min(RG, nrhs - c0);
   const int tid = threadIdx.x, rr = tid & 31, warp = tid >> 5;
   const Slices<CPT> sl(cols, warp);
+  const int seg = blockIdx.z, nseg = gridDim.z;
+  const int Jlo = (int)((int64_t)nrb * seg / nseg), Jhi = (int)((int64_t)nrb * (seg + 1) / nseg);
+  R += (int64_t)seg * pstride;
   double acc[CPT];
 #pragma unroll
   for (int q = 0; q < CPT; ++q) {
     const int c = sl.col(q);
-    acc[q] = (sl.kslice == 0 && rr < rows && c < cols) ? B[(int64_t)(c0 + c) * ldb + I0 + rr] : 0.0;
+    acc[q] = (seg == 0 && sl.kslice == 0 && rr < rows && c < cols) ? B[(int64_t)(c0 + c) * ldb + I0 + rr] : 0.0;
   }
-  for (int J = 0; J < nrb; ++J) {
+  constexpr int NA = RB * RB / 256, NX = RB * RG / 256;
+  double ra[NA], rx[NX];
+  auto load = [&](int J) {
     const int J0 = J * RB, jc = min(RB, n - J0);
-    load_sym_block(A, lda, I, J, n, As);
-    for (int e = tid; e < RB * RG; e += 256) {
-      const int k = e & 31, c = e >> 5;
-      Xs[k * RG + c] = (k < jc && c < cols) ? X[(int64_t)(c0 + c) * ldx + J0 + k] : 0.0;
+#pragma unroll
+    for (int u = 0; u < NA; ++u) ra[u] = sym_value(A, lda, I, J, n, tid + 256 * u);
+#pragma unroll
+    for (int u = 0; u < NX; ++u) {
+      const int e = tid + 256 * u, k = e & 31, c = e >> 5;
+      rx[u] = (k < jc && c < cols) ? __ldcg(X + (int64_t)(c0 + c) * ldx + J0 + k) : 0.0;
+    }
+  };
+  if (Jlo < Jhi) load(Jlo);
+  for (int J = Jlo; J < Jhi; ++J) {
+#pragma unroll
+    for (int u = 0; u < NA; ++u) As[sym_slot(I, J, tid + 256 * u)] = ra[u];
+#pragma unroll
+    for (int u = 0; u < NX; ++u) {
+      const int e = tid + 256 * u;
+      Xs[(e & 31) * RG + (e >> 5)] = rx[u];
     }
     __syncthreads();
+    if (J + 1 < Jhi) load(J + 1);
     acc_step<double, CPT>(acc, As, RLD, Xs, RG, rr, sl);
     __syncthreads();
   }
@@ -140,6 +183,19 @@ __global__ void __launch_bounds__(256) symm_residual_kernel(const double *A, int
   for (int e = tid; e < RB * cols; e += 256) {
     const int i = e & 31, c = e >> 5;
     if (i < rows) R[(int64_t)(c0 + c) * ldr + I0 + i] = Xs[i * RG + c];
+  }
+}
+
+// R = sum over the segments of the partial residuals P + s * pstride (column-major, ld n)
+__global__ void sum_partials_kernel(const double *P, int64_t pstride, int nseg, int n, int nrhs, double *R,
+                                    int64_t ldr, const int *skip) {
+  if (skip && ld_volatile(skip)) return;
+  const int64_t total = (int64_t)n * nrhs;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / n, i = e - c * n;
+    double t = 0.0;
+    for (int sg = 0; sg < nseg; ++sg) t += P[sg * pstride + c * n + i];
+    R[c * ldr + i] = t;
   }
 }
 
@@ -234,8 +290,9 @@ __global__ void refine_out_kernel(const RefineCtrl *ctrl, int *dIters, double *d
 }
 
 struct RefineLayout {
-  size_t ctrl, a32, fwork, r, r32, swork, eta, finfo, scale, total, fbytes, sbytes;
+  size_t ctrl, a32, fwork, r, r32, swork, eta, finfo, scale, rsum, part, total, fbytes, sbytes;
   int64_t lda32, ld32;
+  int nseg;  // J segments of the residual
 };
 
 static RefineLayout refine_layout(int n, int nrhs, const chol_opts *opts) {
@@ -250,6 +307,16 @@ static RefineLayout refine_layout(int n, int nrhs, const chol_opts *opts) {
   L.fwork = o; o += align_up(L.fbytes, 256);
   L.r = o; o += align_up((size_t)n * std::max(nrhs, 1) * 8, 256);
   L.scale = o; o += align_up((size_t)std::max(n, 1) * 8, 256);
+  L.rsum = o; o += align_up((size_t)std::max(n, 1) * 8, 256);
+  {
+    // about nine waves of residual blocks at three blocks per SM
+    const int64_t rows = ((int64_t)n + RB - 1) / RB * (((int64_t)std::max(nrhs, 1) + RG - 1) / RG);
+    const DeviceInfo di = current_device_info();
+    const int64_t want = (int64_t)std::max(di.sms, 1) * 3 * 9;
+    L.nseg = (int)std::max<int64_t>(1, std::min<int64_t>({32, (want + rows - 1) / rows, ((int64_t)n + RB - 1) / RB}));
+  }
+  L.part = o;
+  if (L.nseg > 1) o += align_up((size_t)L.nseg * n * std::max(nrhs, 1) * 8, 256);
   L.r32 = o; o += align_up((size_t)L.ld32 * std::max(nrhs, 1) * 4, 256);
   L.sbytes = solve_workspace_bytes(n, nrhs);
   L.swork = o; o += align_up(L.sbytes, 256);
@@ -305,20 +372,29 @@ extern "C" chol_status chol_solve_refine(int n, int nrhs, const double *dA, int 
   // low-precision factor (of the diagonally scaled matrix for the BF16 forms)
   double *scale = prec == PREC_F32 ? nullptr : reinterpret_cast<double *>(ws + L.scale);
   if (scale) diag_scale_kernel<<<(n + 255) / 256, 256, 0, s>>>(dA, lda, n, scale);
-  convert_lower_kernel<<<eblocks, 256, 0, s>>>(dA, lda, A32, L.lda32, n, scale);
-  CHOL_CUDA_TRY(cudaGetLastError());
+  float *rsum = reinterpret_cast<float *>(ws + L.rsum);
+  CHOL_CUDA_TRY(cudaMemsetAsync(rsum, 0, (size_t)n * 4, s));
+  {
+    const int nt = (n + 31) / 32;
+    convert_lower_kernel<<<dim3(nt, nt), 256, 0, s>>>(dA, lda, A32, L.lda32, n, scale, rsum);
+    CHOL_CUDA_TRY(cudaGetLastError());
+  }
   chol_status st = factor_impl(prec, n, A32, (int)L.lda32, opts, ws + L.fwork, L.fbytes, finfo, stream);
   if (st != CHOL_OK) return st;
   CHOL_CUDA_TRY(cudaMemcpyAsync(dInfo, finfo, sizeof(int), cudaMemcpyDeviceToDevice, s));
   refine_init_kernel<<<1, 32, 0, s>>>(ctrl, finfo);
-  // ||A||_inf
-  rownorm_kernel<<<(n + RB - 1) / RB, 256, 0, s>>>(dA, lda, n, ctrl);
+  // ||A||_inf from the row sums of the conversion pass
+  norm_max_kernel<<<1, 1024, 0, s>>>(rsum, n, ctrl);
   CHOL_CUDA_TRY(cudaGetLastError());
   // x0 = 0, r0 = b
   CHOL_CUDA_TRY(cudaMemset2DAsync(dX, (size_t)ldx * 8, 0, (size_t)n * 8, nrhs, s));
   CHOL_CUDA_TRY(cudaMemcpy2DAsync(R, (size_t)n * 8, dB, (size_t)ldb * 8, (size_t)n * 8, nrhs,
                                   cudaMemcpyDeviceToDevice, s));
-  const dim3 rgrid((n + RB - 1) / RB, (nrhs + RG - 1) / RG);
+  const dim3 rgrid((n + RB - 1) / RB, (nrhs + RG - 1) / RG, L.nseg);
+  double *part = reinterpret_cast<double *>(ws + L.part);
+  // with segments the residual kernel writes partials (ld n), summed into R afterwards
+  double *Rout = L.nseg > 1 ? part : R;
+  const int64_t pstride = (int64_t)n * nrhs;
   for (int it = 0; it < max_iter; ++it) {
     to_f32_kernel<<<eblocks, 256, 0, s>>>(R, n, R32, L.ld32, n, nrhs, scale, skip);
     CHOL_CUDA_TRY(cudaGetLastError());
@@ -326,10 +402,15 @@ extern "C" chol_status chol_solve_refine(int n, int nrhs, const double *dA, int 
     if (st != CHOL_OK) return st;
     axpy_kernel<<<eblocks, 256, 0, s>>>(dX, ldx, R32, L.ld32, n, nrhs, scale, skip);
     const int cpt = cpt_for(std::min(nrhs, RG));
-    if (cpt == 8) symm_residual_kernel<8><<<rgrid, 256, 0, s>>>(dA, lda, dX, ldx, dB, ldb, R, n, n, nrhs, skip);
-    else if (cpt == 4) symm_residual_kernel<4><<<rgrid, 256, 0, s>>>(dA, lda, dX, ldx, dB, ldb, R, n, n, nrhs, skip);
-    else if (cpt == 2) symm_residual_kernel<2><<<rgrid, 256, 0, s>>>(dA, lda, dX, ldx, dB, ldb, R, n, n, nrhs, skip);
-    else symm_residual_kernel<1><<<rgrid, 256, 0, s>>>(dA, lda, dX, ldx, dB, ldb, R, n, n, nrhs, skip);
+    if (cpt == 8)
+      symm_residual_kernel<8><<<rgrid, 256, 0, s>>>(dA, lda, dX, ldx, dB, ldb, Rout, n, pstride, n, nrhs, skip);
+    else if (cpt == 4)
+      symm_residual_kernel<4><<<rgrid, 256, 0, s>>>(dA, lda, dX, ldx, dB, ldb, Rout, n, pstride, n, nrhs, skip);
+    else if (cpt == 2)
+      symm_residual_kernel<2><<<rgrid, 256, 0, s>>>(dA, lda, dX, ldx, dB, ldb, Rout, n, pstride, n, nrhs, skip);
+    else
+      symm_residual_kernel<1><<<rgrid, 256, 0, s>>>(dA, lda, dX, ldx, dB, ldb, Rout, n, pstride, n, nrhs, skip);
+    if (L.nseg > 1) sum_partials_kernel<<<eblocks, 256, 0, s>>>(part, pstride, L.nseg, n, nrhs, R, n, skip);
     berr_cols_kernel<<<nrhs, 256, 0, s>>>(R, n, dX, ldx, dB, ldb, n, ctrl, eta, skip);
     refine_step_done_kernel<<<1, 32, 0, s>>>(ctrl, eta, nrhs, tol, finfo);
     CHOL_CUDA_TRY(cudaGetLastError());

@@ -8,12 +8,17 @@
 // and are held by running blocks: the sweep always progresses, with or without co-residency.
 //
 // Inside an item the eight warps split the blocks m (warp w takes m = w, w + 8, ... in the
-// order the sweep produces them) and work independently: a warp loads its L block, waits for
-// its m's flag (one lane polls, bounded), stages Y_m in its own shared-memory rows and
-// accumulates into registers (lane = row of the item, one register per right-hand side). The
-// block synchronises once per item, to add the eight partial sums; the chain from one block
-// row to the next is therefore one L2 round trip for Y, one warp's 32 x 32 product, the sum
-// and the diagonal solve. Waits are bounded (timeout -> CHOL_INFO_TIMEOUT in *dInfo).
+// order the sweep produces them) and work independently: a warp loads its L block, obtains
+// Y_m, stages it in its own shared-memory rows and accumulates into registers (lane = row of
+// the item, one register per right-hand side). The block synchronises once per item, to add
+// the eight partial sums.
+//
+// A solved block publishes a ready flag after a release fence; a warp checks the flags of its
+// next 32 blocks with one load per lane (blocks solved long ago cost no polling round trip)
+// and polls only a block that is not ready yet. Waits are bounded (timeout ->
+// CHOL_INFO_TIMEOUT in *dInfo). In FP32 (the refinement's sweeps) the 32 x 32 diagonal block
+// is inverted while the item accumulates, so the chain only carries its product with the
+// block; FP64 keeps the substitution (exact on integer data).
 //
 // The kernel is instantiated for FP64 (chol_solve) and FP32 (the low-precision solves of
 // the mixed-precision refinement). In FP64 both sweeps are bound by the FP64 pipe (n^2 nrhs
@@ -72,7 +77,8 @@ struct SolveSmem {
   static constexpr size_t LT = (size_t)SNW * SB * SLD;  // per-warp transposed L block (backward)
   static constexpr size_t YS = (size_t)SB * YLD;        // the item's block before the diagonal solve
   static constexpr size_t LD = (size_t)SB * SLD + SB;   // diagonal block and its reciprocals
-  static constexpr size_t NEED = (YW + LT + YS + LD) * sizeof(T);
+  static constexpr size_t DI = (size_t)SB * SLD;        // inverse of the diagonal block (FP32)
+  static constexpr size_t NEED = (YW + LT + YS + LD + DI) * sizeof(T);
   static constexpr size_t BYTES = NEED > (size_t)SOLVE_EXCL_SMEM ? NEED : (size_t)SOLVE_EXCL_SMEM;
 };
 
@@ -103,6 +109,8 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
   T *Ys = Lt + S::LT;
   T *Ld = Ys + S::YS;
   T *Rs = Ld + SB * SLD;
+  T *Di = Rs + SB;
+  constexpr bool INV = sizeof(T) == 4;  // FP32: multiply by the inverted diagonal block
   __shared__ long long s_item;
   __shared__ int s_abort;
   const T *L = static_cast<const T *>(a.L);
@@ -133,6 +141,25 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
                                                           : (i == j ? T(1) : T(0));
     }
     if (tid < SB) Rs[tid] = tid < rows ? T(1) / __ldcg(L + (int64_t)(r0 + tid) * a.lda + r0 + tid) : T(1);
+    if (INV) {
+      // D^-1 by columns: lane j of warp 0 solves D y = e_j (right-looking, register resident;
+      // y stays zero above row j, so no lane needs a predicate), while the other warps start
+      // accumulating. Identity padding past the end of the matrix gives an identity inverse.
+      __syncthreads();
+      if (warp == 0) {
+        T y[SB];
+#pragma unroll
+        for (int i = 0; i < SB; ++i) y[i] = i == lane ? T(1) : T(0);
+#pragma unroll
+        for (int k = 0; k < SB; ++k) {
+          y[k] = squot(y[k], Ld[k * SLD + k], Rs[k]);
+#pragma unroll
+          for (int i = k + 1; i < SB; ++i) y[i] = fma(-Ld[i * SLD + k], y[k], y[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < SB; ++i) Di[i * SLD + lane] = y[i];
+      }
+    }
     // this thread's entries of B_r for the final sum, loaded now (off the chain)
     constexpr int BPT = (SB * NC + SNT - 1) / SNT;
     T bv[BPT];
@@ -147,11 +174,16 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
     for (int q = 0; q < NC; ++q) acc[q] = T(0);
     const int nsteps = a.trans ? a.nrb - 1 - r : r;
     int wab = 0;
+    // readiness of the warp's next 32 blocks: bit j <-> step mbase + SNW j, one flag load per
+    // lane and a ballot, so blocks solved long ago cost no polling round trip
+    unsigned ready = 0u;
+    int mbase = warp;
     for (int step = warp; step < nsteps; step += SNW) {
       const int m = a.trans ? a.nrb - 1 - step : step;
       const int m0 = m * SB, mrows = min(SB, a.n - m0);
-      // L block, issued before the wait. Forward: lane = row of the item, lr[k] = L_rm(lane, k).
-      // Backward: lane = row k of block m, lr[i] = L_mr(lane, i), staged transposed below.
+      // L block, issued before any wait (it does not depend on other items). Forward: lane =
+      // row of the item, lr[k] = L_rm(lane, k). Backward: lane = row k of block m,
+      // lr[i] = L_mr(lane, i), staged transposed below.
       T lr[SB];
       if (!a.trans) {
 #pragma unroll
@@ -162,31 +194,50 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
         for (int i = 0; i < SB; ++i)
           lr[i] = (lane < mrows && i < rows) ? __ldcg(L + (int64_t)(r0 + i) * a.lda + m0 + lane) : T(0);
       }
-      // wait until block m of this group is solved
-      if (lane == 0) {
-        const uint64_t t0 = globaltimer_ns();
-        int64_t spins = 0;
-        unsigned slp = 32;
-        while (ld_volatile(&a.flags[(int64_t)m * a.ngroups + g]) == 0) {
-          if (ld_volatile(&a.ctrl->abort)) { wab = 1; break; }
-          if (globaltimer_ns() - t0 > (uint64_t)a.timeout_ns || ++spins > (a.timeout_ns >> 7) + 100000) {
-            atomicCAS(&a.ctrl->info, 0, CHOL_INFO_TIMEOUT);
-            atomicExch(&a.ctrl->abort, 1);
-            wab = 1;
-            break;
-          }
-          __nanosleep(slp);
-          slp = slp < 128 ? slp * 2 : 128;
+      T yv[NC];
+      int jb = (step - mbase) / SNW;
+      if (jb >= 32 || !((ready >> jb) & 1u)) {
+        const int sl = step + SNW * lane;
+        int f = 1;
+        if (sl < nsteps) {
+          const int ml = a.trans ? a.nrb - 1 - sl : sl;
+          f = ld_volatile(&a.flags[(int64_t)ml * a.ngroups + g]) != 0;
         }
+        ready = __ballot_sync(0xffffffffu, f);
+        mbase = step;
+        jb = 0;
+        if (!(ready & 1u)) {
+          // wait until block m of this group is solved (one lane, bounded)
+          if (lane == 0) {
+            const uint64_t t0 = globaltimer_ns();
+            int64_t spins = 0;
+            unsigned slp = 32;
+            while (ld_volatile(&a.flags[(int64_t)m * a.ngroups + g]) == 0) {
+              if (ld_volatile(&a.ctrl->abort)) { wab = 1; break; }
+              if (globaltimer_ns() - t0 > (uint64_t)a.timeout_ns || ++spins > (a.timeout_ns >> 7) + 100000) {
+                atomicCAS(&a.ctrl->info, 0, CHOL_INFO_TIMEOUT);
+                atomicExch(&a.ctrl->abort, 1);
+                wab = 1;
+                break;
+              }
+              __nanosleep(slp);
+              slp = slp < 128 ? slp * 2 : 128;
+            }
+          }
+          wab = __shfl_sync(0xffffffffu, wab, 0);
+          if (wab) break;
+          ready = 1u;  // only this block is known to be solved
+        }
+        // every flag this warp observed is ordered before the loads of the blocks' data
         __threadfence();
+        __syncwarp();
       }
-      __syncwarp();
-      wab = __shfl_sync(0xffffffffu, wab, 0);
-      if (wab) break;
-      // Y block m: lane k stages row k
+      // Y block m (lane k stages row k), loaded once the block is known to be solved
 #pragma unroll
       for (int q = 0; q < NC; ++q)
-        yw[lane * YLD + q] = (lane < mrows && q < cols) ? __ldcg(B + (int64_t)(c0 + q) * a.ldb + m0 + lane) : T(0);
+        yv[q] = (lane < mrows && q < cols) ? __ldcg(B + (int64_t)(c0 + q) * a.ldb + m0 + lane) : T(0);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) yw[lane * YLD + q] = yv[q];
       if (a.trans) {
 #pragma unroll
         for (int i = 0; i < SB; ++i) lt[lane * SLD + i] = lr[i];
@@ -222,8 +273,23 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
       }
     }
     __syncthreads();
-    // diagonal block: one thread per right-hand side runs the substitution
-    if (tid < cols) {
+    T *Xo = Ys;  // the solved block, row-major with stride YLD
+    if (INV) {
+      // forward x = D^-1 (b - sum), backward x = D^-T (b - sum): independent 32-term
+      // products (D^-1 is zero above the diagonal)
+      Xo = Yw;     // free once the partial sums are added
+#pragma unroll
+      for (int u = 0; u < (SB * NC + SNT - 1) / SNT; ++u) {
+        const int e = tid + u * SNT, i = e & (SB - 1), q = e >> 5;
+        if (e < SB * NC) {
+          T t = T(0);
+#pragma unroll
+          for (int k = 0; k < SB; ++k) t = fma(a.trans ? Di[k * SLD + i] : Di[i * SLD + k], Ys[k * YLD + q], t);
+          Xo[i * YLD + q] = t;
+        }
+      }
+    } else if (tid < cols) {
+      // diagonal block: one thread per right-hand side runs the substitution
       const int c = tid;
       T x[SB];
 #pragma unroll
@@ -246,9 +312,12 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
         }
       }
 #pragma unroll
-      for (int i = 0; i < SB; ++i)
-        if (i < rows) __stcg(B + (int64_t)(c0 + c) * a.ldb + r0 + i, x[i]);
+      for (int i = 0; i < SB; ++i) Ys[i * YLD + c] = x[i];
     }
+    __syncthreads();
+    // write the solved block column by column (one warp per column: 32 consecutive rows)
+    for (int c = warp; c < cols; c += SNW)
+      if (lane < rows) __stcg(B + (int64_t)(c0 + c) * a.ldb + r0 + lane, Xo[lane * YLD + c]);
     __threadfence();
     __syncthreads();
     if (tid == 0) *(volatile int *)&a.flags[(int64_t)r * a.ngroups + g] = 1;
