@@ -245,6 +245,16 @@ size_t chol_batched_workspace_size(int batch);
 chol_status chol_posv_batched(int precision, int batch, const int *dN, void *const *dA, const int *dLda,
                               void *const *dB, int *dInfo, const chol_batch_opts *bopts, void *dWork,
                               size_t work_bytes, void *stream);
+/* chol_posv_batched without right-hand sides: factor every matrix in place. */
+chol_status chol_factor_batched(int precision, int batch, const int *dN, void *const *dA, const int *dLda,
+                                int *dInfo, const chol_batch_opts *bopts, void *dWork, size_t work_bytes,
+                                void *stream);
+/* Forward and back substitution only: dL[m] holds the factor of matrix m (lower triangle, as
+ * left by chol_factor_batched), dB[m] its right-hand-side vector, overwritten by the solution
+ * (NULL entries are skipped). dInfo[m] = 0, or CHOL_INFO_BAD_ARG for an invalid size. */
+chol_status chol_solve_batched(int precision, int batch, const int *dN, void *const *dL, const int *dLda,
+                               void *const *dB, int *dInfo, const chol_batch_opts *bopts, void *dWork,
+                               size_t work_bytes, void *stream);
 /* Autotuner: times every launch shape (workers per SM x order) on the given batch, copying
  * the matrices dAsrc into dAscratch before each run (both arrays of device pointers with the
  * same orders and leading dimensions), and writes the fastest shape to *best (and its time in

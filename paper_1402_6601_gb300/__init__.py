@@ -20,7 +20,8 @@ __all__ = [
     "lib", "ChOpts", "POLICIES", "opts", "colmajor", "factor", "solve", "trsm_sweep", "posv",
     "posv_host", "workspace_size", "solve_workspace_size", "num_workers", "trace", "factor_f32",
     "solve_refine", "refine_workspace_size", "cholesky_backward", "solve_backward", "lower",
-    "cholesky", "cholesky_solve", "solve_spd", "BatchOpts", "Batch", "posv_batched", "batched_autotune",
+    "cholesky", "cholesky_solve", "solve_spd", "BatchOpts", "Batch", "posv_batched", "factor_batched",
+    "solve_batched", "batched_autotune",
     "dag_describe", "dag_bottom_levels", "sched_activate", "sched_activate_device",
     "CholeskyError",
 ]
@@ -85,6 +86,8 @@ _SIGNATURES = {
     "chol_batch_opts_default": (None, [_P]),
     "chol_batched_workspace_size": (_SZ, [_I]),
     "chol_posv_batched": (_I, [_I, _I, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "chol_factor_batched": (_I, [_I, _I, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "chol_solve_batched": (_I, [_I, _I, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "chol_batched_autotune": (_I, [_I, _I, _P, _P, _P, _P, _P, _P, _SZ, _P, _P, _P]),
     "chol_posv_host_stage_size": (_SZ, [_I, _I, _OPTS]),
     "chol_posv_host": (_I, [_I, _I, _P, _I, _P, _I, _OPTS, _P, _SZ, _P, _P]),
@@ -581,6 +584,31 @@ def posv_batched(batch, bopts=None, stream=None, factor_only=False):
     _check(lib.chol_posv_batched(_prec(batch.flat), batch.batch, batch.N.data_ptr(), batch.A.data_ptr(),
                                  batch.lda.data_ptr(), bptr, batch.info.data_ptr(), ctypes.byref(o),
                                  batch.work.data_ptr(), batch.work.numel(), _stream(stream)), "chol_posv_batched")
+    return batch.info
+
+
+def factor_batched(batch, bopts=None, stream=None):
+    """Factor every matrix of `batch` in place (no right-hand sides). Asynchronous."""
+    o = bopts if bopts is not None else BatchOpts()
+    if bopts is None:
+        lib.chol_batch_opts_default(ctypes.byref(o))
+    _check(lib.chol_factor_batched(_prec(batch.flat), batch.batch, batch.N.data_ptr(), batch.A.data_ptr(),
+                                   batch.lda.data_ptr(), batch.info.data_ptr(), ctypes.byref(o),
+                                   batch.work.data_ptr(), batch.work.numel(), _stream(stream)), "chol_factor_batched")
+    return batch.info
+
+
+def solve_batched(batch, bopts=None, stream=None):
+    """Solve every matrix's right-hand side with the factors already in `batch` (from
+    factor_batched). Asynchronous."""
+    if batch.B is None:
+        raise ValueError("the batch has no right-hand sides")
+    o = bopts if bopts is not None else BatchOpts()
+    if bopts is None:
+        lib.chol_batch_opts_default(ctypes.byref(o))
+    _check(lib.chol_solve_batched(_prec(batch.flat), batch.batch, batch.N.data_ptr(), batch.A.data_ptr(),
+                                  batch.lda.data_ptr(), batch.B.data_ptr(), batch.info.data_ptr(), ctypes.byref(o),
+                                  batch.work.data_ptr(), batch.work.numel(), _stream(stream)), "chol_solve_batched")
     return batch.info
 
 

@@ -28,6 +28,7 @@ struct BatchArgs {
   int *info;
   const int *order;
   unsigned int *counter;
+  int solve_only;  // 1: A already holds the factors; only the substitutions run
 };
 
 // order = indices sorted by decreasing N (ties in any order), or the identity; counter = 0
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(NT, MINB) batched_kernel(const __grid_constant
       __syncthreads();
       continue;
     }
-    const int f = n > 0 ? BatchTiles<T>::potrf(A, lda, n, smem) : 0;
+    const int f = (n > 0 && !a.solve_only) ? BatchTiles<T>::potrf(A, lda, n, smem) : 0;
     if (threadIdx.x == 0) a.info[m] = f;
     if (!f && n > 0 && a.B && a.B[m]) block_solve_vec<T>(A, lda, n, static_cast<T *>(a.B[m]), smem);
     __syncthreads();
@@ -210,9 +211,9 @@ extern "C" size_t chol_batched_workspace_size(int batch) {
   return batch_ws(batch);
 }
 
-extern "C" chol_status chol_posv_batched(int precision, int batch, const int *dN, void *const *dA, const int *dLda,
-                                         void *const *dB, int *dInfo, const chol_batch_opts *bopts, void *dWork,
-                                         size_t work_bytes, void *stream) {
+static chol_status batched_impl(int precision, int batch, const int *dN, void *const *dA, const int *dLda,
+                                void *const *dB, int *dInfo, const chol_batch_opts *bopts, void *dWork,
+                                size_t work_bytes, void *stream, int solve_only) {
   if (batch < 0 || (precision != CHOL_F64 && precision != CHOL_F32)) return CHOL_ERR_INVALID_ARG;
   if (batch == 0) return CHOL_OK;
   if (!dN || !dA || !dLda || !dInfo) return CHOL_ERR_INVALID_ARG;
@@ -234,6 +235,7 @@ extern "C" chol_status chol_posv_batched(int precision, int batch, const int *dN
   a.info = dInfo;
   a.counter = reinterpret_cast<unsigned int *>(ws);
   a.order = reinterpret_cast<int *>(ws + 256);
+  a.solve_only = solve_only;
   batch_order_kernel<<<1, 1024, 0, s>>>(batch, dN, const_cast<int *>(a.order), o.lpt_order, a.counter);
   CHOL_CUDA_TRY(cudaGetLastError());
   cudaError_t e;
@@ -248,6 +250,26 @@ extern "C" chol_status chol_posv_batched(int precision, int batch, const int *dN
   }
   CHOL_CUDA_TRY(e);
   return CHOL_OK;
+}
+
+extern "C" chol_status chol_posv_batched(int precision, int batch, const int *dN, void *const *dA, const int *dLda,
+                                         void *const *dB, int *dInfo, const chol_batch_opts *bopts, void *dWork,
+                                         size_t work_bytes, void *stream) {
+  return batched_impl(precision, batch, dN, dA, dLda, dB, dInfo, bopts, dWork, work_bytes, stream, 0);
+}
+
+extern "C" chol_status chol_factor_batched(int precision, int batch, const int *dN, void *const *dA,
+                                           const int *dLda, int *dInfo, const chol_batch_opts *bopts, void *dWork,
+                                           size_t work_bytes, void *stream) {
+  return batched_impl(precision, batch, dN, dA, dLda, nullptr, dInfo, bopts, dWork, work_bytes, stream, 0);
+}
+
+extern "C" chol_status chol_solve_batched(int precision, int batch, const int *dN, void *const *dL,
+                                          const int *dLda, void *const *dB, int *dInfo,
+                                          const chol_batch_opts *bopts, void *dWork, size_t work_bytes,
+                                          void *stream) {
+  if (batch > 0 && !dB) return CHOL_ERR_INVALID_ARG;
+  return batched_impl(precision, batch, dN, dL, dLda, dB, dInfo, bopts, dWork, work_bytes, stream, 1);
 }
 
 extern "C" chol_status chol_batched_autotune(int precision, int batch, const int *dN, void *const *dAsrc,

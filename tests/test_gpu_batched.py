@@ -114,3 +114,29 @@ def test_batched_graph_replay_and_autotune(chol):
         g.replay()
         torch.cuda.synchronize()
         assert torch.equal(work.flat, ref_flat) and torch.equal(work.rhs_flat, ref_rhs)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_factor_then_solve_batched_equals_posv(chol, dtype):
+    # chol_factor_batched followed by chol_solve_batched runs the same bodies in the same
+    # order as chol_posv_batched: bitwise the same factors and solutions
+    rng = np.random.default_rng(7)
+    orders = [int(x) for x in rng.integers(1, 260, size=90)] + [0, 32, 33]
+    one = _make(chol, orders, dtype=dtype, seed=9)
+    two = _make(chol, orders, dtype=dtype, seed=9)
+    A0 = [one.matrix(m).cpu().numpy().astype(np.float64) for m in range(one.batch)]
+    b0 = [one.rhs(m).cpu().numpy().astype(np.float64) for m in range(one.batch)]
+    chol.posv_batched(one)
+    chol.factor_batched(two)
+    torch.cuda.synchronize()
+    assert int(two.info.abs().max().item()) == 0
+    chol.solve_batched(two)
+    torch.cuda.synchronize()
+    assert int(two.info.abs().max().item()) == 0
+    assert torch.equal(one.flat, two.flat)
+    assert torch.equal(one.rhs_flat, two.rhs_flat)
+    tol = 1e-14 if dtype == torch.float64 else 1e-6
+    for m in range(0, one.batch, 7):
+        if orders[m] == 0:
+            continue
+        assert oracle.backward_error(A0[m], two.rhs(m).cpu().numpy().astype(np.float64), b0[m]) <= tol, m
