@@ -165,10 +165,16 @@ chol_status chol_factor_f32(int n, float *dA, int lda, const chol_opts *opts, vo
                             size_t work_bytes, int *dInfo, void *stream);
 
 /* chol_factor_f32 with the tile bodies of `precision` (CHOL_F32, CHOL_BF16 or CHOL_BF16X3;
- * others return CHOL_ERR_INVALID_ARG). Same workspace size. A wait of the tensor-core update
+ * others return CHOL_ERR_INVALID_ARG), workspace chol_factor_lowp_workspace_size. A wait of the
+ * tensor-core update
  * that exceeds its 2 s limit ends the call with *dInfo = CHOL_INFO_TIMEOUT. */
 chol_status chol_factor_lowp(int precision, int n, float *dA, int lda, const chol_opts *opts, void *dWork,
                              size_t work_bytes, int *dInfo, void *stream);
+/* Workspace of chol_factor_lowp in `precision`. For the BF16 forms with a tile size that is a
+ * multiple of 32 and at most 256 it includes a side buffer of the panel tiles' BF16 terms
+ * (T (T - 1) / 2 tiles of nb / 32 x NTERM x 16 KiB: 384 KiB per tile of 256 for CHOL_BF16X3),
+ * written by each panel's TRSM and bulk-copied by the tile updates. */
+size_t chol_factor_lowp_workspace_size(int precision, int n, const chol_opts *opts);
 
 /* Solve A X = B to a normwise backward error <= tol (Rigal-Gaches, infinity norm, maximised
  * over the right-hand sides) with a factor in `low_precision` (CHOL_F32, CHOL_BF16 or
@@ -189,7 +195,8 @@ chol_status chol_factor_lowp(int precision, int n, float *dA, int lda, const cho
  * All steps run on `stream` with no host synchronisation: every step's kernels return at
  * once after convergence, so the call is one fixed sequence of launches.
  */
-size_t chol_solve_refine_workspace_size(int n, int nrhs, const chol_opts *opts);
+size_t chol_solve_refine_workspace_size(int n, int nrhs, const chol_opts *opts);  /* any form */
+size_t chol_solve_refine_prec_workspace_size(int low_precision, int n, int nrhs, const chol_opts *opts);
 chol_status chol_solve_refine(int n, int nrhs, const double *dA, int lda, const double *dB, int ldb,
                               double *dX, int ldx, int low_precision, double tol, int max_iter,
                               const chol_opts *opts, void *dWork, size_t work_bytes, int *dInfo,

@@ -76,6 +76,8 @@ _SIGNATURES = {
     "chol_solve_noalloc": (_I, [_I, _I, _P, _I, _P, _I, _P, _P]),
     "chol_factor_f32": (_I, [_I, _P, _I, _OPTS, _P, _SZ, _P, _P]),
     "chol_factor_lowp": (_I, [_I, _I, _P, _I, _OPTS, _P, _SZ, _P, _P]),
+    "chol_factor_lowp_workspace_size": (_SZ, [_I, _I, _OPTS]),
+    "chol_solve_refine_prec_workspace_size": (_SZ, [_I, _I, _I, _OPTS]),
     "chol_solve_refine_workspace_size": (_SZ, [_I, _I, _OPTS]),
     "chol_solve_refine": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _I, _D, _I, _OPTS, _P, _SZ, _P, _P, _P, _P]),
     "chol_backward_workspace_size": (_SZ, [_I]),
@@ -235,7 +237,7 @@ def factor_f32(A, o=None, work=None, info=None, stream=None, check=False, precis
         raise ValueError("A must be column-major (stride(0) == 1); use colmajor()")
     lda = max(1, A.stride(1) if n > 1 else n)
     if work is None:
-        work = _workspace(workspace_size(n, o), A.device)
+        work = _workspace(int(lib.chol_factor_lowp_workspace_size(prec, n, ctypes.byref(o))), A.device)
     if info is None:
         info = torch.zeros(1, dtype=torch.int32, device=A.device)
     _check(lib.chol_factor_lowp(prec, n, A.data_ptr(), lda, ctypes.byref(o), work.data_ptr(), work.numel(),
@@ -245,9 +247,17 @@ def factor_f32(A, o=None, work=None, info=None, stream=None, check=False, precis
     return info, work
 
 
-def refine_workspace_size(n, nrhs, o=None):
+def refine_workspace_size(n, nrhs, o=None, precision=None):
+    """Workspace of solve_refine: for one low-precision form, or (None) for any of them."""
     o = o or opts()
-    return int(lib.chol_solve_refine_workspace_size(n, nrhs, ctypes.byref(o)))
+    if precision is None:
+        return int(lib.chol_solve_refine_workspace_size(n, nrhs, ctypes.byref(o)))
+    return int(lib.chol_solve_refine_prec_workspace_size(_PREC[precision], n, nrhs, ctypes.byref(o)))
+
+
+def lowp_workspace_size(n, o=None, precision="bf16x3"):
+    o = o or opts()
+    return int(lib.chol_factor_lowp_workspace_size(_PREC[precision], n, ctypes.byref(o)))
 
 
 def solve_refine(A, B, X=None, tol=1e-14, max_iter=30, o=None, work=None, stream=None, precision="f32"):
@@ -263,7 +273,7 @@ def solve_refine(A, B, X=None, tol=1e-14, max_iter=30, o=None, work=None, stream
         X = colmajor(torch.empty(n, nrhs, dtype=torch.float64, device=A.device))
     ldx = _check_matrix(X, "X")
     if work is None:
-        work = _workspace(refine_workspace_size(n, nrhs, o), A.device)
+        work = _workspace(refine_workspace_size(n, nrhs, o, precision), A.device)
     info = torch.zeros(1, dtype=torch.int32, device=A.device)
     iters = torch.zeros(1, dtype=torch.int32, device=A.device)
     berr = torch.zeros(1, dtype=torch.float64, device=A.device)

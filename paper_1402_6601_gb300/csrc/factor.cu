@@ -64,6 +64,8 @@ struct FactorArgs {
   long long *trace_buf;
   int use_cp;       // communication prediction in the placement
   int64_t comm_ns;  // predicted cost of one input tile a worker did not write last
+  unsigned char *split;  // tensor-core forms: BF16 terms of the panel tiles (nullable)
+  int64_t split_tile;    // bytes per panel tile in `split`
 };
 
 struct Resolved {
@@ -77,7 +79,8 @@ struct Resolved {
 };
 
 struct Layout {
-  size_t ctrl, trace, zero_begin, qhead, qcount, qcost, run_end, slots, zero_end, cnt, owner, bl, total;
+  size_t ctrl, trace, zero_begin, qhead, qcount, qcost, run_end, slots, zero_end, cnt, owner, bl, split, total;
+  size_t split_tile;
   int C;
   int64_t ntasks;
 };
@@ -114,6 +117,14 @@ static Layout make_layout(int n, const Resolved &r, int W) {
   L.cnt = o; o += align_up((size_t)L.ntasks * 4, 256);
   L.owner = o; o += align_up((size_t)T * T * 4, 256);
   L.bl = o; o += align_up((size_t)L.ntasks * 8, 256);
+  // tensor-core forms with 32-aligned tiles up to 256: the panel tiles' BF16 terms, written by
+  // their TRSM and bulk-copied by the updates that use them (T (T - 1) / 2 panel tiles)
+  L.split = o;
+  L.split_tile = 0;
+  if ((r.prec == PREC_BF16 || r.prec == PREC_BF16X3) && r.nb % 32 == 0 && r.nb <= 256) {
+    L.split_tile = r.prec == PREC_BF16 ? tc::Split<1>::tile_bytes(r.nb) : tc::Split<3>::tile_bytes(r.nb);
+    o += align_up((size_t)T * (T - 1) / 2 * L.split_tile, 256);
+  }
   L.total = o;
   (void)n;
   return L;
@@ -380,11 +391,11 @@ struct TilesF64 {
   static constexpr int SMEM = TILE_SMEM_BYTES;
   static constexpr int MIN_BLOCKS = 2;  // two workers per SM share the FP64 pipe
   __device__ static int potrf(T *G, int64_t ld, int nk, T *s) { return potrf_tile(G, ld, nk, s); }
-  __device__ static void trsm(T *B, int64_t ldb, const T *L, int64_t ldl, int mb, int nk, T *s) {
+  __device__ static void trsm(T *B, int64_t ldb, const T *L, int64_t ldl, int mb, int nk, T *s, unsigned char *) {
     trsm_tile(B, ldb, L, ldl, mb, nk, s);
   }
   __device__ static int update(T *C, int64_t ldc, const T *A, int64_t lda, const T *B, int64_t ldb, int M,
-                               int N, int K, bool lower, T *s) {
+                               int N, int K, bool lower, T *s, const unsigned char *, const unsigned char *) {
     update_nt(C, ldc, A, lda, B, ldb, M, N, K, lower, s);
     return 0;
   }
@@ -400,12 +411,12 @@ struct TilesF32 {
   __device__ static int potrf(T *G, int64_t ld, int nk, T *s) {
     return nk <= f32::PANEL_MAX_N ? f32::potrf_tile_smem(G, ld, nk, s) : f32::potrf_tile(G, ld, nk, s);
   }
-  __device__ static void trsm(T *B, int64_t ldb, const T *L, int64_t ldl, int mb, int nk, T *s) {
+  __device__ static void trsm(T *B, int64_t ldb, const T *L, int64_t ldl, int mb, int nk, T *s, unsigned char *) {
     if (nk <= f32::PANEL_MAX_N) f32::trsm_tile_rows(B, ldb, L, ldl, mb, nk, s);
     else f32::trsm_tile(B, ldb, L, ldl, mb, nk, s);
   }
   __device__ static int update(T *C, int64_t ldc, const T *A, int64_t lda, const T *B, int64_t ldb, int M,
-                               int N, int K, bool lower, T *s) {
+                               int N, int K, bool lower, T *s, const unsigned char *, const unsigned char *) {
     f32::update_nt(C, ldc, A, lda, B, ldb, M, N, K, lower, s);
     return 0;
   }
@@ -423,14 +434,29 @@ struct TilesTC : TilesF32 {
     __shared__ tc::State st;
     return st;
   }
+  // with a side buffer the TRSM also writes the tile's BF16 terms, and the updates bulk-copy
+  // them; without one the updates split their FP32 operands themselves
+  __device__ static void trsm(T *B, int64_t ldb, const T *L, int64_t ldl, int mb, int nk, T *s,
+                              unsigned char *split) {
+    if (split && nk <= f32::PANEL_MAX_N)
+      f32::trsm_tile_rows(B, ldb, L, ldl, mb, nk, s, tc::SplitEmit<NTERM>{split});
+    else
+      TilesF32::trsm(B, ldb, L, ldl, mb, nk, s, nullptr);
+  }
   __device__ static int update(T *C, int64_t ldc, const T *A, int64_t lda, const T *B, int64_t ldb, int M,
-                               int N, int K, bool lower, T *s) {
-    return tc::update_nt<NTERM>(C, ldc, A, lda, B, ldb, M, N, K, lower, reinterpret_cast<unsigned char *>(s),
-                                state());
+                               int N, int K, bool lower, T *s, const unsigned char *sa, const unsigned char *sb) {
+    unsigned char *sm = reinterpret_cast<unsigned char *>(s);
+    if (sa && sb) return tc::update_nt_split<NTERM>(C, ldc, sa, sb, M, N, K, lower, sm, state());
+    return tc::update_nt<NTERM>(C, ldc, A, lda, B, ldb, M, N, K, lower, sm, state());
   }
   __device__ static void begin() { tc::begin(state()); }
   __device__ static void end() { tc::end(state()); }
 };
+
+// BF16 terms of panel tile (i, k), i > k, in the side buffer (nullptr without one)
+__device__ __forceinline__ unsigned char *split_ptr(const FactorArgs &a, int i, int k) {
+  return a.split ? a.split + ((int64_t)i * (i - 1) / 2 + k) * a.split_tile : nullptr;
+}
 
 // Run one tile task with the whole block. Returns 0 or a 1-based failing global column.
 template <class P>
@@ -443,18 +469,18 @@ __device__ int run_task(const FactorArgs &a, const TaskDesc &d, typename P::T *s
     }
     case K_TRSM:
       P::trsm(tile_ptr<T>(a, d.i, d.k), a.lda, tile_ptr<T>(a, d.k, d.k), a.lda, tile_dim(a, d.i),
-              tile_dim(a, d.k), smem);
+              tile_dim(a, d.k), smem, split_ptr(a, d.i, d.k));
       return 0;
     case K_SYRK:  // a nonzero return is an expired wait inside the tile update
       return P::update(tile_ptr<T>(a, d.i, d.i), a.lda, tile_ptr<T>(a, d.i, d.k), a.lda,
                        tile_ptr<T>(a, d.i, d.k), a.lda, tile_dim(a, d.i), tile_dim(a, d.i), tile_dim(a, d.k),
-                       true, smem)
+                       true, smem, split_ptr(a, d.i, d.k), split_ptr(a, d.i, d.k))
                  ? CHOL_INFO_TIMEOUT
                  : 0;
     default:
       return P::update(tile_ptr<T>(a, d.i, d.j), a.lda, tile_ptr<T>(a, d.i, d.k), a.lda,
                        tile_ptr<T>(a, d.j, d.k), a.lda, tile_dim(a, d.i), tile_dim(a, d.j), tile_dim(a, d.k),
-                       false, smem)
+                       false, smem, split_ptr(a, d.i, d.k), split_ptr(a, d.j, d.k))
                  ? CHOL_INFO_TIMEOUT
                  : 0;
   }
@@ -645,10 +671,23 @@ static int launch_workers(const Resolved &r, const DeviceInfo &di) {
 
 using namespace chol;
 
+extern "C" size_t chol_factor_lowp_workspace_size(int precision, int n, const chol_opts *opts) {
+  const int prec = precision == CHOL_F32 ? PREC_F32
+                   : precision == CHOL_BF16 ? PREC_BF16
+                   : precision == CHOL_BF16X3 ? PREC_BF16X3
+                                              : -1;
+  Resolved r;
+  if (prec < 0 || n < 0 || !resolve(n, opts, r, prec)) return 0;
+  const DeviceInfo di = current_device_info();
+  const int W = launch_workers(r, di);
+  return make_layout(n, r, W).total;
+}
+
 extern "C" size_t chol_factor_workspace_size(int n, const chol_opts *opts) {
-  // the same workspace serves both precisions of the factor
+  // the same workspace serves the FP64 and FP32 factors (the tensor-core forms also keep the
+  // panel tiles' BF16 terms: chol_factor_lowp_workspace_size)
   size_t best = 0;
-  for (int prec = PREC_F64; prec <= PREC_BF16X3; ++prec) {
+  for (int prec = PREC_F64; prec <= PREC_F32; ++prec) {
     Resolved r;
     if (n < 0 || !resolve(n, opts, r, prec)) return 0;
     const DeviceInfo di = current_device_info();
@@ -715,6 +754,8 @@ chol_status factor_impl(int prec, int n, void *dA, int lda, const chol_opts *opt
   a.qcost = reinterpret_cast<unsigned long long *>(ws + L.qcost);
   a.run_end = reinterpret_cast<unsigned long long *>(ws + L.run_end);
   a.trace_buf = r.trace ? reinterpret_cast<long long *>(ws + L.trace) : nullptr;
+  a.split = L.split_tile ? ws + L.split : nullptr;
+  a.split_tile = (int64_t)L.split_tile;
 
   CHOL_CUDA_TRY(cudaMemsetAsync(ws + L.ctrl, 0, sizeof(Ctrl), s));
   CHOL_CUDA_TRY(cudaMemsetAsync(ws + L.zero_begin, 0, L.zero_end - L.zero_begin, s));

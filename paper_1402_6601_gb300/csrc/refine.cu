@@ -295,7 +295,7 @@ struct RefineLayout {
   int nseg;  // J segments of the residual
 };
 
-static RefineLayout refine_layout(int n, int nrhs, const chol_opts *opts) {
+static RefineLayout refine_layout(int n, int nrhs, const chol_opts *opts, int low_precision) {
   RefineLayout L;
   L.lda32 = std::max<int64_t>(32, ((int64_t)n + 31) / 32 * 32);
   L.ld32 = L.lda32;
@@ -303,7 +303,7 @@ static RefineLayout refine_layout(int n, int nrhs, const chol_opts *opts) {
   L.ctrl = o; o += 256;
   L.finfo = o; o += 256;
   L.a32 = o; o += align_up((size_t)L.lda32 * n * 4, 256);
-  L.fbytes = chol_factor_workspace_size(n, opts);
+  L.fbytes = chol_factor_lowp_workspace_size(low_precision, n, opts);
   L.fwork = o; o += align_up(L.fbytes, 256);
   L.r = o; o += align_up((size_t)n * std::max(nrhs, 1) * 8, 256);
   L.scale = o; o += align_up((size_t)std::max(n, 1) * 8, 256);
@@ -329,10 +329,21 @@ static RefineLayout refine_layout(int n, int nrhs, const chol_opts *opts) {
 
 using namespace chol;
 
-extern "C" size_t chol_solve_refine_workspace_size(int n, int nrhs, const chol_opts *opts) {
+extern "C" size_t chol_solve_refine_prec_workspace_size(int low_precision, int n, int nrhs, const chol_opts *opts) {
   if (n < 0 || nrhs < 0) return 0;
-  if (n > 0 && chol_factor_workspace_size(n, opts) == 0) return 0;
-  return refine_layout(n, nrhs, opts).total;
+  if (n > 0 && chol_factor_lowp_workspace_size(low_precision, n, opts) == 0) return 0;
+  return refine_layout(n, nrhs, opts, low_precision).total;
+}
+
+extern "C" size_t chol_solve_refine_workspace_size(int n, int nrhs, const chol_opts *opts) {
+  // enough for every low-precision form
+  size_t best = 0;
+  for (int p : {CHOL_F32, CHOL_BF16, CHOL_BF16X3}) {
+    const size_t b = chol_solve_refine_prec_workspace_size(p, n, nrhs, opts);
+    if (b == 0) return 0;
+    best = std::max(best, b);
+  }
+  return best;
 }
 
 extern "C" chol_status chol_solve_refine(int n, int nrhs, const double *dA, int lda, const double *dB, int ldb,
@@ -354,7 +365,7 @@ extern "C" chol_status chol_solve_refine(int n, int nrhs, const double *dA, int 
     if (dBerr) CHOL_CUDA_TRY(cudaMemsetAsync(dBerr, 0, sizeof(double), s));
     return CHOL_OK;
   }
-  const RefineLayout L = refine_layout(n, nrhs, opts);
+  const RefineLayout L = refine_layout(n, nrhs, opts, low_precision);
   if (L.fbytes == 0) return CHOL_ERR_INVALID_ARG;
   if (!dWork || work_bytes < L.total || ((uintptr_t)dWork & 255)) return CHOL_ERR_WORKSPACE;
   const DeviceInfo di = current_device_info();

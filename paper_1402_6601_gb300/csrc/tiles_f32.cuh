@@ -421,11 +421,21 @@ static __device__ __noinline__ int potrf_tile_smem(float *G, int64_t ld, int nk,
 // memory, then solves the 32 x 32 diagonal block in registers. The contraction is one long
 // register-resident stream per thread instead of block-wide updates with a 32-deep k, and
 // a column block costs one barrier pair.
+//
+// `emit` receives every finished 32-column block of each row (emit.row(r, j0 / 32, x)) and is
+// told about the rows past mb (emit.zero(r, j0 / 32)), for a consumer that wants the result in
+// another layout as well; the default does nothing.
 constexpr int TR_LD = IB + 4;
 constexpr int TRSM_ROWS_SMEM_BYTES = (PANEL_MAX_N * TR_LD + IB) * 4;
 
+struct NoEmit {
+  __device__ void row(int, int, const float (&)[IB]) const {}
+  __device__ void zero(int, int) const {}
+};
+
+template <class Emit = NoEmit>
 static __device__ __noinline__ void trsm_tile_rows(float *B, int64_t ldb, const float *L, int64_t ldl, int mb,
-                                                   int nk, float *smem) {
+                                                   int nk, float *smem, Emit emit = Emit()) {
   float *Lp = smem;  // Lp[k * TR_LD + c] = L(j0 + c, k), zero above the diagonal, identity padding
   float *Rinv = smem + PANEL_MAX_N * TR_LD;
   const int tid = threadIdx.x;
@@ -476,7 +486,9 @@ static __device__ __noinline__ void trsm_tile_rows(float *B, int64_t ldb, const 
 #pragma unroll
       for (int c = 0; c < IB; ++c)
         if (c < jb) stcg(B + (int64_t)(j0 + c) * ldb + r, acc[c]);
+      emit.row(r, j0 / IB, acc);
     }
+    if (tid >= mb) emit.zero(tid, j0 / IB);
   }
   __syncthreads();
 }

@@ -44,9 +44,11 @@ struct Cfg {
 // per-block state that lives across tasks (static shared memory, not the dynamic buffer the
 // other bodies and the scheduler share)
 struct State {
-  uint64_t mbar[2];
+  uint64_t mbar[2];  // MMA completion of the chunks in stage 0 / 1 (tcgen05.commit)
+  uint64_t full[2];  // bulk copies into stage 0 / 1 complete (transaction bytes)
   uint32_t tmem;
-  uint32_t chunks;  // chunks issued so far by this block (stage = chunk & 1)
+  uint32_t chunks;   // chunks issued so far by this block (stage = chunk & 1)
+  uint32_t fb[2];    // phases of full[0] / full[1] used so far
   int err;
 };
 
@@ -103,11 +105,8 @@ __device__ __forceinline__ bool mbar_try(uint64_t *mbar, uint32_t parity) {
   return ok != 0;
 }
 
-// wait until the commit of chunk q (barrier q & 1, phase (q >> 1) & 1) has arrived; false on
-// expiry of the time limit
-__device__ __forceinline__ bool wait_chunk(State &s, uint32_t q) {
-  uint64_t *mb = &s.mbar[q & 1];
-  const uint32_t par = (q >> 1) & 1u;
+// bounded wait for the phase of parity `par` of an mbarrier; false on expiry of the time limit
+__device__ __forceinline__ bool mbar_wait(uint64_t *mb, uint32_t par) {
   if (mbar_try(mb, par)) return true;
   const uint64_t t0 = globaltimer();
   for (int64_t it = 0; it < (int64_t)1 << 34; ++it) {
@@ -115,6 +114,19 @@ __device__ __forceinline__ bool wait_chunk(State &s, uint32_t q) {
     if (globaltimer() - t0 > WAIT_LIMIT_NS) return false;
   }
   return false;
+}
+
+// wait until the commit of chunk q (barrier q & 1, phase (q >> 1) & 1) has arrived
+__device__ __forceinline__ bool wait_chunk(State &s, uint32_t q) { return mbar_wait(&s.mbar[q & 1], (q >> 1) & 1u); }
+
+// one thread: expect `bytes` on full[st] and copy them from global memory into the stage
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint64_t *mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+               : "memory");
 }
 
 // Allocate the accumulators and set up the barriers; all threads of the block call it.
@@ -128,6 +140,10 @@ __device__ __forceinline__ void begin(State &s) {
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s.mbar[0])) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s.mbar[1])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s.full[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s.full[1])) : "memory");
+    s.fb[0] = 0;
+    s.fb[1] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s.chunks = 0;
     s.err = 0;
@@ -330,6 +346,127 @@ __device__ __noinline__ int update_nt(float *Cm, int64_t ldc, const float *A, in
       __syncthreads();
     }
   }
+  return 0;
+}
+
+// ---------------------------------------------------------------------------------------
+// Pre-split operands. The TRSM that produces a panel tile also writes its NTERM BF16 terms,
+// already in the stage layout, to a side buffer: chunk c (tile columns 32 c .. 32 c + 31) is
+// NTERM term blocks of OPB bytes, each the K-major core-matrix layout of 256 rows x 32 k. A
+// GEMM/SYRK then moves a chunk of each operand into a stage with one bulk copy (the copy
+// engine, completion counted in bytes on the stage's full barrier), and one thread keeps the
+// tensor core fed while the copy of the next chunk runs.
+
+template <int NTERM>
+struct Split {
+  static constexpr int CHUNK = NTERM * Cfg<NTERM>::OPB;
+  static constexpr size_t tile_bytes(int nb) { return (size_t)(nb / Cfg<NTERM>::KC) * CHUNK; }
+};
+
+// Emitter for the row-per-thread TRSM: row r's values of tile columns 32 c .. 32 c + 31.
+template <int NTERM>
+struct SplitEmit {
+  unsigned char *tile;
+  __device__ void row(int r, int c, const float (&v)[32]) const {
+    store_row<NTERM>(tile + (size_t)c * Split<NTERM>::CHUNK, v, r);
+  }
+  __device__ void zero(int r, int c) const {
+    float z[32];
+#pragma unroll
+    for (int e = 0; e < 32; ++e) z[e] = 0.f;
+    store_row<NTERM>(tile + (size_t)c * Split<NTERM>::CHUNK, z, r);
+  }
+};
+
+// C[M x N] -= A B^T with both operands pre-split (sa, sb: their tiles in the side buffer), K a
+// multiple of 32, M, N <= 256. Same accumulators and epilogue as update_nt. Returns 0, or -1
+// when a wait expired.
+template <int NTERM>
+__device__ __noinline__ int update_nt_split(float *Cm, int64_t ldc, const unsigned char *sa, const unsigned char *sb,
+                                            int M, int N, int K, bool lower, unsigned char *smem, State &s) {
+  using C = Cfg<NTERM>;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t sbase = smem_u32(smem);
+  const int nchunk = K / C::KC;
+  const uint32_t c0 = s.chunks;  // same value in every thread (written before a barrier)
+  __syncthreads();               // everyone has read it before thread 0 moves it on
+  if (tid == 0) {
+    // data written by other SMs with ordinary stores, read here by the copy engine
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    int issued = 0;
+    for (int ci = 0; ci < nchunk; ++ci) {
+      const uint32_t q = c0 + ci;
+      const int st = q & 1;
+      if (q >= 2 && !wait_chunk(s, q - 2)) { s.err = 1; break; }  // the MMAs that read this stage
+      const uint32_t bytes = NTERM * C::OPB;
+      const uint32_t sa_s = sbase + st * C::STAGE, sb_s = sa_s + bytes;
+      mbar_expect_tx(&s.full[st], 2 * bytes);
+      bulk_g2s(sa_s, sa + (size_t)ci * bytes, bytes, &s.full[st]);
+      bulk_g2s(sb_s, sb + (size_t)ci * bytes, bytes, &s.full[st]);
+      const bool ok = mbar_wait(&s.full[st], s.fb[st] & 1u);
+      ++s.fb[st];
+      if (!ok) { s.err = 1; break; }
+      fence_after_sync();
+#pragma unroll
+      for (int ks = 0; ks < C::KC / 16; ++ks) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+          for (int pi = 0; pi < C::NPROD; ++pi) {
+            int ta, tb;
+            prod_terms<NTERM>(pi, ta, tb);
+            const uint64_t ad = sdesc(sa_s + ta * C::OPB + h * 16 * C::SBO + ks * 256, C::LBO, C::SBO);
+            const uint64_t bd = sdesc(sb_s + tb * C::OPB + ks * 256, C::LBO, C::SBO);
+            mma_bf16(s.tmem + 256 * h, ad, bd, (ci > 0 || ks > 0 || pi > 0) ? 1u : 0u);
+          }
+        }
+      }
+      mma_commit(&s.mbar[st]);
+      issued = ci + 1;
+    }
+    s.chunks = c0 + issued;
+  }
+  // epilogue: thread = one row of the block, 256 columns in 8 loads of 32; the C values of
+  // the next 32 columns are loaded while the current ones are written
+  const int qd = warp & 3, h = warp >> 2;
+  const int r = 128 * h + 32 * qd + lane;
+  const int ncb = (N + 31) / 32;
+  float cv[32], cn[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const bool w = r < M && j < N && (!lower || r >= j);
+    cv[j] = w ? __ldcg(Cm + (int64_t)j * ldc + r) : 0.f;
+  }
+  __syncthreads();
+  if (s.err) return -1;
+  const bool ok = wait_chunk(s, c0 + nchunk - 1);
+  fence_after_sync();
+  if (!ok) s.err = 1;
+  __syncthreads();
+  if (s.err) return -1;
+#pragma unroll 1
+  for (int cb = 0; cb < ncb; ++cb) {
+    if (cb + 1 < ncb) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int c = 32 * (cb + 1) + j;
+        const bool w = r < M && c < N && (!lower || r >= c);
+        cn[j] = w ? __ldcg(Cm + (int64_t)c * ldc + r) : 0.f;
+      }
+    }
+    uint32_t v[32];
+    tmem_ld32(s.tmem + ((uint32_t)(32 * qd) << 16) + 256 * h + 32 * cb, v);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int c = 32 * cb + j;
+      const bool w = r < M && c < N && (!lower || r >= c);
+      if (w) __stcg(Cm + (int64_t)c * ldc + r, cv[j] - __uint_as_float(v[j]));
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) cv[j] = cn[j];
+  }
+  fence_before_sync();
+  __syncthreads();
   return 0;
 }
 
