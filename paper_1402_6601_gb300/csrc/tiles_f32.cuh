@@ -303,24 +303,40 @@ static __device__ __noinline__ int potrf_tile_smem(float *G, int64_t ld, int nk,
   const bool vec = ((reinterpret_cast<uintptr_t>(G) | (uintptr_t)(ld * 4)) & 15) == 0;
   // load: element (r, c) of block (i, j) is A(32i + r, 32j + c); entries outside the tile form
   // an identity, entries above the diagonal are zero
-  for (int e = tid; e < nlow * IB * 8; e += NT) {
-    const int q = e & 7, c = (e >> 3) & (IB - 1), b = e >> 8;
-    int i = 0;
-    while ((i + 1) * (i + 2) / 2 <= b) ++i;
-    const int j = b - i * (i + 1) / 2;
-    const int gr = IB * i + 4 * q, gc = IB * j + c;
-    float v[4];
-    if (vec && gr + 3 < nk && gc < nk && (i > j || 4 * q >= c)) {
-      const float4 t = __ldcg(reinterpret_cast<const float4 *>(G + (int64_t)gc * ld + gr));
-      v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-    } else {
+  // four vectors in flight per thread: the loads of a group are issued before any is stored
+  for (int e0 = tid; e0 < nlow * IB * 8; e0 += 4 * NT) {
+    float4 t[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int r = gr + u;
-        v[u] = (r < nk && gc < nk) ? (r >= gc ? ldcg(G + (int64_t)gc * ld + r) : 0.f) : (r == gc ? 1.f : 0.f);
+    for (int g = 0; g < 4; ++g) {
+      const int e = e0 + g * NT;
+      t[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (e < nlow * IB * 8) {
+        const int q = e & 7, c = (e >> 3) & (IB - 1), b = e >> 8;
+        int i = 0;
+        while ((i + 1) * (i + 2) / 2 <= b) ++i;
+        const int j = b - i * (i + 1) / 2;
+        const int gr = IB * i + 4 * q, gc = IB * j + c;
+        if (vec && gr + 3 < nk && gc < nk && (i > j || 4 * q >= c)) {
+          t[g] = __ldcg(reinterpret_cast<const float4 *>(G + (int64_t)gc * ld + gr));
+        } else {
+          float v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int r = gr + u;
+            v[u] = (r < nk && gc < nk) ? (r >= gc ? ldcg(G + (int64_t)gc * ld + r) : 0.f) : (r == gc ? 1.f : 0.f);
+          }
+          t[g] = make_float4(v[0], v[1], v[2], v[3]);
+        }
       }
     }
-    *reinterpret_cast<float4 *>(S + b * SB_FLOATS + c * SB_LD + 4 * q) = make_float4(v[0], v[1], v[2], v[3]);
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      const int e = e0 + g * NT;
+      if (e < nlow * IB * 8) {
+        const int q = e & 7, c = (e >> 3) & (IB - 1), b = e >> 8;
+        *reinterpret_cast<float4 *>(S + b * SB_FLOATS + c * SB_LD + 4 * q) = t[g];
+      }
+    }
   }
   if (tid == 0) s_fail = 0;
   __syncthreads();
