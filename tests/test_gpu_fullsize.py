@@ -1,0 +1,143 @@
+"""Parity at the benchmark's full sizes, with the inputs and launch configurations bench.py
+times, on outputs the oracle can compute piece by piece and on properties that hold at any
+size.
+
+FP64 factor + solve, n = 32768, 64 right-hand sides, tile 256 (HEFT) and 512 (DADA):
+  - the leading k x k block of L is the Cholesky factor of the leading k x k block of A, so
+    the oracle factors A[:k, :k] (k = 1024) and the GPU's block must agree within relative
+    Frobenius 1e-12;
+  - any row i of L restricted to those columns solves L[:k, :k] y = A[i, :k]^T, so sampled
+    rows come from the oracle's forward substitution against its own leading factor
+    (relative 1e-12);
+  - info = 0 and a positive diagonal over the whole factor;
+  - the normwise (Rigal-Gaches, infinity norm) backward error of sampled right-hand sides,
+    computed on the host in FP64 from A, x and b, is <= 1e-14.
+Mixed precision, n = 16384, kappa = 1e6, 16 right-hand sides: each form that reaches the
+target (FP32, three-term BF16) must report and have backward error <= 1e-14.
+Batched, 10,000 matrices of orders uniform in [16, 512] (FP64 and FP32): sampled members
+against the oracle's factor and their backward errors.
+Adjoint, 64 matrices of order 1024: sampled gradients against the oracle's gradient.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from oracle import adjoint as oadj
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def chol():
+    import paper_1402_6601_gb300 as c
+    return c
+
+
+def _berr_cols(A_dev, X, B, cols, chunk=2048):
+    """Rigal-Gaches backward error of the columns `cols`, on the host in FP64, reading A from
+    the device in row blocks (no full-size temporaries)."""
+    n = A_dev.shape[0]
+    Xc = X[:, cols].cpu().numpy().astype(np.float64)
+    Bc = B[:, cols].cpu().numpy().astype(np.float64)
+    R = Bc.copy()
+    normA = 0.0
+    for r0 in range(0, n, chunk):
+        blk = A_dev[r0:r0 + chunk, :].cpu().numpy()  # rows r0.. of the symmetric A
+        R[r0:r0 + chunk] -= blk @ Xc
+        normA = max(normA, float(np.abs(blk).sum(axis=1).max()))
+    num = np.abs(R).max(axis=0)
+    den = normA * np.abs(Xc).max(axis=0) + np.abs(Bc).max(axis=0)
+    return float((num / den).max())
+
+
+@pytest.mark.parametrize("nb,policy,alpha", [(256, "heft", 0.5), (512, "dada", 0.5)])
+def test_factor_solve_n32768(chol, nb, policy, alpha):
+    n, nrhs, k, seed = 32768, 64, 1024, 1  # bench.py's main leg: A seed 1, B seed 1001
+    A = chol.colmajor(synth.gram_spd(n, seed=seed, device="cuda"))
+    B = chol.colmajor(synth.rhs(n, nrhs, seed=seed + 1000, device="cuda"))
+    F = A.clone()
+    info, _ = chol.factor(F, chol.opts(nb=nb, policy=policy, alpha=alpha))
+    X = B.clone()
+    chol.solve(F, X)
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    assert bool((torch.diagonal(F) > 0).all().item())
+    # leading block
+    L_lead = oracle.factor(A[:k, :k].cpu().numpy())
+    assert oracle.rel_frobenius(np.tril(F[:k, :k].cpu().numpy()), L_lead) <= 1e-12
+    # sampled rows below it
+    rows = np.sort(np.random.default_rng(7).choice(np.arange(k, n), size=16, replace=False))
+    idx = torch.as_tensor(rows, device="cuda")
+    a_rows = A[idx, :k].cpu().numpy()                        # 16 x k
+    ref = oracle.forward_solve(L_lead, np.asfortranarray(a_rows.T)).T   # L_lead y = a^T
+    got = F[idx, :k].cpu().numpy()
+    assert oracle.rel_frobenius(got, ref) <= 1e-12
+    # backward error of sampled right-hand sides
+    assert _berr_cols(A, X, B, [0, 17, 40, 63]) <= 1e-14
+
+
+@pytest.mark.parametrize("precision", ["f32", "bf16x3"])
+def test_mixed_precision_n16384(chol, precision):
+    n, nrhs, seed = 16384, 16, 1  # bench.py's mixed leg
+    A = chol.colmajor(synth.householder_spd(n, seed=seed, cond=1e6, device="cuda"))
+    B = chol.colmajor(synth.rhs(n, nrhs, seed=seed + 7, device="cuda"))
+    X, info, iters, berr = chol.solve_refine(A, B, tol=1e-14, max_iter=30, o=chol.opts(nb=256),
+                                             precision=precision)
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    assert float(berr.item()) <= 1e-14
+    assert 2 <= int(iters.item()) <= 8
+    assert _berr_cols(A, X, B, list(range(nrhs))) <= 1e-14
+
+
+@pytest.mark.parametrize("dtype,tol_l,tol_b", [(torch.float64, 1e-12, 1e-14), (torch.float32, 2e-5, 1e-6)])
+def test_batched_10000(chol, dtype, tol_l, tol_b):
+    seed = 1  # bench.py's batched leg
+    orders = [int(n) for n in synth.batch_orders(10000, 16, 512, seed=seed)]
+    roffs, off = [], 0
+    for n in orders:
+        roffs.append(off)
+        off += n
+    flat, offs = synth.gram_spd_batch(orders, seed=seed + 3, device="cuda", dtype=dtype)
+    g = torch.Generator(device="cuda").manual_seed(seed + 4)
+    rhs = torch.randn(off, generator=g, device="cuda", dtype=torch.float64).to(dtype)
+    bt = chol.Batch(flat.clone(), offs, orders, rhs.clone(), roffs)
+    src = chol.Batch(flat, offs, orders, rhs, roffs)
+    chol.posv_batched(bt)
+    torch.cuda.synchronize()
+    assert int(bt.info.abs().max().item()) == 0
+    rng = np.random.default_rng(3)
+    sample = list(rng.choice(len(orders), size=24, replace=False)) + [int(np.argmax(orders))]
+    for m in sample:
+        A0 = src.matrix(m).cpu().numpy().astype(np.float64)
+        L = np.tril(bt.matrix(m).cpu().numpy().astype(np.float64))
+        assert oracle.rel_frobenius(L, oracle.factor(A0)) <= tol_l, m
+        x = bt.rhs(m).cpu().numpy().astype(np.float64)
+        b = src.rhs(m).cpu().numpy().astype(np.float64)
+        assert oracle.backward_error(A0, x, b) <= tol_b, m
+
+
+def test_adjoint_64_matrices_n1024(chol):
+    n, m, seed = 1024, 64, 1  # bench.py's adjoint leg
+    bw = synth.rhs(n, 2 * m, seed=seed + 11, device="cuda")
+    o = chol.opts(nb=128, num_workers=32)
+    for i in (0, 31, m - 1):
+        A = chol.colmajor(synth.gram_spd(n, seed=seed + 100 + i, device="cuda"))
+        b = chol.colmajor(bw[:, i:i + 1])
+        w = chol.colmajor(bw[:, m + i:m + i + 1])
+        F = A.clone()
+        chol.factor(F, o, check=True)
+        X = b.clone()
+        chol.solve(F, X)
+        _, Lbar = chol.solve_backward(F, X, w)
+        Abar = chol.cholesky_backward(F, Lbar)
+        torch.cuda.synchronize()
+        # oracle: the same chain of adjoints on the oracle's factor
+        An = A.cpu().numpy()
+        Lo = oracle.factor(An)
+        xo = oracle.solve(Lo, b.cpu().numpy())
+        _, Lbar_o = oadj.solve_backward(Lo, xo, w.cpu().numpy())
+        Abar_o = oadj.cholesky_backward(Lo, Lbar_o)
+        assert oracle.rel_frobenius(Abar.cpu().numpy(), Abar_o) <= 1e-10, i
