@@ -428,6 +428,8 @@ struct TilesF32 {
 template <int NTERM>
 struct TilesTC : TilesF32 {
   static constexpr int SMEM = tc::Cfg<NTERM>::SMEM > TilesF32::SMEM ? tc::Cfg<NTERM>::SMEM : TilesF32::SMEM;
+  static constexpr int EMIT_OFF = (f32::TRSM_ROWS_SMEM_BYTES + 127) / 128 * 128;
+  static_assert(EMIT_OFF + 2 * tc::Split<NTERM>::CHUNK <= SMEM, "TRSM split buffers must fit");
   // one worker per SM: a second one would wait in tcgen05.alloc for columns the first holds
   static_assert(2 * SMEM > 228 * 1024, "tensor-core workers must not share an SM");
   __device__ static tc::State &state() {
@@ -438,8 +440,10 @@ struct TilesTC : TilesF32 {
   // them; without one the updates split their FP32 operands themselves
   __device__ static void trsm(T *B, int64_t ldb, const T *L, int64_t ldl, int mb, int nk, T *s,
                               unsigned char *split) {
+    // the chunk buffers sit past the TRSM's own shared memory
     if (split && nk <= f32::PANEL_MAX_N)
-      f32::trsm_tile_rows(B, ldb, L, ldl, mb, nk, s, tc::SplitEmit<NTERM>{split});
+      f32::trsm_tile_rows(B, ldb, L, ldl, mb, nk, s,
+                          tc::SplitEmit<NTERM>{split, reinterpret_cast<unsigned char *>(s) + EMIT_OFF});
     else
       TilesF32::trsm(B, ldb, L, ldl, mb, nk, s, nullptr);
   }

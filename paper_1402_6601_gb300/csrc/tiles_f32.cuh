@@ -440,13 +440,16 @@ static __device__ __noinline__ int potrf_tile_smem(float *G, int64_t ld, int nk,
 //
 // `emit` receives every finished 32-column block of each row (emit.row(r, j0 / 32, x)) and is
 // told about the rows past mb (emit.zero(r, j0 / 32)), for a consumer that wants the result in
-// another layout as well; the default does nothing.
+// another layout as well; emit.flush(j0 / 32) follows each block (all threads) and
+// emit.finish() the last one. The default does nothing.
 constexpr int TR_LD = IB + 4;
 constexpr int TRSM_ROWS_SMEM_BYTES = (PANEL_MAX_N * TR_LD + IB) * 4;
 
 struct NoEmit {
   __device__ void row(int, int, const float (&)[IB]) const {}
   __device__ void zero(int, int) const {}
+  __device__ void flush(int) const {}
+  __device__ void finish() const {}
 };
 
 template <class Emit = NoEmit>
@@ -505,7 +508,9 @@ static __device__ __noinline__ void trsm_tile_rows(float *B, int64_t ldb, const 
       emit.row(r, j0 / IB, acc);
     }
     if (tid >= mb) emit.zero(tid, j0 / IB);
+    emit.flush(j0 / IB);
   }
+  emit.finish();
   __syncthreads();
 }
 

@@ -363,18 +363,45 @@ struct Split {
   static constexpr size_t tile_bytes(int nb) { return (size_t)(nb / Cfg<NTERM>::KC) * CHUNK; }
 };
 
-// Emitter for the row-per-thread TRSM: row r's values of tile columns 32 c .. 32 c + 31.
+// Emitter for the row-per-thread TRSM: row r's values of tile columns 32 c .. 32 c + 31 are
+// split into `buf` (two chunk buffers in shared memory, alternating), and after each column
+// block one thread writes the chunk to the tile's side buffer with one bulk copy (shared ->
+// global, bulk async-group). Before the task completes, finish() waits for the copies and
+// orders them (async proxy) before the completion's release, so the updates that bulk-copy
+// the tile see it.
 template <int NTERM>
 struct SplitEmit {
-  unsigned char *tile;
+  unsigned char *tile;  // global: the tile's chunks
+  unsigned char *buf;   // shared: 2 x CHUNK bytes, 16-byte aligned
   __device__ void row(int r, int c, const float (&v)[32]) const {
-    store_row<NTERM>(tile + (size_t)c * Split<NTERM>::CHUNK, v, r);
+    store_row<NTERM>(buf + (c & 1) * Split<NTERM>::CHUNK, v, r);
   }
   __device__ void zero(int r, int c) const {
     float z[32];
 #pragma unroll
     for (int e = 0; e < 32; ++e) z[e] = 0.f;
-    store_row<NTERM>(tile + (size_t)c * Split<NTERM>::CHUNK, z, r);
+    store_row<NTERM>(buf + (c & 1) * Split<NTERM>::CHUNK, z, r);
+  }
+  __device__ void flush(int c) const {
+    fence_async_smem();  // the generic-proxy writes of the chunk, before the copy engine reads
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(
+                       tile + (size_t)c * Split<NTERM>::CHUNK),
+                   "r"(smem_u32(buf + (c & 1) * Split<NTERM>::CHUNK)), "r"((uint32_t)Split<NTERM>::CHUNK)
+                   : "memory");
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      // the other buffer is written next: its copy (issued one block ago) must have read it
+      asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+    }
+    __syncthreads();
+  }
+  __device__ void finish() const {
+    if (threadIdx.x == 0) {
+      asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
+    __syncthreads();
   }
 };
 
