@@ -60,7 +60,8 @@ typedef enum {
 
 /* Options of chol_factor. Initialise with chol_opts_default and change what is needed. */
 typedef struct {
-  int nb;                 /* tile order; 0 = 256. 16 <= nb <= 1024 and ceil(n/nb) <= 1024 */
+  int nb;                 /* tile order; 0 (default) = automatic: 128 for n <= 32768, else 256.
+                             16 <= nb <= 1024 and ceil(n/nb) <= 1024 */
   int policy;             /* chol_policy */
   double alpha;           /* DADA affinity parameter, 0 <= alpha <= 1 (Section 3.2) */
   int steal;              /* 1: an idle worker steals from random victims (Section 2.1) */

@@ -124,7 +124,7 @@ for _name in _SIGNATURES:
     __all__.append(_name)
 
 
-def opts(nb=256, policy="heft", alpha=0.5, steal=None, workers_per_sm=2, num_workers=0,
+def opts(nb=0, policy="heft", alpha=0.5, steal=None, workers_per_sm=2, num_workers=0,
          queue_order=None, dada_max_iter=16, dada_eps=0.01, cost_ns=None, timeout_ns=0, trace=False,
          hold_task=-1, use_cp=False, cp_gbs=40.0):
     o = ChOpts()
@@ -523,7 +523,7 @@ class _SolveSPDFn(torch.autograd.Function):
         return Abar, (Bbar.reshape(-1) if ctx.vec else Bbar), None, None
 
 
-def cholesky(A, nb=256):
+def cholesky(A, nb=0):
     """Differentiable lower Cholesky factor of a symmetric positive definite FP64 CUDA matrix."""
     return _CholeskyFn.apply(A, nb)
 
@@ -533,7 +533,7 @@ def cholesky_solve(B, L):
     return _CholSolveFn.apply(B, L)
 
 
-def solve_spd(A, B, nb=256, recompute=False):
+def solve_spd(A, B, nb=0, recompute=False):
     """Differentiable X = A^-1 B for symmetric positive definite A. With recompute=True the
     backward pass refactors A instead of keeping L."""
     return _SolveSPDFn.apply(A, B, nb, recompute)

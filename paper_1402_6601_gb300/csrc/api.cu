@@ -90,7 +90,7 @@ extern "C" const char *chol_version(void) { return "paper_1402_6601_gb300 0.1 (s
 
 extern "C" void chol_opts_default(chol_opts *o) {
   if (!o) return;
-  o->nb = 256;
+  o->nb = 0;  // automatic by n
   o->policy = CHOL_POLICY_HEFT;
   o->alpha = 0.5;
   o->steal = 1;

@@ -35,7 +35,7 @@ def test_opts_struct_layout_matches_header():
     import paper_1402_6601_gb300 as chol
     o = chol.ChOpts()
     chol.lib.chol_opts_default(ctypes.byref(o))
-    assert o.nb == 256 and o.policy == 0 and o.alpha == 0.5 and o.steal == 1
+    assert o.nb == 0 and o.policy == 0 and o.alpha == 0.5 and o.steal == 1
     assert o.dada_max_iter == 16 and abs(o.dada_eps - 0.01) < 1e-15
     assert o.timeout_ns == 10_000_000_000 and o.trace == 0
     assert ctypes.sizeof(chol.ChOpts) == 120 and o.hold_task == -1 and o.use_cp == 0 and o.cp_gbs == 40.0
@@ -173,3 +173,12 @@ def test_cp_with_zero_comm_equals_plain():
         load = [rng.randint(0, 999) for _ in range(W)]
         assert chol.sched_activate("heft", LR, load, use_cp=True) == chol.sched_activate("heft", LR, load)
         assert chol.sched_activate("dada", LR, load, use_cp=True) == chol.sched_activate("dada", LR, load)
+
+
+def test_automatic_tile_size():
+    import paper_1402_6601_gb300 as chol
+    # nb = 0 picks 128 up to n = 32768 and 256 above (the workspace size depends on the tile count)
+    for n, nb in ((8192, 128), (32768, 128), (32769, 256), (40000, 256)):
+        auto = chol.workspace_size(n, chol.opts(nb=0))
+        assert auto == chol.workspace_size(n, chol.opts(nb=nb)), (n, nb)
+        assert auto != chol.workspace_size(n, chol.opts(nb=64 if nb == 128 else 128)), n
