@@ -168,3 +168,23 @@ def test_refine_bf16_well_conditioned(chol):
     assert int(info.item()) == 0
     assert oracle.backward_error(A, X.cpu().numpy(), B) <= 1e-14
     assert int(iters.item()) >= 2  # a BF16 factor alone cannot reach it
+
+
+@pytest.mark.parametrize("precision", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("n,nb", [(700, 80), (1100, 512)])
+def test_tc_register_staged_path(chol, precision, n, nb):
+    # tiles that are not a multiple of 32, or larger than 256, have no pre-split side buffer:
+    # the tensor-core update splits its FP32 operands itself (integer data stays exact)
+    L, A = synth.integer_factor(n, seed=n + 3)
+    Ad = _f32(chol, A)
+    info, _ = chol.factor_f32(Ad, chol.opts(nb=nb), precision=precision)
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    np.testing.assert_array_equal(np.tril(Ad.cpu().numpy().astype(np.float64)), L)
+    if precision == "bf16x3":
+        G = synth.gram_spd(n, seed=n).numpy()
+        Gd = _f32(chol, G)
+        info, _ = chol.factor_f32(Gd, chol.opts(nb=nb), precision=precision)
+        torch.cuda.synchronize()
+        assert int(info.item()) == 0
+        assert oracle.rel_frobenius(np.tril(Gd.cpu().numpy().astype(np.float64)), oracle.factor(G)) <= 2e-5
