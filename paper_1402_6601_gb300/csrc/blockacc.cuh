@@ -1,12 +1,12 @@
 // Thread layout for the products "32-row block x (32 x G right-hand-side block)" that the
-// solve sweeps and the FP64 residual accumulate, inside a 256-thread block: lane = row of
-// the block, warp = slice.
+// FP64 residual of the refinement accumulates, inside a 256-thread block: lane = row of the
+// block, warp = slice.
 //
 // CPT columns per thread (compile time), CSP column slices (a power of two, CSP * CPT >= G)
 // and KS = 8 / CSP k-slices: warp w owns columns (w % CSP) * CPT + q and the k values
 // w / CSP + KS * t. Every fused multiply-add issued therefore works on a live column (or
 // the zero padding of a ragged last group): predicated-off FP64 instructions would still
-// occupy the FP64 pipe. With KS > 1 the k-slices are summed once at the end of an item.
+// occupy the FP64 pipe. With KS > 1 the k-slices are summed once at the end of a block.
 #pragma once
 
 namespace chol {
