@@ -68,16 +68,20 @@ __device__ __forceinline__ T squot(T b, T d, T r) {
   return fma(e, r, x);
 }
 
-// shared memory of solve_kernel<T, NC>, in elements of T
-template <class T, int NC>
+// shared memory of solve_kernel<T, NC, SBK>, in elements of T (SBK rows per item; L and Y
+// blocks are consumed in 32-row chunks)
+template <class T, int NC, int SBK>
 struct SolveSmem {
   static constexpr int V = 16 / (int)sizeof(T) < NC ? 16 / (int)sizeof(T) : NC;  // vector width
   static constexpr int YLD = NC + 16 / (int)sizeof(T);  // row stride: 16-byte rows, no conflicts
-  static constexpr size_t YW = (size_t)SNW * SB * YLD;  // per-warp Y_m rows, later partial sums
-  static constexpr size_t LT = (size_t)SNW * SB * SLD;  // per-warp transposed L block (backward)
-  static constexpr size_t YS = (size_t)SB * YLD;        // the item's block before the diagonal solve
-  static constexpr size_t LD = (size_t)SB * SLD + SB;   // diagonal block and its reciprocals
-  static constexpr size_t DI = (size_t)SB * SLD;        // inverse of the diagonal block (FP32)
+  static constexpr int DLD = SBK + 1;                   // stride of the diagonal block
+  static constexpr int MLD = SBK + 4;                   // stride of its inverse: 16-byte columns
+  static constexpr size_t YW = (size_t)SNW * SBK * YLD; // per-warp Y chunk, later partial sums
+                                                        // (column-major, SBK x NC)
+  static constexpr size_t LT = (size_t)SNW * SB * DLD;  // per-warp transposed L chunk (backward)
+  static constexpr size_t YS = (size_t)SBK * YLD;       // the item's block before the diagonal solve
+  static constexpr size_t LD = (size_t)SBK * DLD + SBK; // diagonal block and its reciprocals
+  static constexpr size_t DI = (size_t)SBK * MLD;       // inverse of the diagonal block (FP32)
   static constexpr size_t NEED = (YW + LT + YS + LD + DI) * sizeof(T);
   static constexpr size_t BYTES = NEED > (size_t)SOLVE_EXCL_SMEM ? NEED : (size_t)SOLVE_EXCL_SMEM;
 };
@@ -99,26 +103,30 @@ __device__ __forceinline__ void vload(const T *p, T (&v)[V]) {
   for (int u = 0; u < V; ++u) v[u] = e[u];
 }
 
-template <class T, int NC>
+// SBK rows per item: 32 (lane = row) or, in FP32, 64 (lane = rows lane and lane + 32), which
+// halves the number of links in the chain of block rows. TRANS: the backward sweep (a.trans).
+template <class T, int NC, int SBK, bool TRANS>
 __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ SolveArgs a) {
-  using S = SolveSmem<T, NC>;
-  constexpr int V = S::V, YLD = S::YLD;
+  using S = SolveSmem<T, NC, SBK>;
+  constexpr int V = S::V, YLD = S::YLD, DLD = S::DLD, MLD = S::MLD;
+  constexpr int RPL = SBK / 32;         // rows per lane
+  constexpr bool INV = sizeof(T) == 4;  // FP32: multiply by the inverted diagonal block
+  static_assert(SBK == 32 || (SBK == 64 && INV), "64-row items are for the FP32 sweeps");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *Yw = reinterpret_cast<T *>(smem_raw);
   T *Lt = Yw + S::YW;
   T *Ys = Lt + S::LT;
   T *Ld = Ys + S::YS;
-  T *Rs = Ld + SB * SLD;
-  T *Di = Rs + SB;
-  constexpr bool INV = sizeof(T) == 4;  // FP32: multiply by the inverted diagonal block
+  T *Rs = Ld + SBK * DLD;
+  T *Mi = Rs + SBK;  // 16-byte aligned: YW, LT, YS and LD are multiples of four elements
   __shared__ long long s_item;
   __shared__ int s_abort;
   const T *L = static_cast<const T *>(a.L);
   T *B = static_cast<T *>(a.B);
   if (a.skip && ld_volatile(a.skip)) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  T *yw = Yw + (size_t)warp * SB * YLD;
-  T *lt = Lt + (size_t)warp * SB * SLD;
+  T *yw = Yw + (size_t)warp * SBK * YLD;
+  T *lt = Lt + (size_t)warp * SB * DLD;
   while (true) {
     if (tid == 0) {
       s_abort = ld_volatile(&a.ctrl->abort) || (a.prev_abort && ld_volatile(a.prev_abort));
@@ -129,83 +137,91 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
     if (item < 0 || item >= a.nitems) break;
     const int g = (int)(item % a.ngroups);
     const int ord = (int)(item / a.ngroups);
-    const int r = a.trans ? a.nrb - 1 - ord : ord;
-    const int r0 = r * SB, rows = min(SB, a.n - r0);
+    const int r = TRANS ? a.nrb - 1 - ord : ord;
+    const int r0 = r * SBK, rows = min(SBK, a.n - r0);
     const int c0 = g * SG, cols = min(SG, a.nrhs - c0);
     // the diagonal block and its reciprocals do not depend on other items: load them now,
     // off the chain of waits. Rows past the end of the matrix get an identity block, so the
-    // substitution runs over a fixed 32 rows with register-resident data.
-    for (int e = tid; e < SB * SB; e += SNT) {
-      const int i = e & 31, j = e >> 5;
-      Ld[i * SLD + j] = (i < rows && j < rows && i >= j) ? __ldcg(L + (int64_t)(r0 + j) * a.lda + r0 + i)
+    // substitution runs over a fixed SBK rows with register-resident data.
+    for (int e = tid; e < SBK * SBK; e += SNT) {
+      const int i = e % SBK, j = e / SBK;
+      Ld[i * DLD + j] = (i < rows && j < rows && i >= j) ? __ldcg(L + (int64_t)(r0 + j) * a.lda + r0 + i)
                                                           : (i == j ? T(1) : T(0));
     }
-    if (tid < SB) Rs[tid] = tid < rows ? T(1) / __ldcg(L + (int64_t)(r0 + tid) * a.lda + r0 + tid) : T(1);
-    if (INV) {
-      // D^-1 by columns: lane j of warp 0 solves D y = e_j (right-looking, register resident;
-      // y stays zero above row j, so no lane needs a predicate), while the other warps start
-      // accumulating. Identity padding past the end of the matrix gives an identity inverse.
+    if (tid < SBK) Rs[tid] = tid < rows ? T(1) / __ldcg(L + (int64_t)(r0 + tid) * a.lda + r0 + tid) : T(1);
+    if constexpr (INV) {
+      // D^-1 by columns: thread j of the first SBK threads solves D y = e_j (right-looking;
+      // y stays zero above row j) while the other warps start accumulating. It is stored as
+      // the matrix the product below reads k-major, Mi[k * MLD + i]: D^-1(i, k) forward,
+      // D^-1(k, i) = D^-T(i, k) backward. Identity padding gives an identity inverse.
       __syncthreads();
-      if (warp == 0) {
-        T y[SB];
-#pragma unroll
-        for (int i = 0; i < SB; ++i) y[i] = i == lane ? T(1) : T(0);
-#pragma unroll
-        for (int k = 0; k < SB; ++k) {
-          y[k] = squot(y[k], Ld[k * SLD + k], Rs[k]);
-#pragma unroll
-          for (int i = k + 1; i < SB; ++i) y[i] = fma(-Ld[i * SLD + k], y[k], y[i]);
+      if (tid < SBK) {
+        const int j = tid;
+        T *col = TRANS ? Mi + j : Mi + j * MLD;  // entry i of column j at col[i * cs]
+        const int cs = TRANS ? MLD : 1;
+        for (int i = 0; i < SBK; ++i) col[i * cs] = i == j ? T(1) : T(0);
+        for (int k = j; k < SBK; ++k) {
+          const T yk = squot(col[k * cs], Ld[k * DLD + k], Rs[k]);
+          col[k * cs] = yk;
+#pragma unroll 4
+          for (int i = k + 1; i < SBK; ++i) col[i * cs] = fma(-Ld[i * DLD + k], yk, col[i * cs]);
         }
-#pragma unroll
-        for (int i = 0; i < SB; ++i) Di[i * SLD + lane] = y[i];
       }
     }
     // this thread's entries of B_r for the final sum, loaded now (off the chain)
-    constexpr int BPT = (SB * NC + SNT - 1) / SNT;
+    constexpr int BPT = (SBK * NC + SNT - 1) / SNT;
     T bv[BPT];
 #pragma unroll
     for (int u = 0; u < BPT; ++u) {
-      const int e = tid + u * SNT, i = e & (SB - 1), q = e >> 5;
-      bv[u] = (e < SB * NC && i < rows && q < cols) ? __ldcg(B + (int64_t)(c0 + q) * a.ldb + r0 + i) : T(0);
+      const int e = tid + u * SNT, i = e % SBK, q = e / SBK;
+      bv[u] = (e < SBK * NC && i < rows && q < cols) ? __ldcg(B + (int64_t)(c0 + q) * a.ldb + r0 + i) : T(0);
     }
     // warp-parallel accumulation over the solved blocks
-    T acc[NC];
+    T acc[RPL][NC];
 #pragma unroll
-    for (int q = 0; q < NC; ++q) acc[q] = T(0);
-    const int nsteps = a.trans ? a.nrb - 1 - r : r;
+    for (int rr = 0; rr < RPL; ++rr)
+#pragma unroll
+      for (int q = 0; q < NC; ++q) acc[rr][q] = T(0);
+    const int nsteps = TRANS ? a.nrb - 1 - r : r;
+    // the solved blocks are consumed in 32-row chunks, one chunk per warp step: chunk kc of
+    // block m is step m * RPL + kc, so the chunks of the newest block go to different warps
+    const int nchunks = nsteps * RPL;
     int wab = 0;
-    // readiness of the warp's next 32 blocks: bit j <-> step mbase + SNW j, one flag load per
+    // readiness of the warp's next 32 chunks: bit j <-> step mbase + SNW j, one flag load per
     // lane and a ballot, so blocks solved long ago cost no polling round trip
     unsigned ready = 0u;
     int mbase = warp;
-    for (int step = warp; step < nsteps; step += SNW) {
-      const int m = a.trans ? a.nrb - 1 - step : step;
-      const int m0 = m * SB, mrows = min(SB, a.n - m0);
-      // L block, issued before any wait (it does not depend on other items). Forward: lane =
-      // row of the item, lr[k] = L_rm(lane, k). Backward: lane = row k of block m,
-      // lr[i] = L_mr(lane, i), staged transposed below.
-      T lr[SB];
-      if (!a.trans) {
+    for (int step = warp; step < nchunks; step += SNW) {
+      const int mi = step / RPL, kc = step % RPL;
+      const int m = TRANS ? a.nrb - 1 - mi : mi;
+      const int k0 = m * SBK + SB * kc, krows = min(SB, a.n - k0);  // this 32-row chunk of block m
+      // L chunk, issued before any wait (it does not depend on other items). Forward: lane =
+      // row of the item, lr[rr][k] = L(r0 + lane + 32 rr, k0 + k). Backward: lane = row k0 +
+      // lane, lb[i] = L(k0 + lane, r0 + i), staged transposed below.
+      T lr[TRANS ? 1 : RPL][SB];
+      T lb[TRANS ? SBK : 1];
+      if (!TRANS) {
 #pragma unroll
-        for (int k = 0; k < SB; ++k)
-          lr[k] = (lane < rows && k < mrows) ? __ldcg(L + (int64_t)(m0 + k) * a.lda + r0 + lane) : T(0);
+        for (int rr = 0; rr < RPL; ++rr)
+#pragma unroll
+          for (int k = 0; k < SB; ++k)
+            lr[rr][k] = (lane + SB * rr < rows && k < krows)
+                            ? __ldcg(L + (int64_t)(k0 + k) * a.lda + r0 + lane + SB * rr) : T(0);
       } else {
 #pragma unroll
-        for (int i = 0; i < SB; ++i)
-          lr[i] = (lane < mrows && i < rows) ? __ldcg(L + (int64_t)(r0 + i) * a.lda + m0 + lane) : T(0);
+        for (int i = 0; i < SBK; ++i)
+          lb[i] = (lane < krows && i < rows) ? __ldcg(L + (int64_t)(r0 + i) * a.lda + k0 + lane) : T(0);
       }
-      T yv[NC];
       int jb = (step - mbase) / SNW;
       if (jb >= 32 || !((ready >> jb) & 1u)) {
         const int sl = step + SNW * lane;
         int f = 1;
-        if (sl < nsteps) {
-          const int ml = a.trans ? a.nrb - 1 - sl : sl;
+        if (sl < nchunks) {
+          const int ml = TRANS ? a.nrb - 1 - sl / RPL : sl / RPL;
           f = ld_volatile(&a.flags[(int64_t)ml * a.ngroups + g]) != 0;
         }
         ready = __ballot_sync(0xffffffffu, f);
         mbase = step;
-        jb = 0;
         if (!(ready & 1u)) {
           // wait until block m of this group is solved (one lane, bounded)
           if (lane == 0) {
@@ -232,92 +248,115 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
         __threadfence();
         __syncwarp();
       }
-      // Y block m (lane k stages row k), loaded once the block is known to be solved
+      // Y chunk (lane k stages row k0 + k), loaded once the block is known to be solved
+      T yv[NC];
 #pragma unroll
       for (int q = 0; q < NC; ++q)
-        yv[q] = (lane < mrows && q < cols) ? __ldcg(B + (int64_t)(c0 + q) * a.ldb + m0 + lane) : T(0);
+        yv[q] = (lane < krows && q < cols) ? __ldcg(B + (int64_t)(c0 + q) * a.ldb + k0 + lane) : T(0);
 #pragma unroll
       for (int q = 0; q < NC; ++q) yw[lane * YLD + q] = yv[q];
-      if (a.trans) {
+      if (TRANS) {
 #pragma unroll
-        for (int i = 0; i < SB; ++i) lt[lane * SLD + i] = lr[i];
+        for (int i = 0; i < SBK; ++i) lt[lane * DLD + i] = lb[i];
       }
       __syncwarp();
 #pragma unroll
       for (int k = 0; k < SB; ++k) {
-        const T l = a.trans ? lt[k * SLD + lane] : lr[k];
+        T l[RPL];
+#pragma unroll
+        for (int rr = 0; rr < RPL; ++rr) l[rr] = TRANS ? lt[k * DLD + lane + SB * rr] : lr[TRANS ? 0 : rr][k];
 #pragma unroll
         for (int q = 0; q < NC; q += V) {
           T y[V];
           vload<T, V>(yw + k * YLD + q, y);
 #pragma unroll
-          for (int u = 0; u < V; ++u) acc[q + u] = fma(l, y[u], acc[q + u]);
+          for (int rr = 0; rr < RPL; ++rr)
+#pragma unroll
+            for (int u = 0; u < V; ++u) acc[rr][q + u] = fma(l[rr], y[u], acc[rr][q + u]);
         }
       }
       __syncwarp();
     }
     if (wab && lane == 0) s_abort = 1;
-    // the eight partial sums: into the warps' rows, then B_r minus their sum into Ys
+    // the eight partial sums, column-major per warp (consecutive lanes, consecutive words),
+    // then B_r minus their sum into Ys
 #pragma unroll
-    for (int q = 0; q < NC; ++q) yw[lane * YLD + q] = acc[q];
+    for (int rr = 0; rr < RPL; ++rr)
+#pragma unroll
+      for (int q = 0; q < NC; ++q) yw[q * SBK + lane + SB * rr] = acc[rr][q];
     __syncthreads();
     if (s_abort) break;
 #pragma unroll
     for (int u = 0; u < BPT; ++u) {
-      const int e = tid + u * SNT, i = e & (SB - 1), q = e >> 5;
-      if (e < SB * NC) {
+      const int e = tid + u * SNT, i = e % SBK, q = e / SBK;
+      if (e < SBK * NC) {
         T sum = T(0);
 #pragma unroll
-        for (int w = 0; w < SNW; ++w) sum += Yw[(size_t)w * SB * YLD + i * YLD + q];
+        for (int w = 0; w < SNW; ++w) sum += Yw[(size_t)w * SBK * YLD + q * SBK + i];
         Ys[i * YLD + q] = bv[u] - sum;
       }
     }
     __syncthreads();
     T *Xo = Ys;  // the solved block, row-major with stride YLD
-    if (INV) {
-      // forward x = D^-1 (b - sum), backward x = D^-T (b - sum): independent 32-term
+    if constexpr (INV) {
+      // forward x = D^-1 (b - sum), backward x = D^-T (b - sum): independent SBK-term
       // products (D^-1 is zero above the diagonal)
-      Xo = Yw;     // free once the partial sums are added
+      Xo = Yw;  // free once the partial sums are added
+      // thread: column q, RPT consecutive rows; per k one broadcast of Y(k, q) and RPT/4
+      // vector loads of Mi's column k (same k order as a plain dot product)
+      constexpr int RPT = SBK * NC / SNT >= 4 ? SBK * NC / SNT : 4;
+      static_assert(SBK % RPT == 0 && RPT % 4 == 0, "rows per thread");
+      if (tid < SBK * NC / RPT) {
+        const int q = tid % NC, i0 = (tid / NC) * RPT;
+        T t[RPT];
 #pragma unroll
-      for (int u = 0; u < (SB * NC + SNT - 1) / SNT; ++u) {
-        const int e = tid + u * SNT, i = e & (SB - 1), q = e >> 5;
-        if (e < SB * NC) {
-          T t = T(0);
+        for (int u = 0; u < RPT; ++u) t[u] = T(0);
+#pragma unroll 8
+        for (int k = 0; k < SBK; ++k) {
+          const T y = Ys[k * YLD + q];
 #pragma unroll
-          for (int k = 0; k < SB; ++k) t = fma(a.trans ? Di[k * SLD + i] : Di[i * SLD + k], Ys[k * YLD + q], t);
-          Xo[i * YLD + q] = t;
+          for (int u = 0; u < RPT; u += 4) {
+            T m[4];
+            vload<T, 4>(Mi + k * MLD + i0 + u, m);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) t[u + v] = fma(m[v], y, t[u + v]);
+          }
         }
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) Xo[(i0 + u) * YLD + q] = t[u];
       }
     } else if (tid < cols) {
       // diagonal block: one thread per right-hand side runs the substitution
       const int c = tid;
-      T x[SB];
+      T x[SBK];
 #pragma unroll
-      for (int i = 0; i < SB; ++i) x[i] = Ys[i * YLD + c];
+      for (int i = 0; i < SBK; ++i) x[i] = Ys[i * YLD + c];
       // right-looking: once x_k is known every later row is updated at once, so each x_k
       // is one quotient and one multiply-add after x_{k-1}
-      if (!a.trans) {
+      if (!TRANS) {
 #pragma unroll
-        for (int k = 0; k < SB; ++k) {
-          x[k] = squot(x[k], Ld[k * SLD + k], Rs[k]);
+        for (int k = 0; k < SBK; ++k) {
+          x[k] = squot(x[k], Ld[k * DLD + k], Rs[k]);
 #pragma unroll
-          for (int i = k + 1; i < SB; ++i) x[i] = fma(-Ld[i * SLD + k], x[k], x[i]);
+          for (int i = k + 1; i < SBK; ++i) x[i] = fma(-Ld[i * DLD + k], x[k], x[i]);
         }
       } else {
 #pragma unroll
-        for (int k = SB - 1; k >= 0; --k) {
-          x[k] = squot(x[k], Ld[k * SLD + k], Rs[k]);
+        for (int k = SBK - 1; k >= 0; --k) {
+          x[k] = squot(x[k], Ld[k * DLD + k], Rs[k]);
 #pragma unroll
-          for (int i = 0; i < k; ++i) x[i] = fma(-Ld[k * SLD + i], x[k], x[i]);
+          for (int i = 0; i < k; ++i) x[i] = fma(-Ld[k * DLD + i], x[k], x[i]);
         }
       }
 #pragma unroll
-      for (int i = 0; i < SB; ++i) Ys[i * YLD + c] = x[i];
+      for (int i = 0; i < SBK; ++i) Ys[i * YLD + c] = x[i];
     }
     __syncthreads();
-    // write the solved block column by column (one warp per column: 32 consecutive rows)
+    // write the solved block column by column (one warp per column: consecutive rows)
     for (int c = warp; c < cols; c += SNW)
-      if (lane < rows) __stcg(B + (int64_t)(c0 + c) * a.ldb + r0 + lane, Xo[lane * YLD + c]);
+#pragma unroll
+      for (int rr = 0; rr < RPL; ++rr)
+        if (lane + SB * rr < rows) __stcg(B + (int64_t)(c0 + c) * a.ldb + r0 + lane + SB * rr, Xo[(lane + SB * rr) * YLD + c]);
     __threadfence();
     __syncthreads();
     if (tid == 0) *(volatile int *)&a.flags[(int64_t)r * a.ngroups + g] = 1;
@@ -338,16 +377,23 @@ static size_t solve_ws(int n, int nrhs) { return 512 + 2 * flags_bytes(n, nrhs);
 
 size_t solve_workspace_bytes(int n, int nrhs) { return solve_ws(n, nrhs); }
 
+// rows per item: 64 in FP32 (half the links of the chain), 32 in FP64 (exact substitution)
+template <class T>
+constexpr int item_rows() { return sizeof(T) == 4 ? 64 : 32; }
+
 template <class T, int NC>
 static cudaError_t launch_solve(const SolveArgs &a, int grid, cudaStream_t s) {
   // one block per SM: the dynamic shared memory request (more than half an SM's) makes a
   // second block impossible
-  constexpr size_t bytes = SolveSmem<T, NC>::BYTES;
+  constexpr int SBK = item_rows<T>();
+  constexpr size_t bytes = SolveSmem<T, NC, SBK>::BYTES;
   static std::once_flag once;
   std::call_once(once, [] {
-    cudaFuncSetAttribute(solve_kernel<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaFuncSetAttribute(solve_kernel<T, NC, SBK, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaFuncSetAttribute(solve_kernel<T, NC, SBK, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   });
-  solve_kernel<T, NC><<<grid, SNT, bytes, s>>>(a);
+  if (a.trans) solve_kernel<T, NC, SBK, true><<<grid, SNT, bytes, s>>>(a);
+  else solve_kernel<T, NC, SBK, false><<<grid, SNT, bytes, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -356,7 +402,7 @@ static chol_status launch_sweep(int trans, int slot, int n, int nrhs, const T *d
                                 void *dWork, const int *skip, cudaStream_t s) {
   SolveArgs a;
   a.L = dL; a.lda = lda; a.B = dB; a.ldb = ldb; a.n = n; a.nrhs = nrhs;
-  a.nrb = (n + SB - 1) / SB;
+  a.nrb = (n + item_rows<T>() - 1) / item_rows<T>();  // flags are sized for 32-row blocks: enough
   a.ngroups = (nrhs + SG - 1) / SG;
   a.nitems = (int64_t)a.nrb * a.ngroups;
   a.trans = trans;

@@ -85,6 +85,31 @@ def test_refine_reaches_fp64_backward_error(chol, n, nrhs, nb):
     np.testing.assert_array_equal(Ad.cpu().numpy(), A)
 
 
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (63, 2), (64, 16), (65, 5), (777, 16), (1100, 33), (1024, 64)])
+def test_f32_solve_matches_oracle_substitution(chol, n, nrhs):
+    """The first refinement step from x0 = 0 returns the FP32 forward and back substitution of
+    b (rounded to FP32) with the FP32 factor (no diagonal scaling in this form). The oracle
+    substitutes in FP64 with the same factor and right-hand sides; the difference is the FP32
+    substitution's rounding error (kappa(A) <= 5 here), far below the O(1) error of a wrong
+    block, chunk or transposed inverse. Sizes: one item, ragged last items (64-row items),
+    one to two 32-column groups."""
+    A = synth.gram_spd(n, seed=5).numpy()
+    B = synth.rhs(n, nrhs, seed=6).numpy()
+    Ad = chol.colmajor(torch.from_numpy(A).to("cuda"))
+    Bd = chol.colmajor(torch.from_numpy(B).to("cuda"))
+    o = chol.opts(nb=128)
+    X, info, iters, _ = chol.solve_refine(Ad, Bd, tol=0.0, max_iter=1, o=o, precision="f32")
+    L32 = chol.colmajor(torch.from_numpy(A).to("cuda").float())
+    chol.factor_f32(L32, o, check=True)
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0 and int(iters.item()) == 1
+    L = np.tril(L32.cpu().numpy().astype(np.float64))
+    ref = oracle.solve(L, B.astype(np.float32).astype(np.float64))
+    got = X.cpu().numpy()
+    err = np.abs(got - ref).max(axis=0) / np.abs(ref).max(axis=0)
+    assert err.max() <= 1e-4, err.max()
+
+
 def test_refine_reports_indefinite(chol):
     n = 300
     A = synth.gram_spd(n, seed=1).numpy()
