@@ -375,8 +375,8 @@ def run_mixed(args, chol, dev):
     t64, _ = timed(fp64_step)
     e64 = _backward_error(A, Bw, B)
     low = {"f32": "FP32 (FFMA) tile bodies",
-           "bf16x3": "FP32 storage, SYRK/GEMM on tcgen05 with three BF16 operand terms (FP32-accurate), "
-                     "diagonal scaling",
+           "bf16x3": "FP32 storage, GEMM updates on tcgen05 with three BF16 operand terms (FP32-accurate), "
+                     "SYRK updates in FFMA, diagonal scaling",
            "bf16": "FP32 storage, SYRK/GEMM on tcgen05 with one BF16 operand term, diagonal scaling"}
     variants = {}
     for prec in ("f32", "bf16x3", "bf16"):

@@ -158,7 +158,10 @@ typedef enum {
                       BF16 operands (8-bit significands) and FP32 accumulation; POTRF/TRSM FP32 */
   CHOL_BF16X3 = 3  /* as CHOL_BF16, but each FP32 operand is split into three BF16 terms
                       t0 + t1 + t2 and the six products t_i t_j (i + j <= 2) are accumulated
-                      in FP32: an FP32-accurate tile update on the tensor cores */
+                      in FP32: an FP32-accurate GEMM tile update on the tensor cores. The SYRK
+                      updates of the diagonal tiles run in FFMA: their products mostly share
+                      a sign, and the tensor cores' accumulation errors then add up to a bias
+                      that costs the refinement a step */
 } chol_precision;
 
 /* chol_factor on an FP32 matrix (same task graph, scheduler, options and workspace size). */

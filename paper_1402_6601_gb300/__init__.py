@@ -227,7 +227,8 @@ _PREC = {"f32": F32, "bf16": BF16, "bf16x3": BF16X3, F32: F32, BF16: BF16, BF16X
 def factor_f32(A, o=None, work=None, info=None, stream=None, check=False, precision="f32"):
     """FP32-storage tile Cholesky in place on a column-major float32 CUDA tensor. precision:
     "f32" (FFMA tile bodies), "bf16" (tensor-core SYRK/GEMM with BF16 operands, FP32
-    accumulation) or "bf16x3" (three BF16 operand terms: FP32-accurate tensor-core updates)."""
+    accumulation) or "bf16x3" (three BF16 operand terms: FP32-accurate tensor-core GEMM updates,
+    SYRK updates in FFMA)."""
     o = o or opts()
     prec = _PREC[precision]
     n = A.shape[0]

@@ -423,8 +423,9 @@ struct TilesF32 {
   __device__ static void begin() {}
   __device__ static void end() {}
 };
-// FP32 storage and FP32 POTRF/TRSM; SYRK/GEMM on the tensor cores with NTERM BF16 operand
-// terms. The accumulators (all 512 TMEM columns) are held by the worker for the whole launch.
+// FP32 storage and FP32 POTRF/TRSM; GEMM (and, with one term, SYRK) updates on the tensor
+// cores with NTERM BF16 operand terms. The accumulators (all 512 TMEM columns) are held by the
+// worker for the whole launch.
 template <int NTERM>
 struct TilesTC : TilesF32 {
   static constexpr int SMEM = tc::Cfg<NTERM>::SMEM > TilesF32::SMEM ? tc::Cfg<NTERM>::SMEM : TilesF32::SMEM;
@@ -447,8 +448,19 @@ struct TilesTC : TilesF32 {
     else
       TilesF32::trsm(B, ldb, L, ldl, mb, nk, s, nullptr);
   }
+  // SYRK updates (C -= A A^T on a diagonal tile, rows of A that lie close together in the
+  // matrix) add products that mostly share one sign, and the errors of the tensor cores' FP32
+  // accumulation then pile up in one direction: a bias in the Schur complements that the
+  // refinement removes only slowly. Measured at n = 16384, kappa = 1e6 (four matrices): with
+  // the SYRKs on the tensor cores it contracts ~50x per step and needs five steps to 1e-14;
+  // with them in FFMA (round to nearest) ~80x and four steps for every matrix. The multi-term
+  // form therefore runs its SYRKs on the FFMA body and only the GEMMs, whose products take
+  // both signs, on the tensor cores. (Recomputing only the diagonal entries in FFMA does not
+  // help; keeping each tile's last SYRK on the tensor cores saves 3 ms of factor time but
+  // leaves half of those matrices just above 1e-14 after four steps.)
   __device__ static int update(T *C, int64_t ldc, const T *A, int64_t lda, const T *B, int64_t ldb, int M,
                                int N, int K, bool lower, T *s, const unsigned char *sa, const unsigned char *sb) {
+    if (NTERM > 1 && lower) return TilesF32::update(C, ldc, A, lda, B, ldb, M, N, K, true, s, sa, sb);
     unsigned char *sm = reinterpret_cast<unsigned char *>(s);
     if (sa && sb) return tc::update_nt_split<NTERM>(C, ldc, sa, sb, M, N, K, lower, sm, state());
     return tc::update_nt<NTERM>(C, ldc, A, lda, B, ldb, M, N, K, lower, sm, state());

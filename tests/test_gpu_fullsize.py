@@ -88,7 +88,9 @@ def test_mixed_precision_n16384(chol, precision):
     torch.cuda.synchronize()
     assert int(info.item()) == 0
     assert float(berr.item()) <= 1e-14
-    assert 2 <= int(iters.item()) <= 8
+    # four refinement steps for both forms (the three-term form runs its SYRK updates in
+    # FFMA; with them on the tensor cores it needed five)
+    assert 2 <= int(iters.item()) <= 4
     assert _berr_cols(A, X, B, list(range(nrhs))) <= 1e-14
 
 
