@@ -33,13 +33,17 @@
 
 namespace chol {
 
+constexpr int SM_SLOTS = 1024;  // %smid values tracked by the co-scheduling rule
+
 struct Ctrl {
   int done;
   int abort;
   int info;
   unsigned int fifo_seq;
   int spills;
-  int pad[59];
+  int queued;    // tasks in all queues
+  int free_sms;  // SMs that host a worker and run no task
+  int pad[57];
 };
 
 struct FactorArgs {
@@ -61,6 +65,7 @@ struct FactorArgs {
   int *qcount;
   unsigned long long *qcost;   // int64 two's complement
   unsigned long long *run_end; // ns, 0 = idle
+  int *sm_busy;                // per SM (by %smid, < SM_SLOTS): running tasks, then hosted workers
   long long *trace_buf;
   int use_cp;       // communication prediction in the placement
   int64_t comm_ns;  // predicted cost of one input tile a worker did not write last
@@ -79,7 +84,7 @@ struct Resolved {
 };
 
 struct Layout {
-  size_t ctrl, trace, zero_begin, qhead, qcount, qcost, run_end, slots, zero_end, cnt, owner, bl, split, total;
+  size_t ctrl, trace, zero_begin, qhead, qcount, qcost, run_end, sm_busy, slots, zero_end, cnt, owner, bl, split, total;
   size_t split_tile;
   int C;
   int64_t ntasks;
@@ -112,6 +117,7 @@ static Layout make_layout(int n, const Resolved &r, int W) {
   L.qcount = o; o += align_up((size_t)W * 4, 256);
   L.qcost = o; o += align_up((size_t)W * 8, 256);
   L.run_end = o; o += align_up((size_t)W * 8, 256);
+  L.sm_busy = o; o += align_up((size_t)2 * SM_SLOTS * 4, 256);
   L.slots = o; o += align_up((size_t)W * L.C * 8, 256);
   L.zero_end = o;
   L.cnt = o; o += align_up((size_t)L.ntasks * 4, 256);
@@ -164,6 +170,7 @@ __device__ int push_task(const FactorArgs &a, int w, unsigned long long entry) {
     for (int probe = 0; probe < a.C; ++probe) {
       if (atomicCAS(&s[idx], 0ull, entry) == 0ull) {
         atomicAdd(&a.qcount[q], 1);
+        atomicAdd(&a.ctrl->queued, 1);
         if (hop) atomicAdd(&a.ctrl->spills, 1);
         return q;
       }
@@ -206,7 +213,10 @@ __device__ int64_t try_pop(const FactorArgs &a, int q) {
     if (lane == 0) ok = atomicCAS(&s[bslot], best, 0ull) == best;
     ok = __shfl_sync(0xffffffffu, ok, 0);
     if (ok) {
-      if (lane == 0) atomicSub(&a.qcount[q], 1);
+      if (lane == 0) {
+        atomicSub(&a.qcount[q], 1);
+        atomicSub(&a.ctrl->queued, 1);
+      }
       return entry_tid(best);
     }
   }
@@ -225,7 +235,7 @@ __device__ __forceinline__ void raise_abort(const FactorArgs &a, int info) {
 
 // Get the next task for worker wid (warp 0). Returns -1 when all tasks are done or the run
 // was aborted. `from` receives the queue the task came from.
-__device__ int64_t acquire(const FactorArgs &a, int wid, uint32_t &rng, int &from) {
+__device__ int64_t acquire(const FactorArgs &a, int wid, int smid, uint32_t &rng, int &from) {
   const int lane = threadIdx.x & 31;
   int last_done = -1;
   uint64_t t_last = 0;
@@ -243,9 +253,16 @@ __device__ int64_t acquire(const FactorArgs &a, int wid, uint32_t &rng, int &fro
     done_ = __shfl_sync(0xffffffffu, done_, 0);
     now = __shfl_sync(0xffffffffu, now, 0);
     if (abort_ || done_ >= a.ntasks) return -1;
-    int64_t id = try_pop(a, wid);
+    // while the SM's other worker runs a task, take one only if the queued work exceeds what
+    // the SMs with no running task can start: two tasks on one SM each run at about half
+    // speed, which lengthens the critical path when work is scarce
+    int yield_ = 0;
+    if (lane == 0 && smid >= 0 && ld_volatile(&a.sm_busy[smid]) > 0)
+      yield_ = ld_volatile(&a.ctrl->queued) <= ld_volatile(&a.ctrl->free_sms);
+    yield_ = __shfl_sync(0xffffffffu, yield_, 0);
+    int64_t id = yield_ ? -1 : try_pop(a, wid);
     if (id >= 0) { from = wid; return id; }
-    if (a.steal && a.W > 1) {
+    if (!yield_ && a.steal && a.W > 1) {
       for (int t = 0; t < 4; ++t) {
         rng = xorshift32(rng);
         int v = (int)(rng % (uint32_t)(a.W - 1));
@@ -512,6 +529,14 @@ __global__ void __launch_bounds__(NT, P::MIN_BLOCKS) factor_kernel(const __grid_
   const int wid = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t rng = 0x9E3779B9u ^ ((uint32_t)wid * 0x85EBCA6Bu + 1u);
+  int smid = -1;
+  {
+    unsigned v;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(v));
+    if (a.W > 1 && v < (unsigned)SM_SLOTS) smid = (int)v;
+  }
+  if (smid >= 0 && threadIdx.x == 0 && atomicAdd(&a.sm_busy[SM_SLOTS + smid], 1) == 0)
+    atomicAdd(&a.ctrl->free_sms, 1);
   P::begin();
   if (wid == 0 && threadIdx.x == 0) {
     const uint32_t key = a.queue_order == 1 ? 0xFFFFFFFFu : prio_key(a.bl[0]);
@@ -521,7 +546,9 @@ __global__ void __launch_bounds__(NT, P::MIN_BLOCKS) factor_kernel(const __grid_
   while (true) {
     if (warp == 0) {
       int from = -1;
-      const int64_t id = acquire(a, wid, rng, from);
+      const int64_t id = acquire(a, wid, smid, rng, from);
+      if (id >= 0 && lane == 0 && smid >= 0 && atomicAdd(&a.sm_busy[smid], 1) == 0)
+        atomicSub(&a.ctrl->free_sms, 1);
       if (id >= 0 && lane == 0) {
         const TaskDesc d = task_desc(a.T, id);
         const int64_t c = a.cost[d.kind];
@@ -550,6 +577,7 @@ __global__ void __launch_bounds__(NT, P::MIN_BLOCKS) factor_kernel(const __grid_
       } else {
         complete(a, wid, d, smem_raw, &s_nready);
       }
+      if (lane == 0 && smid >= 0 && atomicSub(&a.sm_busy[smid], 1) == 1) atomicAdd(&a.ctrl->free_sms, 1);
       if (a.trace && lane == 0) {
         long long *tr = a.trace_buf + 4 * id;
         tr[0] = wid;
@@ -773,6 +801,7 @@ chol_status factor_impl(int prec, int n, void *dA, int lda, const chol_opts *opt
   a.qcount = reinterpret_cast<int *>(ws + L.qcount);
   a.qcost = reinterpret_cast<unsigned long long *>(ws + L.qcost);
   a.run_end = reinterpret_cast<unsigned long long *>(ws + L.run_end);
+  a.sm_busy = reinterpret_cast<int *>(ws + L.sm_busy);
   a.trace_buf = r.trace ? reinterpret_cast<long long *>(ws + L.trace) : nullptr;
   a.split = L.split_tile ? ws + L.split : nullptr;
   a.split_tile = (int64_t)L.split_tile;
