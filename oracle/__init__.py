@@ -13,6 +13,8 @@ imports it.
   a task becomes ready when its predecessors have completed).
 * ``sched`` restates Algorithm 1 (HEFT activate) and Algorithm 2 (DADA activate) for one
   activation on identical workers.
+* ``lu`` is the tile LU with incremental pivoting (PLASMA DGETRF, the paper's second
+  workload, Section 4.1) and its solve, kernel by kernel in program order (numpy).
 """
 import ctypes
 import os

@@ -15,6 +15,16 @@ Task kinds and tuples (kind, i, j, k):
   1 TRSM(i, k)    (1, i, k, k)  R A_kk,           RW A_ik
   2 SYRK(i, k)    (2, i, i, k)  R A_ik,           RW A_ii
   3 GEMM(i, j, k) (3, i, j, k)  R A_ik, R A_jk,   RW A_ij     (k < j < i)
+
+The tile LU with incremental pivoting (DGETRF, the paper's second workload) has its own
+program (program_lu). A diagonal tile is two regions there: its unit lower part L, written
+by GETRF and read by GESSM, and its upper part U, which the TSTRF chain of the step updates;
+a task that writes the whole tile writes both. The kernels' pivots and the L11 blocks of
+TSTRF travel with the tile whose multipliers they describe.
+  0 GETRF(k)        (0, k, k, k)  RW A_kk (L and U)
+  1 GESSM(k, j)     (1, k, j, k)  R A_kk.L,             RW A_kj          (j > k)
+  2 TSTRF(i, k)     (2, i, k, k)  RW A_kk.U, RW A_ik                     (i > k)
+  3 SSSSM(i, j, k)  (3, i, j, k)  R A_ik,  RW A_kj, RW A_ij              (i, j > k)
 """
 from functools import lru_cache
 
@@ -35,9 +45,32 @@ def program(T):
     return out
 
 
-def build(T):
-    """Return (tasks, preds, succs): tasks in program order, dict task -> set of tasks."""
-    prog = program(T)
+GETRF, GESSM, TSTRF, SSSSM = 0, 1, 2, 3
+
+
+def _whole(i, j):
+    """The regions of tile (i, j): a diagonal tile has an L and a U part."""
+    return [(i, j, "L"), (i, j, "U")] if i == j else [(i, j)]
+
+
+def program_lu(T):
+    """Tile LU with incremental pivoting in sequential program order, (reads, writes)."""
+    out = []
+    for k in range(T):
+        out.append(((GETRF, k, k, k), [], _whole(k, k)))
+        for j in range(k + 1, T):
+            out.append(((GESSM, k, j, k), [(k, k, "L")], _whole(k, j)))
+        for i in range(k + 1, T):
+            out.append(((TSTRF, i, k, k), [], [(k, k, "U")] + _whole(i, k)))
+            for j in range(k + 1, T):
+                out.append(((SSSSM, i, j, k), _whole(i, k), _whole(k, j) + _whole(i, j)))
+    return out
+
+
+def build(T, prog=None):
+    """Return (tasks, preds, succs): tasks in program order, dict task -> set of tasks.
+    prog: a program as returned by program / program_lu (default: the Cholesky one)."""
+    prog = program(T) if prog is None else prog
     last_writer = {}
     readers = {}
     preds = {}
@@ -64,12 +97,12 @@ def build(T):
     return [t for t, _, _ in prog], preds, succs
 
 
-def bottom_levels(T, cost):
+def bottom_levels(T, cost, prog=None):
     """Longest cost-weighted path from each task to the exit, the task itself included.
 
     cost maps a task kind to its (integer) cost. bl(t) = cost(t) + max over successors.
     """
-    tasks, _, succs = build(T)
+    tasks, _, succs = build(T, prog)
 
     @lru_cache(maxsize=None)
     def bl(t):

@@ -18,6 +18,12 @@ Recipes
   integer_factor(n)   integer lower L, diag in [1, 8], off-diagonal in [-8, 8]; A = L L^T is
                       then exact in FP64 (|a_ij| <= 64 n < 2^53).
   pascal(n)           P_ij = C(i + j, i) (0-based).
+  general_matrix(n)   A with i.i.d. N(0,1) entries in float64 (the LU workload: a dense
+                      general matrix; kappa grows like n).
+  dyadic_lu(n)        unit lower L with off-diagonal entries in {0, +-1/4, +-1/2}, upper U
+                      with integer entries (|u_jj| in [16, 32], off-diagonal in [-8, 8]);
+                      A = L U is exact in FP64, and since every multiplier is below 1 in
+                      magnitude, partial pivoting never interchanges rows.
 """
 import math
 
@@ -92,6 +98,24 @@ def integer_factor(n, seed=0):
 def integer_vector(n, nrhs, seed=0):
     rng = np.random.default_rng(seed + 7919)
     return rng.integers(-4, 5, size=(n, nrhs)).astype(np.float64)
+
+
+def general_matrix(n, seed=0, device="cpu"):
+    """A with i.i.d. N(0,1) entries, float64, column-major (Fortran) layout."""
+    device = torch.device(device)
+    g = _gen(seed, device)
+    return torch.randn(n, n, generator=g, device=device, dtype=torch.float64).T
+
+
+def dyadic_lu(n, seed=0):
+    """(L, U, A) float64 numpy with A = L U exact (see the module docstring)."""
+    rng = np.random.default_rng(seed + 104729)
+    L = np.tril(rng.integers(-2, 3, size=(n, n)) * 0.25, -1)
+    L[np.arange(n), np.arange(n)] = 1.0
+    U = np.triu(rng.integers(-8, 9, size=(n, n)).astype(np.float64), 1)
+    U[np.arange(n), np.arange(n)] = rng.integers(16, 33, size=n) * rng.choice([-1.0, 1.0], size=n)
+    A = L @ U  # two fractional bits, magnitudes far below 2^53: exact in any order
+    return L, U, A
 
 
 def pascal(n):
