@@ -68,6 +68,11 @@ def parse():
     p.add_argument("--adj-batch", type=int, default=64)
     p.add_argument("--adj-steps", type=int, default=2)
     p.add_argument("--adj-streams", type=int, default=8)
+    p.add_argument("--no-lu", action="store_true")
+    p.add_argument("--lu-n", type=int, default=8192)
+    p.add_argument("--lu-nb", type=int, default=0)
+    p.add_argument("--lu-steps", type=int, default=3)
+    p.add_argument("--lu-policy", default="heft")
     return p.parse_args()
 
 
@@ -296,6 +301,9 @@ def main():
     adjoint = None
     if not args.no_adjoint and rank == 0:
         adjoint = run_adjoint(args, chol, dev)
+    lu = None
+    if not args.no_lu and rank == 0:
+        lu = run_lu(args, chol, dev)
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         cpu = cpu_baseline(args)
@@ -309,7 +317,7 @@ def main():
             "config": workload_config(args),
             "factor_ms": round(fac_avg, 2), "solve_backward_error": berr,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "mixed_precision": mixed, "batched": batched,
-            "adjoint": adjoint,
+            "adjoint": adjoint, "lu": lu,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
                        "reasons": clk.get("reasons"), "samples": clk.get("samples"),
@@ -415,6 +423,57 @@ def run_mixed(args, chol, dev):
             "target_backward_error": 1e-14, "fp64_backward_error": e64, "mixed_backward_error": b["backward_error"],
             "mixed_reported_backward_error": b["reported_backward_error"], "iterations": b["iterations"],
             "info": b["info"], "x_rel_diff_vs_fp64": b.get("x_rel_diff_vs_fp64"), "variants": variants}
+
+
+def run_lu(args, chol, dev):
+    """The LU configuration (the paper's DGETRF workload, Section 4.1): a general n x n matrix
+    with i.i.d. N(0,1) entries, tile LU with incremental pivoting on the persistent kernel
+    (inner blocks of 32), --lu-steps factorizations timed with CUDA events after one warm-up,
+    each on a fresh copy of A; GFLOP/s with 2n^3/3 flops. One solve with one right-hand side
+    checks the timed factors (backward error on the device)."""
+    import torch
+    import synth
+    n = args.lu_n
+    o = chol.opts(nb=args.lu_nb, policy=args.lu_policy, alpha=args.alpha)
+    A0 = chol.colmajor(synth.general_matrix(n, seed=args.seed + 11, device=dev))
+    A = torch.empty_like(A0)
+    work = torch.empty(chol.lu_workspace_size(n, o), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    A.copy_(A0)
+    f = chol.lu_factor(A, o, work=work, stream=stream)
+    torch.cuda.synchronize()
+    if int(f.info.item()) != 0:
+        raise RuntimeError("LU info %d" % int(f.info.item()))
+    ms = []
+    for _ in range(args.lu_steps):
+        A.copy_(A0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f = chol.lu_factor(A, o, work=work, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    b = chol.colmajor(synth.rhs(n, 1, seed=args.seed + 12, device=dev))
+    x = b.clone()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    chol.lu_solve(f, x, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    solve_ms = e0.elapsed_time(e1)
+    berr = _backward_error(A0, x, b)
+    t = sum(ms) / len(ms)
+    gf = 2.0 * n ** 3 / 3.0 / (t / 1000.0) / 1e9
+    T = -(-n // (o.nb if o.nb else (128 if n <= 32768 else 256)))
+    return {"workload": "tile LU with incremental pivoting (GETRF/GESSM/TSTRF/SSSSM), n=%d, tile %s, inner "
+                        "block 32, %s ready queues; A with i.i.d. N(0,1) entries" % (
+                            n, o.nb or "auto", args.lu_policy.upper()),
+            "factor_ms": round(t, 2), "gflops": round(gf, 1), "flops": "2n^3/3",
+            "frac_of_fp64_peak": round(gf / FP64_PEAK_GFLOPS, 4), "tiles": T,
+            "tasks": int(chol.lib.chol_lu_dag_task_count(T)),
+            "solve_ms_1rhs": round(solve_ms, 2), "solve_backward_error": berr, "info": int(f.info.item())}
 
 
 def run_batched(args, chol, dev):

@@ -288,6 +288,48 @@ chol_status chol_posv_host(int n, int nrhs, double *hA, int lda, double *hB, int
                            int *hInfo, void *stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Tile LU factorization with incremental pivoting, the paper's second workload (Section 4.1
+ * "Benchmarks": the PLASMA tile algorithm for DGETRF; Section 4.1 "Methodology": double
+ * precision, an inner block IB), run by the same persistent data-flow kernel and policies
+ * as chol_factor. Tasks per step k: GETRF(k) (LU with partial pivoting of the diagonal
+ * tile), GESSM(k, j) (its transformation applied to A_kj), TSTRF(i, k) (LU with partial
+ * pivoting of [U_kk; A_ik]), SSSSM(i, j, k) (that transformation applied to [A_kj; A_ij]).
+ * Every kernel works on inner blocks of 32 columns (the inner block of these kernels); the
+ * transformation of one block is its row interchanges in order, then the unit lower
+ * triangle L11 of the block's pivot rows, then the elimination of the rows below with the
+ * multipliers L21. Multipliers of a block are not interchanged by later blocks.
+ *
+ * dA    n x n general matrix, leading dimension lda >= max(1, n). On exit: its upper
+ *       triangle is U; the strict lower triangle of a diagonal tile holds the multipliers
+ *       of GETRF; tile (i, k), i > k, holds the multipliers of TSTRF(i, k).
+ * dPiv  device ints, chol_lu_aux_size's piv_count of them: for tile column k the pivots of
+ *       GETRF(k) at ((k T + k) nb) and of TSTRF(i, k) at ((k T + i) nb), one per column of
+ *       the tile: the position (relative to the inner block's first row) interchanged with
+ *       that column's diagonal position; for TSTRF positions 0..w-1 are rows of U_kk and
+ *       w + r is row r of A_ik (w = the inner block's width).
+ * dLw   device doubles, lw_count of them: the L11 blocks of TSTRF(i, k) at
+ *       ((k T + i) 32 nb), a 32 x nb column-major array (block b's strict lower triangle in
+ *       columns 32 b ..; zeros elsewhere).
+ * opts  as chol_factor (policies, workers, ...); the tile order nb must be <= 256 (0 =
+ *       automatic, as chol_factor). cost_ns[] are the GETRF, GESSM, TSTRF, SSSSM costs.
+ * dWork at least chol_lu_workspace_size(n, opts) bytes, 256-byte aligned.
+ * dInfo device int: 0, j > 0 (the first zero pivot met was in global column j: U is
+ *       singular; the run stops and the outputs are unspecified) or a negative CHOL_INFO_*.
+ * The caller owns every buffer; nothing is allocated. One initialisation kernel, one
+ * bottom-level kernel and one persistent kernel run on `stream`.
+ */
+size_t chol_lu_workspace_size(int n, const chol_opts *opts);
+chol_status chol_lu_aux_size(int n, const chol_opts *opts, long long *piv_count, long long *lw_count);
+chol_status chol_lu_factor(int n, double *dA, int lda, int *dPiv, double *dLw, const chol_opts *opts,
+                           void *dWork, size_t work_bytes, int *dInfo, void *stream);
+
+/* Solve A X = B with the outputs of chol_lu_factor (same n and opts, so the same tiles):
+ * the recorded transformations applied to B in factorization order, then back substitution
+ * with U. dB n x nrhs (ldb >= max(1, n)) is overwritten by X. One kernel; no workspace. */
+chol_status chol_lu_solve(int n, int nrhs, const double *dF, int lda, const int *dPiv, const double *dLw,
+                          const chol_opts *opts, double *dB, int ldb, void *stream);
+
+/* ---------------------------------------------------------------------------------------
  * Introspection of the task graph and of the activate policies. These run on the HOST,
  * with host pointers, using the same code the persistent kernel runs; they exist so the
  * graph and the placement rules can be checked without a GPU.
@@ -307,6 +349,13 @@ chol_status chol_dag_describe(int T, int *kind, int *ti, int *tj, int *tk, int *
 /* Bottom level of every task: its cost plus the longest cost-weighted path to the exit
  * (the upward rank that orders the original HEFT, Section 3.1). cost_ns[4] per kind. */
 chol_status chol_dag_bottom_levels(int T, const long long *cost_ns, long long *bl);
+
+/* The same for the tile LU graph: count 1 + 2m + m^2 per step (m = T-1-k); kinds 0 GETRF
+ * (k,k,k), 1 GESSM (k,j,k), 2 TSTRF (i,k,k), 3 SSSSM (i,j,k). */
+long long chol_lu_dag_task_count(int T);
+chol_status chol_lu_dag_describe(int T, int *kind, int *ti, int *tj, int *tk, int *indeg,
+                                 long long *succ_ptr, long long *succ);
+chol_status chol_lu_dag_bottom_levels(int T, const long long *cost_ns, long long *bl);
 
 /* One activate operation on identical workers (Algorithm 1 for CHOL_POLICY_HEFT,
  * Algorithm 2 for CHOL_POLICY_DADA). Ready list of m tasks: task ids tid[m], processing

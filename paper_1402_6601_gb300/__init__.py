@@ -21,8 +21,8 @@ __all__ = [
     "posv_host", "workspace_size", "solve_workspace_size", "num_workers", "trace", "factor_f32",
     "solve_refine", "refine_workspace_size", "cholesky_backward", "solve_backward", "lower",
     "cholesky", "cholesky_solve", "solve_spd", "BatchOpts", "Batch", "posv_batched", "factor_batched",
-    "solve_batched", "batched_autotune",
-    "dag_describe", "dag_bottom_levels", "sched_activate", "sched_activate_device",
+    "solve_batched", "batched_autotune", "lu_factor", "lu_solve", "lu_workspace_size", "LUFactors",
+    "dag_describe", "dag_bottom_levels", "lu_dag_describe", "lu_dag_bottom_levels", "sched_activate", "sched_activate_device",
     "CholeskyError",
 ]
 
@@ -93,6 +93,13 @@ _SIGNATURES = {
     "chol_batched_autotune": (_I, [_I, _I, _P, _P, _P, _P, _P, _P, _SZ, _P, _P, _P]),
     "chol_posv_host_stage_size": (_SZ, [_I, _I, _OPTS]),
     "chol_posv_host": (_I, [_I, _I, _P, _I, _P, _I, _OPTS, _P, _SZ, _P, _P]),
+    "chol_lu_workspace_size": (_SZ, [_I, _OPTS]),
+    "chol_lu_aux_size": (_I, [_I, _OPTS, _P, _P]),
+    "chol_lu_factor": (_I, [_I, _P, _I, _P, _P, _OPTS, _P, _SZ, _P, _P]),
+    "chol_lu_solve": (_I, [_I, _I, _P, _I, _P, _P, _OPTS, _P, _I, _P]),
+    "chol_lu_dag_task_count": (_LL, [_I]),
+    "chol_lu_dag_describe": (_I, [_I, _P, _P, _P, _P, _P, _P, _P]),
+    "chol_lu_dag_bottom_levels": (_I, [_I, _P, _P]),
     "chol_dag_task_count": (_LL, [_I]),
     "chol_dag_edge_count": (_LL, [_I]),
     "chol_dag_describe": (_I, [_I, _P, _P, _P, _P, _P, _P, _P]),
@@ -361,6 +368,31 @@ def dag_describe(T):
     _check(lib.chol_dag_describe(T, *[a.ctypes.data for a in arrs], ptr.ctypes.data, succ.ctypes.data),
            "chol_dag_describe")
     return (*arrs, ptr, succ[:ne])
+
+
+def lu_dag_describe(T):
+    """The tile LU graph: (kind, i, j, k, indeg, succ_ptr, succ) as numpy arrays (host code)."""
+    import numpy as np
+    nt = int(lib.chol_lu_dag_task_count(T))
+    if nt < 0:
+        raise ValueError("T out of range")
+    arrs = [np.zeros(nt, np.int32) for _ in range(5)]
+    ptr = np.zeros(nt + 1, np.int64)
+    _check(lib.chol_lu_dag_describe(T, *[a.ctypes.data for a in arrs], ptr.ctypes.data, None),
+           "chol_lu_dag_describe")
+    succ = np.zeros(max(int(ptr[-1]), 1), np.int64)
+    _check(lib.chol_lu_dag_describe(T, None, None, None, None, None, None, succ.ctypes.data),
+           "chol_lu_dag_describe")
+    return (*arrs, ptr, succ[:int(ptr[-1])])
+
+
+def lu_dag_bottom_levels(T, cost_ns):
+    import numpy as np
+    nt = int(lib.chol_lu_dag_task_count(T))
+    c = np.asarray(cost_ns, dtype=np.int64)
+    bl = np.zeros(nt, np.int64)
+    _check(lib.chol_lu_dag_bottom_levels(T, c.ctypes.data, bl.ctypes.data), "chol_lu_dag_bottom_levels")
+    return bl
 
 
 def dag_bottom_levels(T, cost_ns):
@@ -633,3 +665,51 @@ def batched_autotune(batch, scratch, stream=None):
                                      scratch.work.data_ptr(), scratch.work.numel(), ctypes.byref(best),
                                      ctypes.byref(ms), _stream(stream)), "chol_batched_autotune")
     return best, float(ms.value)
+
+
+# ------------------------------------------------------------------------------------------
+# tile LU with incremental pivoting (chol_lu_factor / chol_lu_solve)
+
+class LUFactors:
+    """What chol_lu_factor leaves: the factored matrix F (in place of A), the pivots and the
+    L11 blocks, with the options (tile size) they were made with."""
+
+    def __init__(self, F, piv, lw, o, info):
+        self.F, self.piv, self.lw, self.opts, self.info = F, piv, lw, o, info
+
+
+def lu_workspace_size(n, o=None):
+    o = o or opts()
+    return int(lib.chol_lu_workspace_size(n, ctypes.byref(o)))
+
+
+def lu_factor(A, o=None, work=None, stream=None, check=False):
+    """Tile LU with incremental pivoting of the column-major float64 CUDA matrix A, in place.
+    Returns LUFactors. With check=True the call synchronises and raises on a non-zero info."""
+    o = o or opts()
+    n = A.shape[0]
+    if A.shape[1] != n:
+        raise ValueError("A must be square")
+    lda = _check_matrix(A, "A")
+    npiv, nlw = ctypes.c_longlong(0), ctypes.c_longlong(0)
+    _check(lib.chol_lu_aux_size(n, ctypes.byref(o), ctypes.byref(npiv), ctypes.byref(nlw)), "chol_lu_aux_size")
+    piv = torch.zeros(max(1, npiv.value), dtype=torch.int32, device=A.device)
+    lw = torch.zeros(max(1, nlw.value), dtype=torch.float64, device=A.device)
+    if work is None:
+        work = _workspace(lu_workspace_size(n, o), A.device)
+    info = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _check(lib.chol_lu_factor(n, A.data_ptr(), lda, piv.data_ptr(), lw.data_ptr(), ctypes.byref(o),
+                              work.data_ptr(), work.numel(), info.data_ptr(), _stream(stream)), "chol_lu_factor")
+    if check and int(info.item()) != 0:
+        raise CholeskyError("chol_lu_factor: info = %d" % int(info.item()))
+    return LUFactors(A, piv, lw, o, info)
+
+
+def lu_solve(f, B, stream=None):
+    """X = A^{-1} B in place on the column-major float64 CUDA matrix B, from lu_factor's output."""
+    n = f.F.shape[0]
+    ldb = _check_matrix(B, "B")
+    _check(lib.chol_lu_solve(n, B.shape[1], f.F.data_ptr(), _check_matrix(f.F, "F"), f.piv.data_ptr(),
+                             f.lw.data_ptr(), ctypes.byref(f.opts), B.data_ptr(), ldb, _stream(stream)),
+           "chol_lu_solve")
+    return B

@@ -14,9 +14,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libchol_gb300.so")
-SOURCES = ["csrc/adjoint.cu", "csrc/api.cu", "csrc/batched.cu", "csrc/factor.cu", "csrc/solve.cu", "csrc/refine.cu"]
-HEADERS = ["csrc/blockacc.cuh", "csrc/common.cuh", "csrc/dag.cuh", "csrc/internal.cuh", "csrc/sched.cuh", "csrc/tiles_f32.cuh",
-           "csrc/tiles_f64.cuh", "csrc/tiles_tc.cuh"]
+SOURCES = ["csrc/adjoint.cu", "csrc/api.cu", "csrc/batched.cu", "csrc/factor.cu", "csrc/lu.cu", "csrc/solve.cu",
+           "csrc/refine.cu"]
+HEADERS = ["csrc/blockacc.cuh", "csrc/common.cuh", "csrc/dag.cuh", "csrc/dag_lu.cuh", "csrc/internal.cuh", "csrc/sched.cuh",
+           "csrc/tiles_f32.cuh", "csrc/tiles_f64.cuh", "csrc/tiles_lu.cuh", "csrc/tiles_tc.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -4,6 +4,7 @@
 #include <vector>
 #include "common.cuh"
 #include "dag.cuh"
+#include "dag_lu.cuh"
 #include "sched.cuh"
 
 namespace chol {
@@ -117,24 +118,49 @@ extern "C" long long chol_dag_edge_count(int T) {
   return edge_count(T);
 }
 
-extern "C" chol_status chol_dag_describe(int T, int *kind, int *ti, int *tj, int *tk, int *indeg,
-                                         long long *succ_ptr, long long *succ) {
+template <class G>
+static chol_status describe_graph(int T, int *kind, int *ti, int *tj, int *tk, int *indeg, long long *succ_ptr,
+                                  long long *succ) {
   if (T < 1 || T > 1024) return CHOL_ERR_INVALID_ARG;
-  const int64_t nt = task_count(T);
+  const int64_t nt = G::count(T);
   int64_t e = 0;
   for (int64_t id = 0; id < nt; ++id) {
-    const TaskDesc d = task_desc(T, id);
+    const TaskDesc d = G::desc(T, id);
     if (kind) kind[id] = d.kind;
     if (ti) ti[id] = d.i;
     if (tj) tj[id] = d.j;
     if (tk) tk[id] = d.k;
-    if (indeg) indeg[id] = initial_count(d);
+    if (indeg) indeg[id] = G::initial(d);
     if (succ_ptr) succ_ptr[id] = e;
-    const int ns = num_successors(T, d);
+    const int ns = G::nsucc(T, d);
     for (int s = 0; s < ns; ++s, ++e)
-      if (succ) succ[e] = successor(T, d, s);
+      if (succ) succ[e] = G::succ(T, d, s);
   }
   if (succ_ptr) succ_ptr[nt] = e;
+  return CHOL_OK;
+}
+
+extern "C" chol_status chol_dag_describe(int T, int *kind, int *ti, int *tj, int *tk, int *indeg,
+                                         long long *succ_ptr, long long *succ) {
+  return describe_graph<CholGraph>(T, kind, ti, tj, tk, indeg, succ_ptr, succ);
+}
+
+extern "C" long long chol_lu_dag_task_count(int T) {
+  if (T < 1 || T > 1024) return -1;
+  return LuGraph::count(T);
+}
+
+extern "C" chol_status chol_lu_dag_describe(int T, int *kind, int *ti, int *tj, int *tk, int *indeg,
+                                            long long *succ_ptr, long long *succ) {
+  return describe_graph<LuGraph>(T, kind, ti, tj, tk, indeg, succ_ptr, succ);
+}
+
+extern "C" chol_status chol_lu_dag_bottom_levels(int T, const long long *cost_ns, long long *bl) {
+  if (T < 1 || T > 1024 || !cost_ns || !bl) return CHOL_ERR_INVALID_ARG;
+  const int64_t cost[4] = {cost_ns[0], cost_ns[1], cost_ns[2], cost_ns[3]};
+  int64_t *b = reinterpret_cast<int64_t *>(bl);
+  // every successor has a larger id: reverse id order
+  for (int64_t id = LuGraph::count(T) - 1; id >= 0; --id) b[id] = LuGraph::bottom_level_of(T, LuGraph::desc(T, id), cost, b);
   return CHOL_OK;
 }
 

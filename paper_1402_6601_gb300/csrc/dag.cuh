@@ -152,3 +152,31 @@ CHOL_HD int64_t bottom_level_of(int T, const TaskDesc &d, const int64_t *cost, c
 }
 
 }  // namespace chol
+
+namespace chol {
+
+// The Cholesky graph behind the interface the persistent kernel runs any tile graph through.
+struct CholGraph {
+  static constexpr int KIND0 = K_POTRF;
+  CHOL_HD static int64_t count(int T) { return task_count(T); }
+  CHOL_HD static TaskDesc desc(int T, int64_t id) { return task_desc(T, id); }
+  CHOL_HD static int initial(const TaskDesc &d) { return initial_count(d); }
+  CHOL_HD static int nsucc(int T, const TaskDesc &d) { return num_successors(T, d); }
+  CHOL_HD static int64_t succ(int T, const TaskDesc &d, int s) { return successor(T, d, s); }
+  CHOL_HD static void rw(const TaskDesc &d, int &ti, int &tj) { rw_tile(d, ti, tj); }
+  // at most one ready task per tile of the lower triangle (the writers of a tile form a chain)
+  CHOL_HD static int64_t max_ready(int T) { return (int64_t)T * (T + 1) / 2; }
+  // tiles a task reads or updates, for the communication prediction
+  CHOL_HD static int inputs(const TaskDesc &d, int *ti, int *tj) {
+    switch (d.kind) {
+      case K_POTRF: ti[0] = d.k; tj[0] = d.k; return 1;
+      case K_TRSM: ti[0] = d.k; tj[0] = d.k; ti[1] = d.i; tj[1] = d.k; return 2;
+      case K_SYRK: ti[0] = d.i; tj[0] = d.k; ti[1] = d.i; tj[1] = d.i; return 2;
+      default:
+        ti[0] = d.i; tj[0] = d.k; ti[1] = d.j; tj[1] = d.k; ti[2] = d.i; tj[2] = d.j;
+        return 3;
+    }
+  }
+};
+
+}  // namespace chol

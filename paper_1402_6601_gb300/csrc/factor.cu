@@ -25,11 +25,13 @@
 #include <mutex>
 #include "common.cuh"
 #include "dag.cuh"
+#include "dag_lu.cuh"
 #include "internal.cuh"
 #include "sched.cuh"
 #include "tiles_f32.cuh"
 #include "tiles_tc.cuh"
 #include "tiles_f64.cuh"
+#include "tiles_lu.cuh"
 
 namespace chol {
 
@@ -71,10 +73,12 @@ struct FactorArgs {
   int64_t comm_ns;  // predicted cost of one input tile a worker did not write last
   unsigned char *split;  // tensor-core forms: BF16 terms of the panel tiles (nullable)
   int64_t split_tile;    // bytes per panel tile in `split`
+  int *lu_piv;           // LU: pivots of GETRF(k) / TSTRF(i, k) at ((k T + i) nb), nb per tile
+  double *lu_lw;         // LU: L11 blocks of TSTRF(i, k) at ((k T + i) LU_IB nb)
 };
 
 struct Resolved {
-  int prec, nb, T, policy, queue_order, steal, wps, W, max_iter, trace;
+  int prec, lu, nb, T, policy, queue_order, steal, wps, W, max_iter, trace;
   double alpha, eps;
   int64_t cost[4];
   int64_t timeout_ns;
@@ -102,9 +106,10 @@ static size_t sched_smem_bytes(int T, int W) {
 static Layout make_layout(int n, const Resolved &r, int W) {
   Layout L;
   const int T = r.T;
-  L.ntasks = task_count(T);
+  L.ntasks = r.lu ? LuGraph::count(T) : CholGraph::count(T);
   {
-    const int64_t need = ((int64_t)T * (T + 1) / 2 + W - 1) / W + 64;
+    const int64_t ready = r.lu ? LuGraph::max_ready(T) : CholGraph::max_ready(T);
+    const int64_t need = (ready + W - 1) / W + 64;
     L.C = (int)std::max<int64_t>(128, (need + 31) / 32 * 32);
   }
   size_t o = 0;
@@ -285,6 +290,7 @@ __device__ int64_t acquire(const FactorArgs &a, int wid, int smid, uint32_t &rng
 }
 
 // Activate the successors of a finished task and place the ready ones (warp 0).
+template <class G>
 __device__ void complete(const FactorArgs &a, int wid, const TaskDesc &d, unsigned char *smem_raw,
                          int *s_nready) {
   const int lane = threadIdx.x & 31;
@@ -304,15 +310,15 @@ __device__ void complete(const FactorArgs &a, int wid, const TaskDesc &d, unsign
 
   if (lane == 0) {
     int ti, tj;
-    rw_tile(d, ti, tj);
+    G::rw(d, ti, tj);
     *(volatile int *)&a.owner[ti * T + tj] = wid;
     *(volatile unsigned long long *)&a.run_end[wid] = 0ull;
     *s_nready = 0;
   }
   __syncwarp();
-  const int ns = num_successors(T, d);
+  const int ns = G::nsucc(T, d);
   for (int s = lane; s < ns; s += 32) {
-    const int64_t sid = successor(T, d, s);
+    const int64_t sid = G::succ(T, d, s);
     if (atomicSub(&a.cnt[sid], 1) == 1) {
       const int pos = atomicAdd(s_nready, 1);
       LR[pos].tid = (int)sid;
@@ -323,9 +329,9 @@ __device__ void complete(const FactorArgs &a, int wid, const TaskDesc &d, unsign
   const int m = *(volatile int *)s_nready;
   if (m > 0) {
     for (int i = lane; i < m; i += 32) {
-      const TaskDesc sd = task_desc(T, LR[i].tid);
+      const TaskDesc sd = G::desc(T, LR[i].tid);
       int ti, tj;
-      rw_tile(sd, ti, tj);
+      G::rw(sd, ti, tj);
       LR[i].p = a.cost[sd.kind];
       LR[i].prio = a.queue_order == 0 ? a.bl[LR[i].tid] : 0;
       const int aff = ld_volatile(&a.owner[ti * T + tj]);
@@ -335,23 +341,12 @@ __device__ void complete(const FactorArgs &a, int wid, const TaskDesc &d, unsign
       LR[i].comm = a.comm_ns;
       LR[i].own[0] = LR[i].own[1] = LR[i].own[2] = -1;
       if (a.use_cp) {
-        if (sd.kind == K_POTRF) {
-          LR[i].own[0] = ld_volatile(&a.owner[sd.k * T + sd.k]);
-          LR[i].nin = 1;
-        } else if (sd.kind == K_TRSM) {
-          LR[i].own[0] = ld_volatile(&a.owner[sd.k * T + sd.k]);
-          LR[i].own[1] = ld_volatile(&a.owner[sd.i * T + sd.k]);
-          LR[i].nin = 2;
-        } else if (sd.kind == K_SYRK) {
-          LR[i].own[0] = ld_volatile(&a.owner[sd.i * T + sd.k]);
-          LR[i].own[1] = ld_volatile(&a.owner[sd.i * T + sd.i]);
-          LR[i].nin = 2;
-        } else {
-          LR[i].own[0] = ld_volatile(&a.owner[sd.i * T + sd.k]);
-          LR[i].own[1] = ld_volatile(&a.owner[sd.j * T + sd.k]);
-          LR[i].own[2] = ld_volatile(&a.owner[sd.i * T + sd.j]);
-          LR[i].nin = 3;
-        }
+        int ii[3], jj[3];
+        const int nin = G::inputs(sd, ii, jj);
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          if (q < nin) LR[i].own[q] = ld_volatile(&a.owner[ii[q] * T + jj[q]]);
+        LR[i].nin = nin;
       } else {
         LR[i].nin = 0;
       }
@@ -375,9 +370,9 @@ __device__ void complete(const FactorArgs &a, int wid, const TaskDesc &d, unsign
         if (a.policy == P_STEAL) {
           ps.assign[i] = wid;
         } else {
-          const TaskDesc sd = task_desc(T, LR[i].tid);
+          const TaskDesc sd = G::desc(T, LR[i].tid);
           int ti, tj;
-          rw_tile(sd, ti, tj);
+          G::rw(sd, ti, tj);
           ps.assign[i] = (ti + tj * T) % a.W;
         }
         ps.ord_prio[i] = i;
@@ -405,6 +400,7 @@ __device__ void complete(const FactorArgs &a, int wid, const TaskDesc &d, unsign
 // Tile bodies per precision of the factored matrix.
 struct TilesF64 {
   using T = double;
+  using Graph = CholGraph;
   static constexpr int SMEM = TILE_SMEM_BYTES;
   static constexpr int MIN_BLOCKS = 2;  // two workers per SM share the FP64 pipe
   __device__ static int potrf(T *G, int64_t ld, int nk, T *s) { return potrf_tile(G, ld, nk, s); }
@@ -421,6 +417,7 @@ struct TilesF64 {
 };
 struct TilesF32 {
   using T = float;
+  using Graph = CholGraph;
   static constexpr int SMEM = f32::PANEL_SMEM_BYTES > f32::TILE_SMEM_BYTES ? f32::PANEL_SMEM_BYTES
                                                                             : f32::TILE_SMEM_BYTES;
   static constexpr int MIN_BLOCKS = 1;  // the 8x8 register tiles need more than 128 registers
@@ -491,9 +488,24 @@ __device__ __forceinline__ unsigned char *split_ptr(const FactorArgs &a, int i, 
   return a.split ? a.split + ((int64_t)i * (i - 1) / 2 + k) * a.split_tile : nullptr;
 }
 
+// LU with incremental pivoting, FP64 (tile bodies in tiles_lu.cuh).
+struct LuF64 {
+  using T = double;
+  using Graph = LuGraph;
+  static constexpr int SMEM = LU_SMEM_BYTES;
+  static constexpr int MIN_BLOCKS = 2;
+  __device__ static void begin() {}
+  __device__ static void end() {}
+};
+
 // Run one tile task with the whole block. Returns 0 or a 1-based failing global column.
 template <class P>
-__device__ int run_task(const FactorArgs &a, const TaskDesc &d, typename P::T *smem) {
+struct Runner {
+  __device__ static int run(const FactorArgs &a, const TaskDesc &d, typename P::T *smem);
+};
+
+template <class P>
+__device__ int Runner<P>::run(const FactorArgs &a, const TaskDesc &d, typename P::T *smem) {
   using T = typename P::T;
   switch (d.kind) {
     case K_POTRF: {
@@ -519,8 +531,41 @@ __device__ int run_task(const FactorArgs &a, const TaskDesc &d, typename P::T *s
   }
 }
 
+__device__ __forceinline__ int *lu_piv_ptr(const FactorArgs &a, int i, int k) {
+  return a.lu_piv + ((int64_t)k * a.T + i) * a.nb;
+}
+__device__ __forceinline__ double *lu_lw_ptr(const FactorArgs &a, int i, int k) {
+  return a.lu_lw + ((int64_t)k * a.T + i) * LU_IB * a.nb;
+}
+
+template <>
+__device__ int Runner<LuF64>::run(const FactorArgs &a, const TaskDesc &d, double *smem) {
+  const int64_t ld = a.lda;
+  switch (d.kind) {
+    case K_GETRF: {
+      const int f = lu_getrf_tile(tile_ptr<double>(a, d.k, d.k), ld, tile_dim(a, d.k), lu_piv_ptr(a, d.k, d.k), smem);
+      return f ? d.k * a.nb + f : 0;
+    }
+    case K_GESSM:
+      lu_gessm_tile(tile_ptr<double>(a, d.k, d.j), ld, tile_dim(a, d.k), tile_dim(a, d.j),
+                    tile_ptr<double>(a, d.k, d.k), lu_piv_ptr(a, d.k, d.k), smem);
+      return 0;
+    case K_TSTRF: {
+      const int f = lu_tstrf_tile(tile_ptr<double>(a, d.k, d.k), tile_ptr<double>(a, d.i, d.k), ld, tile_dim(a, d.k),
+                                  tile_dim(a, d.i), lu_piv_ptr(a, d.i, d.k), lu_lw_ptr(a, d.i, d.k), smem);
+      return f ? d.k * a.nb + f : 0;
+    }
+    default:
+      lu_ssssm_tile(tile_ptr<double>(a, d.k, d.j), tile_ptr<double>(a, d.i, d.j), ld, tile_ptr<double>(a, d.i, d.k),
+                    tile_dim(a, d.k), tile_dim(a, d.i), tile_dim(a, d.j), lu_piv_ptr(a, d.i, d.k),
+                    lu_lw_ptr(a, d.i, d.k), smem);
+      return 0;
+  }
+}
+
 template <class P>
 __global__ void __launch_bounds__(NT, P::MIN_BLOCKS) factor_kernel(const __grid_constant__ FactorArgs a) {
+  using G = typename P::Graph;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   typename P::T *smem = reinterpret_cast<typename P::T *>(smem_raw);
   __shared__ long long s_id;
@@ -540,7 +585,7 @@ __global__ void __launch_bounds__(NT, P::MIN_BLOCKS) factor_kernel(const __grid_
   P::begin();
   if (wid == 0 && threadIdx.x == 0) {
     const uint32_t key = a.queue_order == 1 ? 0xFFFFFFFFu : prio_key(a.bl[0]);
-    atomicAdd(&a.qcost[0], (unsigned long long)a.cost[K_POTRF]);
+    atomicAdd(&a.qcost[0], (unsigned long long)a.cost[G::KIND0]);
     if (push_task(a, 0, make_entry(key, 0)) < 0) raise_abort(a, CHOL_INFO_QUEUE_FULL);
   }
   while (true) {
@@ -550,7 +595,7 @@ __global__ void __launch_bounds__(NT, P::MIN_BLOCKS) factor_kernel(const __grid_
       if (id >= 0 && lane == 0 && smid >= 0 && atomicAdd(&a.sm_busy[smid], 1) == 0)
         atomicSub(&a.ctrl->free_sms, 1);
       if (id >= 0 && lane == 0) {
-        const TaskDesc d = task_desc(a.T, id);
+        const TaskDesc d = G::desc(a.T, id);
         const int64_t c = a.cost[d.kind];
         atomicAdd(&a.qcost[from], (unsigned long long)(-c));
         *(volatile unsigned long long *)&a.run_end[wid] = globaltimer_ns() + (uint64_t)c;
@@ -561,10 +606,10 @@ __global__ void __launch_bounds__(NT, P::MIN_BLOCKS) factor_kernel(const __grid_
     const int64_t id = s_id;
     if (id < 0) break;
     __threadfence();
-    const TaskDesc d = task_desc(a.T, id);
+    const TaskDesc d = G::desc(a.T, id);
     unsigned long long t0 = 0;
     if (a.trace && threadIdx.x == 0) t0 = globaltimer_ns();
-    const int fail = run_task<P>(a, d, smem);
+    const int fail = Runner<P>::run(a, d, smem);
     __threadfence();
     __syncthreads();
     if (warp == 0) {
@@ -575,7 +620,7 @@ __global__ void __launch_bounds__(NT, P::MIN_BLOCKS) factor_kernel(const __grid_
       if (fail) {
         if (lane == 0) raise_abort(a, fail);
       } else {
-        complete(a, wid, d, smem_raw, &s_nready);
+        complete<G>(a, wid, d, smem_raw, &s_nready);
       }
       if (lane == 0 && smid >= 0 && atomicSub(&a.sm_busy[smid], 1) == 1) atomicAdd(&a.ctrl->free_sms, 1);
       if (a.trace && lane == 0) {
@@ -590,10 +635,11 @@ __global__ void __launch_bounds__(NT, P::MIN_BLOCKS) factor_kernel(const __grid_
   P::end();
 }
 
+template <class G>
 __global__ void init_kernel(int T, int64_t ntasks, int *cnt, int *owner, int64_t hold_task) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; id < ntasks; id += stride)
-    cnt[id] = initial_count(task_desc(T, id)) + (id == hold_task ? 1 : 0);
+    cnt[id] = G::initial(G::desc(T, id)) + (id == hold_task ? 1 : 0);
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)T * T; t += stride)
     owner[t] = -1;
 }
@@ -618,6 +664,38 @@ __global__ void __launch_bounds__(1024) bottom_level_kernel(int T, int64_t c0, i
   }
 }
 
+// Bottom levels of the LU graph by steps k = T-1 .. 0. Inside a step the SSSSM and TSTRF
+// chains run down the tile rows: for i = T-1 .. k+1 the SSSSM(i, j, k) (successors in row
+// i+1 and in step k+1), then TSTRF(i, k); then the GESSM, then GETRF(k). One block.
+__global__ void __launch_bounds__(1024) lu_bottom_level_kernel(int T, int64_t c0, int64_t c1, int64_t c2,
+                                                               int64_t c3, int64_t *bl) {
+  const int64_t cost[4] = {c0, c1, c2, c3};
+  for (int k = T - 1; k >= 0; --k) {
+    for (int i = T - 1; i > k; --i) {
+      for (int j = k + 1 + threadIdx.x; j < T; j += blockDim.x) {
+        const int64_t id = LuGraph::id(T, K_SSSSM, i, j, k);
+        bl[id] = LuGraph::bottom_level_of(T, LuGraph::desc(T, id), cost, bl);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const int64_t id = LuGraph::id(T, K_TSTRF, i, k, k);
+        bl[id] = LuGraph::bottom_level_of(T, LuGraph::desc(T, id), cost, bl);
+      }
+      __syncthreads();
+    }
+    for (int j = k + 1 + threadIdx.x; j < T; j += blockDim.x) {
+      const int64_t id = LuGraph::id(T, K_GESSM, k, j, k);
+      bl[id] = LuGraph::bottom_level_of(T, LuGraph::desc(T, id), cost, bl);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int64_t id = LuGraph::id(T, K_GETRF, k, k, k);
+      bl[id] = LuGraph::bottom_level_of(T, LuGraph::desc(T, id), cost, bl);
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void copy_info_kernel(const Ctrl *ctrl, int *dInfo) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *dInfo = ctrl->info;
 }
@@ -630,6 +708,7 @@ static std::once_flag g_attr_once;
 static size_t tile_smem_bytes(int prec) {
   switch (prec) {
     case PREC_F64: return TilesF64::SMEM;
+    case PREC_LU_F64: return LuF64::SMEM;
     case PREC_F32: return TilesF32::SMEM;
     case PREC_BF16: return TilesTC<1>::SMEM;
     default: return TilesTC<3>::SMEM;
@@ -641,6 +720,7 @@ static size_t factor_smem_bytes(int prec, int T, int W) { return std::max(tile_s
 static const void *kernel_for(int prec) {
   switch (prec) {
     case PREC_F64: return (const void *)factor_kernel<TilesF64>;
+    case PREC_LU_F64: return (const void *)factor_kernel<LuF64>;
     case PREC_F32: return (const void *)factor_kernel<TilesF32>;
     case PREC_BF16: return (const void *)factor_kernel<TilesTC<1>>;
     default: return (const void *)factor_kernel<TilesTC<3>>;
@@ -652,12 +732,14 @@ static bool resolve(int n, const chol_opts *opts, Resolved &r, int prec = PREC_F
   chol_opts_default(&o);
   if (opts) o = *opts;
   r.prec = prec;
+  r.lu = prec == PREC_LU_F64 ? 1 : 0;
   // automatic tile: FP64 factors of mid-size matrices are bound by the POTRF -> TRSM -> SYRK
   // chain of each step, whose tile bodies run on one SM, so a smaller tile shortens it
   // (fraction of the FP64 peak at 128 vs 256: 0.76 vs 0.41 at n = 8192, 0.94 vs 0.84 at
   // 16384, 0.971 vs 0.964 at 32768); larger orders keep 256 (fewer tasks, T <= 1024)
   r.nb = o.nb > 0 ? o.nb : (n <= 32768 ? 128 : 256);
   if (r.nb < 16 || r.nb > 1024) return false;
+  if (r.lu && r.nb > LU_NB_MAX) return false;
   r.T = n > 0 ? (n + r.nb - 1) / r.nb : 1;
   if (r.T > 1024) return false;
   if (o.policy < 0 || o.policy > 3) return false;
@@ -675,9 +757,15 @@ static bool resolve(int n, const chol_opts *opts, Resolved &r, int prec = PREC_F
   const double nb = (double)r.nb;
   // predicted rate per worker (GFLOP/s = flop per ns): FP64 DFMA ~7.5 per SM, FP32 FFMA tile
   // bodies ~300, tensor-core updates ~700 (one BF16 term) and ~500 (three terms)
-  const double per_sm = prec == PREC_F64 ? 7.5 : prec == PREC_F32 ? 300.0 : prec == PREC_BF16 ? 700.0 : 500.0;
+  const double per_sm = prec == PREC_F64 || prec == PREC_LU_F64 ? 7.5
+                        : prec == PREC_F32                      ? 300.0
+                        : prec == PREC_BF16                     ? 700.0
+                                                                : 500.0;
   const double rate = per_sm / (double)r.wps;
-  const double flops[4] = {nb * nb * nb / 3.0, nb * nb * nb, nb * nb * nb, 2.0 * nb * nb * nb};
+  // per kind: POTRF/TRSM/SYRK/GEMM, or GETRF/GESSM/TSTRF/SSSSM
+  const double chol_flops[4] = {nb * nb * nb / 3.0, nb * nb * nb, nb * nb * nb, 2.0 * nb * nb * nb};
+  const double lu_flops[4] = {2.0 * nb * nb * nb / 3.0, nb * nb * nb, nb * nb * nb, 2.0 * nb * nb * nb};
+  const double *flops = r.lu ? lu_flops : chol_flops;
   for (int k = 0; k < 4; ++k) {
     if (o.cost_ns[k] < 0) return false;
     r.cost[k] = o.cost_ns[k] > 0 ? o.cost_ns[k] : std::max<int64_t>(1, (int64_t)(flops[k] / rate));
@@ -691,7 +779,7 @@ static bool resolve(int n, const chol_opts *opts, Resolved &r, int prec = PREC_F
     const double tile_bytes = nb * nb * (prec == PREC_F64 ? 8.0 : 4.0);
     r.comm_ns = std::max<int64_t>(1, (int64_t)(tile_bytes / gbs));
   }
-  if (r.hold_task >= task_count(r.T)) return false;
+  if (r.hold_task >= (r.lu ? LuGraph::count(r.T) : CholGraph::count(r.T))) return false;
   return true;
 }
 
@@ -703,6 +791,7 @@ static int launch_workers(const Resolved &r, const DeviceInfo &di) {
     cudaFuncSetAttribute(factor_kernel<TilesF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(factor_kernel<TilesTC<1>>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(factor_kernel<TilesTC<3>>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(factor_kernel<LuF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
   });
   const size_t smem = factor_smem_bytes(r.prec, r.T, 2 * di.sms);
   int per_sm = 0;
@@ -764,10 +853,11 @@ extern "C" int chol_num_workers(const chol_opts *opts) {
 namespace chol {
 
 chol_status factor_impl(int prec, int n, void *dA, int lda, const chol_opts *opts, void *dWork,
-                        size_t work_bytes, int *dInfo, void *stream) {
+                        size_t work_bytes, int *dInfo, void *stream, int *lu_piv, double *lu_lw) {
   Resolved r;
   if (n < 0 || !dInfo || !resolve(n, opts, r, prec)) return CHOL_ERR_INVALID_ARG;
   if (lda < std::max(1, n) || (n > 0 && !dA)) return CHOL_ERR_INVALID_ARG;
+  if (r.lu && n > 0 && (!lu_piv || !lu_lw)) return CHOL_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   if (n == 0) {
     CHOL_CUDA_TRY(cudaMemsetAsync(dInfo, 0, sizeof(int), s));
@@ -805,6 +895,8 @@ chol_status factor_impl(int prec, int n, void *dA, int lda, const chol_opts *opt
   a.trace_buf = r.trace ? reinterpret_cast<long long *>(ws + L.trace) : nullptr;
   a.split = L.split_tile ? ws + L.split : nullptr;
   a.split_tile = (int64_t)L.split_tile;
+  a.lu_piv = lu_piv;
+  a.lu_lw = lu_lw;
 
   CHOL_CUDA_TRY(cudaMemsetAsync(ws + L.ctrl, 0, sizeof(Ctrl), s));
   CHOL_CUDA_TRY(cudaMemsetAsync(ws + L.zero_begin, 0, L.zero_end - L.zero_begin, s));
@@ -812,11 +904,13 @@ chol_status factor_impl(int prec, int n, void *dA, int lda, const chol_opts *opt
   {
     const int64_t work = std::max<int64_t>(L.ntasks, (int64_t)r.T * r.T);
     const int blocks = (int)std::min<int64_t>((work + 255) / 256, (int64_t)di.sms * 8);
-    init_kernel<<<blocks, 256, 0, s>>>(r.T, L.ntasks, a.cnt, a.owner, r.hold_task);
+    if (r.lu) init_kernel<LuGraph><<<blocks, 256, 0, s>>>(r.T, L.ntasks, a.cnt, a.owner, r.hold_task);
+    else init_kernel<CholGraph><<<blocks, 256, 0, s>>>(r.T, L.ntasks, a.cnt, a.owner, r.hold_task);
     CHOL_CUDA_TRY(cudaGetLastError());
   }
   if (r.queue_order == 0) {
-    bottom_level_kernel<<<1, 1024, 0, s>>>(r.T, r.cost[0], r.cost[1], r.cost[2], r.cost[3], a.bl);
+    if (r.lu) lu_bottom_level_kernel<<<1, 1024, 0, s>>>(r.T, r.cost[0], r.cost[1], r.cost[2], r.cost[3], a.bl);
+    else bottom_level_kernel<<<1, 1024, 0, s>>>(r.T, r.cost[0], r.cost[1], r.cost[2], r.cost[3], a.bl);
     CHOL_CUDA_TRY(cudaGetLastError());
   }
   const size_t smem = factor_smem_bytes(prec, r.T, W);
@@ -848,4 +942,39 @@ extern "C" chol_status chol_factor_lowp(int precision, int n, float *dA, int lda
 extern "C" chol_status chol_factor_f32(int n, float *dA, int lda, const chol_opts *opts, void *dWork,
                                        size_t work_bytes, int *dInfo, void *stream) {
   return factor_impl(PREC_F32, n, dA, lda, opts, dWork, work_bytes, dInfo, stream);
+}
+
+// ------------------------------------------------------------------------------------
+// LU with incremental pivoting on the same persistent kernel
+
+namespace chol {
+
+int lu_tile_size(int n, const chol_opts *opts) {
+  Resolved r;
+  if (n < 0 || !resolve(n, opts, r, PREC_LU_F64)) return 0;
+  return r.nb;
+}
+
+}  // namespace chol
+
+extern "C" size_t chol_lu_workspace_size(int n, const chol_opts *opts) {
+  Resolved r;
+  if (n < 0 || !resolve(n, opts, r, PREC_LU_F64)) return 0;
+  const DeviceInfo di = current_device_info();
+  const int W = launch_workers(r, di);
+  return make_layout(n, r, W).total;
+}
+
+extern "C" chol_status chol_lu_aux_size(int n, const chol_opts *opts, long long *piv_count, long long *lw_count) {
+  const int nb = lu_tile_size(n, opts);
+  if (nb <= 0) return CHOL_ERR_INVALID_ARG;
+  const long long T = n > 0 ? (n + nb - 1) / nb : 0;
+  if (piv_count) *piv_count = T * T * nb;
+  if (lw_count) *lw_count = T * T * (long long)LU_IB * nb;
+  return CHOL_OK;
+}
+
+extern "C" chol_status chol_lu_factor(int n, double *dA, int lda, int *dPiv, double *dLw, const chol_opts *opts,
+                                      void *dWork, size_t work_bytes, int *dInfo, void *stream) {
+  return factor_impl(PREC_LU_F64, n, dA, lda, opts, dWork, work_bytes, dInfo, stream, dPiv, dLw);
 }

@@ -6,13 +6,18 @@
 
 namespace chol {
 
-// tile bodies of the factor: FP64 DFMA, FP32 FFMA, FP32 with tensor-core BF16 updates (one or
-// three operand terms)
-enum { PREC_F64 = 0, PREC_F32 = 1, PREC_BF16 = 2, PREC_BF16X3 = 3 };
+// tile bodies of the persistent factor kernel: Cholesky with FP64 DFMA, FP32 FFMA, FP32 with
+// tensor-core BF16 updates (one or three operand terms); LU with incremental pivoting in FP64
+enum { PREC_F64 = 0, PREC_F32 = 1, PREC_BF16 = 2, PREC_BF16X3 = 3, PREC_LU_F64 = 4 };
 
-// Tile Cholesky of the n x n matrix at dA (double for PREC_F64, float for PREC_F32).
+// Tile Cholesky of the n x n matrix at dA (double for PREC_F64, float for PREC_F32), or with
+// PREC_LU_F64 the tile LU with incremental pivoting (pivots to lu_piv, L11 blocks to lu_lw).
 chol_status factor_impl(int prec, int n, void *dA, int lda, const chol_opts *opts, void *dWork,
-                        size_t work_bytes, int *dInfo, void *stream);
+                        size_t work_bytes, int *dInfo, void *stream, int *lu_piv = nullptr,
+                        double *lu_lw = nullptr);
+
+// Tile size the LU entry points use for (n, opts) (0 if the options are invalid).
+int lu_tile_size(int n, const chol_opts *opts);
 
 // FP32 forward + back substitution in place; does nothing while *skip != 0 (skip nullable).
 chol_status solve_f32(int n, int nrhs, const float *dL, int lda, float *dB, int ldb, void *dWork,

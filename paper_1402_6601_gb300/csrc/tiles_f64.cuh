@@ -27,17 +27,20 @@ constexpr int TILE_SMEM_BYTES = (STAGE_DOUBLES + IB * DS_LD + IB) * 8;
 __device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
 __device__ __forceinline__ void stcg(double *p, double v) { __stcg(p, v); }
 
-// C[M x N] -= A[M x K] * B[N x K]^T, column-major. With `lower`, only elements with
-// row >= column (relative to C) are written and blocks wholly above the diagonal skipped.
-// Called by all NT threads; ends with the block synchronised.
-static __device__ __noinline__ void update_nt(double *C, int64_t ldc, const double *A, int64_t lda,
-                                       const double *B, int64_t ldb, int M, int N, int K,
-                                       bool lower, double *smem) {
+// C[M x N] -= A[M x K] * op(B), column-major: op(B) = B^T with B N x K (B_KN = false), or
+// op(B) = B with B K x N (B_KN = true, the form of the LU updates). With `lower`, only
+// elements with row >= column (relative to C) are written and blocks wholly above the
+// diagonal skipped. Called by all NT threads; ends with the block synchronised.
+template <bool B_KN>
+static __device__ __noinline__ void update_core(double *C, int64_t ldc, const double *A, int64_t lda,
+                                                const double *B, int64_t ldb, int M, int N, int K,
+                                                bool lower, double *smem) {
   double *As = smem;
   double *Bs = smem + 2 * BK * BM;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int lrow = tid & 63, lk = tid >> 6;  // loader: row lrow, k columns lk + 4q
+  const int kk_b = tid & 31, ncol_b = tid >> 5;  // K x N loader of B: k = kk_b, columns ncol_b + 8q
   for (int bn = 0; bn < N; bn += BN) {
     for (int bm = 0; bm < M; bm += BM) {
       if (lower && bm + BM <= bn) continue;
@@ -49,17 +52,21 @@ static __device__ __noinline__ void update_nt(double *C, int64_t ldc, const doub
       double ra[8], rb[8];
       const bool arow = bm + lrow < M, brow = bn + lrow < N;
       const double *Ap = A + bm + lrow;
-      const double *Bp = B + bn + lrow;
+      const double *Bp = B_KN ? B + (int64_t)(bn + ncol_b) * ldb + kk_b : B + bn + lrow;
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int kk = lk + 4 * q;
         ra[q] = (arow && kk < K) ? ldcg(Ap + (int64_t)kk * lda) : 0.0;
-        rb[q] = (brow && kk < K) ? ldcg(Bp + (int64_t)kk * ldb) : 0.0;
+        if (B_KN)
+          rb[q] = (bn + ncol_b + 8 * q < N && kk_b < K) ? ldcg(Bp + (int64_t)(8 * q) * ldb) : 0.0;
+        else
+          rb[q] = (brow && kk < K) ? ldcg(Bp + (int64_t)kk * ldb) : 0.0;
       }
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         As[(lk + 4 * q) * BM + lrow] = ra[q];
-        Bs[(lk + 4 * q) * BN + lrow] = rb[q];
+        if (B_KN) Bs[kk_b * BN + ncol_b + 8 * q] = rb[q];
+        else Bs[(lk + 4 * q) * BN + lrow] = rb[q];
       }
       __syncthreads();
       int buf = 0;
@@ -70,7 +77,11 @@ static __device__ __noinline__ void update_nt(double *C, int64_t ldc, const doub
           for (int q = 0; q < 8; ++q) {
             const int kk = k0 + BK + lk + 4 * q;
             ra[q] = (arow && kk < K) ? ldcg(Ap + (int64_t)kk * lda) : 0.0;
-            rb[q] = (brow && kk < K) ? ldcg(Bp + (int64_t)kk * ldb) : 0.0;
+            if (B_KN)
+              rb[q] = (bn + ncol_b + 8 * q < N && k0 + BK + kk_b < K)
+                          ? ldcg(Bp + (int64_t)(8 * q) * ldb + k0 + BK) : 0.0;
+            else
+              rb[q] = (brow && kk < K) ? ldcg(Bp + (int64_t)kk * ldb) : 0.0;
           }
         }
         const double *as = As + buf * BK * BM;
@@ -93,7 +104,8 @@ static __device__ __noinline__ void update_nt(double *C, int64_t ldc, const doub
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             an[(lk + 4 * q) * BM + lrow] = ra[q];
-            bnx[(lk + 4 * q) * BN + lrow] = rb[q];
+            if (B_KN) bnx[kk_b * BN + ncol_b + 8 * q] = rb[q];
+            else bnx[(lk + 4 * q) * BN + lrow] = rb[q];
           }
         }
         __syncthreads();
@@ -123,6 +135,13 @@ static __device__ __noinline__ void update_nt(double *C, int64_t ldc, const doub
     }
   }
   __syncthreads();
+}
+
+// C[M x N] -= A[M x K] * B[N x K]^T (the Cholesky updates)
+static __device__ __forceinline__ void update_nt(double *C, int64_t ldc, const double *A, int64_t lda,
+                                                 const double *B, int64_t ldb, int M, int N, int K,
+                                                 bool lower, double *smem) {
+  update_core<false>(C, ldc, A, lda, B, ldb, M, N, K, lower, smem);
 }
 
 // Quotient b / d from the correctly rounded reciprocal r = RN(1/d) with one correction step

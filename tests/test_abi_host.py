@@ -75,6 +75,33 @@ def test_bottom_levels_match_oracle(T):
         assert bl[i] == ref[(int(kind[i]), int(ti[i]), int(tj[i]), int(tk[i]))]
 
 
+@pytest.mark.parametrize("T", [1, 2, 3, 4, 7, 10])
+def test_lu_dag_matches_dataflow_oracle(T):
+    # the tile LU graph (GETRF/GESSM/TSTRF/SSSSM) the persistent kernel runs, against the
+    # graph derived from the kernels' access modes
+    import paper_1402_6601_gb300 as chol
+    kind, ti, tj, tk, indeg, ptr, succ = chol.lu_dag_describe(T)
+    tasks, preds, succs = odag.build(T, odag.program_lu(T))
+    lib_tasks = [(int(kind[i]), int(ti[i]), int(tj[i]), int(tk[i])) for i in range(len(kind))]
+    assert sorted(lib_tasks) == sorted(tasks) and len(set(lib_tasks)) == len(tasks)
+    for i, t in enumerate(lib_tasks):
+        assert indeg[i] == len(preds[t]), t
+        got = {lib_tasks[int(s)] for s in succ[ptr[i]:ptr[i + 1]]}
+        assert got == succs[t], t
+        assert all(int(s) > i for s in succ[ptr[i]:ptr[i + 1]])  # ids are a topological order
+
+
+@pytest.mark.parametrize("T", [1, 3, 6])
+def test_lu_bottom_levels_match_oracle(T):
+    import paper_1402_6601_gb300 as chol
+    cost = [11, 30, 29, 60]
+    bl = chol.lu_dag_bottom_levels(T, cost)
+    kind, ti, tj, tk, *_ = chol.lu_dag_describe(T)
+    ref = odag.bottom_levels(T, dict(enumerate(cost)), odag.program_lu(T))
+    for i in range(len(bl)):
+        assert bl[i] == ref[(int(kind[i]), int(ti[i]), int(tj[i]), int(tk[i]))]
+
+
 def _random_ready(rng, m, W):
     return [dict(tid=rng.randint(0, 10**6) * 64 + i, p=rng.choice([100, 300, 300, 600, rng.randint(1, 900)]),
                  prio=rng.randint(0, 5000), aff=rng.choice([-1] + list(range(W))),

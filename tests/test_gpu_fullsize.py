@@ -17,6 +17,16 @@ target (FP32, three-term BF16) must report and have backward error <= 1e-14.
 Batched, 10,000 matrices of orders uniform in [16, 512] (FP64 and FP32): sampled members
 against the oracle's factor and their backward errors.
 Adjoint, 64 matrices of order 1024: sampled gradients against the oracle's gradient.
+LU with incremental pivoting, n = 8192, automatic tile (128), HEFT (the LU leg of bench.py):
+  - the multipliers, pivots and L11 blocks of every task in the leading T' x T' tiles
+    (T' = 8) depend only on A's leading T' x T' tiles, so they must agree with the oracle's
+    factorization of A[:1024, :1024] (pivots identical, values within relative Frobenius
+    max(1e-12, kappa_2(A[:1024, :1024]) k u), k = 1024, u = 2^-53: rounding differences
+    amplified by the conditioning, the bound of test_gpu_lu.py);
+  - every multiplier is at most 1 in magnitude (partial pivoting inside each panel);
+  - the backward error of the solve is at most n u rho with rho = max|U| / max|A| the growth
+    factor of the computed U (the classical bound of Gaussian elimination; incremental
+    pivoting lets rho rise with n).
 """
 import numpy as np
 import pytest
@@ -25,6 +35,7 @@ import torch
 import oracle
 import synth
 from oracle import adjoint as oadj
+from oracle import lu as olu
 
 pytestmark = pytest.mark.gpu
 
@@ -143,3 +154,53 @@ def test_adjoint_64_matrices_n1024(chol):
         _, Lbar_o = oadj.solve_backward(Lo, xo, w.cpu().numpy())
         Abar_o = oadj.cholesky_backward(Lo, Lbar_o)
         assert oracle.rel_frobenius(Abar.cpu().numpy(), Abar_o) <= 1e-10, i
+
+
+def test_lu_n8192(chol):
+    n, k = 8192, 1024
+    o = chol.opts(nb=0)
+    nb = 128
+    A0 = chol.colmajor(synth.general_matrix(n, seed=1 + 11, device="cuda"))  # bench.py's LU input (seed 1)
+    A = A0.clone()
+    f = chol.lu_factor(A, o)
+    torch.cuda.synchronize()
+    assert int(f.info.item()) == 0
+    T, Tk = n // nb, k // nb
+    Ak = A0[:k, :k].cpu().numpy()
+    Fr, pr, Lr, info = olu.lu_incpiv(Ak, nb)
+    assert info == 0
+    F = A[:k, :k].cpu().numpy()
+    P = f.piv.cpu().numpy()
+    W = f.lw.cpu().numpy()
+    tol = max(1e-12, np.linalg.cond(Ak) * k * 2.0 ** -53)
+    got, ref = [], []
+    for kk in range(Tk):
+        cols = slice(kk * nb, (kk + 1) * nb)
+        for i in range(kk, Tk):
+            rows = slice(i * nb, (i + 1) * nb)
+            off = (kk * T + i) * nb
+            np.testing.assert_array_equal(P[off:off + nb], pr[(i, kk)])
+            if i == kk:
+                got.append(np.tril(F[rows, cols], -1).ravel())
+                ref.append(np.tril(Fr[rows, cols], -1).ravel())
+            else:
+                got.append(F[rows, cols].ravel())
+                ref.append(Fr[rows, cols].ravel())
+                woff = (kk * T + i) * olu.IB * nb
+                got.append(W[woff:woff + olu.IB * nb].reshape(nb, olu.IB).T.ravel())
+                ref.append(Lr[(i, kk)].ravel())
+    got, ref = np.concatenate(got), np.concatenate(ref)
+    assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref)
+    # multipliers bounded by 1 everywhere (strict lower part of the tiled factor and Lw)
+    low = torch.tril(A, -1)
+    assert float(low.abs().max()) <= 1.0
+    assert float(f.lw.abs().max()) <= 1.0
+    # backward error of a solve against the classical bound n u rho
+    rho = float(torch.triu(A).abs().max() / A0.abs().max())
+    b = chol.colmajor(synth.rhs(n, 2, seed=5, device="cuda"))
+    x = b.clone()
+    chol.lu_solve(f, x)
+    torch.cuda.synchronize()
+    R = b - A0 @ x
+    berr = float((R.abs().amax(0) / (A0.abs().sum(1).amax() * x.abs().amax(0) + b.abs().amax(0))).amax())
+    assert berr <= n * 1.11e-16 * rho
