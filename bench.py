@@ -35,7 +35,7 @@ FP64_PEAK_GFLOPS = SMS * FP64_FMA_PER_CLK_PER_SM * 2 * SM_MAX_MHZ / 1000.0  # 12
 # DRAM bytes (read + write) of one factor launch, from a one-pass ncu capture of this exact
 # configuration (profiles/bench_n32768_nb256_launch_list.txt); None for configurations that
 # were not captured with the current kernel.
-MEASURED_FACTOR_TRAFFIC = {(32768, 256, "heft"): 1004220507392 + 201737060864}
+MEASURED_FACTOR_TRAFFIC = {(32768, 256, "heft"): 1003565810432 + 201701767424}
 
 
 def parse():
