@@ -73,6 +73,9 @@ def parse():
     p.add_argument("--lu-nb", type=int, default=0)
     p.add_argument("--lu-steps", type=int, default=3)
     p.add_argument("--lu-policy", default="heft")
+    p.add_argument("--lu-sweep", action="store_true",
+                   help="also time the LU leg under every ready-queue policy (HEFT, DADA(0/0.5/1), "
+                        "DADA(0.5)+CP, stealing, static)")
     return p.parse_args()
 
 
@@ -439,21 +442,36 @@ def run_lu(args, chol, dev):
     A = torch.empty_like(A0)
     work = torch.empty(chol.lu_workspace_size(n, o), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    A.copy_(A0)
-    f = chol.lu_factor(A, o, work=work, stream=stream)
-    torch.cuda.synchronize()
-    if int(f.info.item()) != 0:
-        raise RuntimeError("LU info %d" % int(f.info.item()))
-    ms = []
-    for _ in range(args.lu_steps):
+
+    def timed_factors(o):
         A.copy_(A0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
         f = chol.lu_factor(A, o, work=work, stream=stream)
-        e1.record(stream)
         torch.cuda.synchronize()
-        ms.append(e0.elapsed_time(e1))
+        if int(f.info.item()) != 0:
+            raise RuntimeError("LU info %d" % int(f.info.item()))
+        ms = []
+        for _ in range(args.lu_steps):
+            A.copy_(A0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            f = chol.lu_factor(A, o, work=work, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return f, ms
+
+    sweep = None
+    if args.lu_sweep:
+        sweep = []
+        for pol, alpha, cp in (("heft", 0.5, False), ("heft", 0.5, True), ("dada", 0.0, False), ("dada", 0.5, False),
+                               ("dada", 1.0, False), ("dada", 0.5, True), ("steal", 0.5, False),
+                               ("static", 0.5, False)):
+            _, pm = timed_factors(chol.opts(nb=args.lu_nb, policy=pol, alpha=alpha, use_cp=cp))
+            pt = sum(pm) / len(pm)
+            sweep.append({"policy": pol + ("(%g)" % alpha if pol == "dada" else "") + ("+CP" if cp else ""),
+                          "factor_ms": round(pt, 2), "gflops": round(2.0 * n ** 3 / 3.0 / (pt / 1000.0) / 1e9, 1)})
+    f, ms = timed_factors(o)
     b = chol.colmajor(synth.rhs(n, 1, seed=args.seed + 12, device=dev))
     x = b.clone()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -473,7 +491,8 @@ def run_lu(args, chol, dev):
             "factor_ms": round(t, 2), "gflops": round(gf, 1), "flops": "2n^3/3",
             "frac_of_fp64_peak": round(gf / FP64_PEAK_GFLOPS, 4), "tiles": T,
             "tasks": int(chol.lib.chol_lu_dag_task_count(T)),
-            "solve_ms_1rhs": round(solve_ms, 2), "solve_backward_error": berr, "info": int(f.info.item())}
+            "solve_ms_1rhs": round(solve_ms, 2), "solve_backward_error": berr, "info": int(f.info.item()),
+            "policies": sweep}
 
 
 def run_batched(args, chol, dev):
