@@ -83,6 +83,21 @@ def step_flops(n, nrhs):
     return n ** 3 / 3.0 + 2.0 * n * n * nrhs
 
 
+def job_throughput(ms_local, flops_per_rank, device=None):
+    """(ms, GFLOP/s) of the whole job: the slowest rank's time (max over ranks when a process
+    group is up) and the work of all ranks divided by it (replicas: every rank runs the
+    same workload)."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    ms = float(ms_local)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, flops_per_rank * world / (ms / 1000.0) / 1e9
+
+
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -269,12 +284,7 @@ def main():
     clk = clocks.stop()
     ms = e_start.elapsed_time(e_end)
     fac_ms = [a.elapsed_time(b) for a, b in fac_events]
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    total_flops = step_flops(n, nrhs) * args.steps * world
-    value = total_flops / (ms / 1000.0) / 1e9
+    ms, value = job_throughput(ms, step_flops(n, nrhs) * args.steps, device=dev)
 
     # correctness of the timed result (cheap O(n^2 nrhs) check on the device)
     R = B0 - torch.mm(A0, B)
