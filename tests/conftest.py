@@ -8,6 +8,21 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+def _load_by_path(name, path):
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(name, path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def pytest_sessionstart(session):
+    # the tests load the CUDA library (host code and exports on CPU, kernels on a GPU) and the
+    # oracle's C code: compile them first when they are missing or older than their sources
+    _load_by_path("_chol_build", os.path.join(ROOT, "paper_1402_6601_gb300", "build.py")).build()
+    _load_by_path("_oracle_build", os.path.join(ROOT, "oracle", "build.py")).build()
+
+
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: takes more than a few seconds")
