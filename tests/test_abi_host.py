@@ -209,3 +209,30 @@ def test_automatic_tile_size():
         auto = chol.workspace_size(n, chol.opts(nb=0))
         assert auto == chol.workspace_size(n, chol.opts(nb=nb)), (n, nb)
         assert auto != chol.workspace_size(n, chol.opts(nb=64 if nb == 128 else 128)), n
+
+
+@pytest.mark.parametrize("n,nb", [(8192, 128), (1000, 128), (300, 64), (1, 16), (0, 128)])
+def test_lu_aux_sizes(n, nb):
+    # pivots: T^2 nb ints; L11 blocks: T^2 x 32 x nb doubles (T = ceil(n / nb))
+    import paper_1402_6601_gb300 as chol
+    o = chol.opts(nb=nb)
+    npiv, nlw = ctypes.c_longlong(-1), ctypes.c_longlong(-1)
+    assert chol.lib.chol_lu_aux_size(n, ctypes.byref(o), ctypes.byref(npiv), ctypes.byref(nlw)) == 0
+    T = -(-n // nb)
+    assert npiv.value == T * T * nb and nlw.value == T * T * 32 * nb
+
+
+def test_lu_options_checked_on_the_host():
+    import paper_1402_6601_gb300 as chol
+    n = ctypes.c_longlong(0)
+    # the LU tile kernels take tiles up to 256
+    assert chol.lib.chol_lu_aux_size(1000, ctypes.byref(chol.opts(nb=512)), ctypes.byref(n), None) == -1
+    assert chol.lib.chol_lu_workspace_size(1000, ctypes.byref(chol.opts(nb=512))) == 0
+    assert chol.lib.chol_lu_workspace_size(1000, ctypes.byref(chol.opts(nb=256))) > 0
+    assert chol.lib.chol_lu_aux_size(-1, ctypes.byref(chol.opts(nb=64)), None, None) == -1
+
+
+@pytest.mark.parametrize("T", [1, 2, 8, 64, 128])
+def test_lu_task_counts_closed_form(T):
+    import paper_1402_6601_gb300 as chol
+    assert chol.lib.chol_lu_dag_task_count(T) == sum(1 + 2 * m + m * m for m in range(T))
