@@ -13,6 +13,8 @@ imports it.
   a task becomes ready when its predecessors have completed).
 * ``sched`` restates Algorithm 1 (HEFT activate) and Algorithm 2 (DADA activate) for one
   activation on identical workers.
+* ``simulate`` runs the data-flow loop (Section 2) in simulated time on W identical
+  workers with a given placement, so whole schedules can be checked on the CPU.
 * ``lu`` is the tile LU with incremental pivoting (PLASMA DGETRF, the paper's second
   workload, Section 4.1) and its solve, kernel by kernel in program order (numpy).
 """
