@@ -22,7 +22,7 @@ __all__ = [
     "solve_refine", "refine_workspace_size", "cholesky_backward", "solve_backward", "lower",
     "cholesky", "cholesky_solve", "solve_spd", "BatchOpts", "Batch", "posv_batched", "factor_batched",
     "solve_batched", "batched_autotune", "lu_factor", "lu_solve", "lu_workspace_size", "LUFactors",
-    "dag_describe", "dag_bottom_levels", "lu_dag_describe", "lu_dag_bottom_levels", "sched_activate", "sched_activate_device",
+    "dag_describe", "dag_bottom_levels", "lu_dag_describe", "lu_dag_bottom_levels", "chrome_trace", "sched_activate", "sched_activate_device",
     "CholeskyError",
 ]
 
@@ -345,14 +345,47 @@ def posv_host(A, B, o=None, stage=None, stream=None):
     return int(info.value)
 
 
-def trace(work, n, o):
-    """The per-task trace (ntasks x 4 int64) recorded when o.trace is set."""
+def trace(work, n, o, graph="chol"):
+    """The per-task trace (ntasks x 4 int64: worker, queue it was taken from, start ns, end ns)
+    recorded when o.trace is set, from the workspace of chol_factor (graph="chol") or of
+    chol_lu_factor (graph="lu"). o.nb must be the tile size the call used (not 0)."""
     off = int(lib.chol_factor_trace_offset(n, ctypes.byref(o)))
     if off < 0:
         raise ValueError("tracing is off")
+    if o.nb <= 0:
+        raise ValueError("pass the options with the tile size the factorization used")
     T = (n + o.nb - 1) // o.nb
-    nt = int(lib.chol_dag_task_count(T))
+    nt = int(lib.chol_lu_dag_task_count(T) if graph == "lu" else lib.chol_dag_task_count(T))
     return work[off:off + nt * 32].view(torch.int64).reshape(nt, 4)
+
+
+_KIND_NAMES = {"chol": ("POTRF", "TRSM", "SYRK", "GEMM"), "lu": ("GETRF", "GESSM", "TSTRF", "SSSSM")}
+
+
+def chrome_trace(records, T, graph="chol", path=None):
+    """Chrome-trace (about:tracing / Perfetto) events from a per-task trace: one complete
+    event per task on the row of the worker that ran it, named by kind and tile indices,
+    times in microseconds from the first start. Tasks without a record (start < 0) are left
+    out. Returns the JSON object; writes it to `path` when given."""
+    import json
+    import numpy as np
+    rec = np.asarray(records.cpu() if hasattr(records, "cpu") else records, dtype=np.int64)
+    kind, ti, tj, tk, *_ = lu_dag_describe(T) if graph == "lu" else dag_describe(T)
+    names = _KIND_NAMES[graph]
+    ran = rec[:, 2] >= 0
+    t0 = int(rec[ran, 2].min()) if ran.any() else 0
+    events = []
+    for t in np.nonzero(ran)[0]:
+        w, q, a, b = (int(x) for x in rec[t])
+        k = int(kind[t])
+        events.append({"name": "%s(%d,%d,%d)" % (names[k], ti[t], tj[t], tk[t]), "cat": names[k], "ph": "X",
+                       "ts": (a - t0) / 1000.0, "dur": (b - a) / 1000.0, "pid": 0, "tid": w,
+                       "args": {"task": int(t), "queue": q}})
+    out = {"traceEvents": events, "displayTimeUnit": "ms"}
+    if path is not None:
+        with open(path, "w") as f:
+            json.dump(out, f)
+    return out
 
 
 def dag_describe(T):

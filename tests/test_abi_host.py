@@ -236,3 +236,27 @@ def test_lu_options_checked_on_the_host():
 def test_lu_task_counts_closed_form(T):
     import paper_1402_6601_gb300 as chol
     assert chol.lib.chol_lu_dag_task_count(T) == sum(1 + 2 * m + m * m for m in range(T))
+
+
+@pytest.mark.parametrize("graph", ["chol", "lu"])
+def test_chrome_trace_export(graph, tmp_path):
+    # synthetic per-task records (worker, queue, start ns, end ns) in the trace's layout
+    import json
+    import paper_1402_6601_gb300 as chol
+    T = 3
+    kind, ti, tj, tk, *_ = chol.lu_dag_describe(T) if graph == "lu" else chol.dag_describe(T)
+    nt = len(kind)
+    rec = np.zeros((nt, 4), np.int64)
+    for t in range(nt):
+        rec[t] = (t % 2, (t + 1) % 2, 5000 + 2000 * t, 5000 + 2000 * t + 1500)
+    rec[nt - 1] = (-1, -1, -1, -1)  # a task without a record is left out
+    path = tmp_path / "trace.json"
+    out = chol.chrome_trace(rec, T, graph=graph, path=str(path))
+    assert json.loads(path.read_text()) == out
+    ev = out["traceEvents"]
+    assert len(ev) == nt - 1
+    first = "GETRF(0,0,0)" if graph == "lu" else "POTRF(0,0,0)"
+    assert ev[0]["name"] == first and ev[0]["ts"] == 0.0 and ev[0]["dur"] == 1.5 and ev[0]["tid"] == 0
+    assert ev[1]["ts"] == 2.0 and ev[1]["tid"] == 1 and ev[1]["args"] == {"task": 1, "queue": 0}
+    names = {e["name"].split("(")[0] for e in ev}
+    assert names <= set(chol._KIND_NAMES[graph])
