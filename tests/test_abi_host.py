@@ -260,3 +260,21 @@ def test_chrome_trace_export(graph, tmp_path):
     assert ev[1]["ts"] == 2.0 and ev[1]["tid"] == 1 and ev[1]["args"] == {"task": 1, "queue": 0}
     names = {e["name"].split("(")[0] for e in ev}
     assert names <= set(chol._KIND_NAMES[graph])
+
+
+def test_lu_argument_errors_before_any_launch():
+    # argument checks return before the library touches a device (they hold on a CPU-only host)
+    import paper_1402_6601_gb300 as chol
+    o = ctypes.byref(chol.opts(nb=128))
+    big = ctypes.byref(chol.opts(nb=512))
+    f, s = chol.lib.chol_lu_factor, chol.lib.chol_lu_solve
+    assert f(-1, None, 1, None, None, o, None, 0, None, None) == -1            # negative order
+    assert f(100, None, 100, None, None, o, None, 0, None, None) == -1         # no dInfo
+    fake = ctypes.c_void_p(256)  # never dereferenced: rejected before any launch
+    assert f(100, fake, 99, fake, fake, o, fake, 1 << 20, fake, None) == -1    # lda < n
+    assert f(100, fake, 100, None, fake, o, fake, 1 << 20, fake, None) == -1   # no pivot array
+    assert f(100, fake, 100, fake, fake, big, fake, 1 << 20, fake, None) == -1  # tile above 256
+    assert s(-1, 1, None, 1, None, None, o, None, 1, None) == -1
+    assert s(100, 1, fake, 100, fake, fake, o, fake, 99, None) == -1           # ldb < n
+    assert s(100, 1, fake, 100, fake, fake, big, fake, 100, None) == -1
+    assert s(100, 0, None, 100, None, None, o, None, 100, None) == 0            # nothing to solve
