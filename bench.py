@@ -16,7 +16,6 @@ maximum time over ranks is used; rank 0 prints the JSON line.
 """
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -220,7 +219,6 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    import numpy as np
     import torch
     import torch.distributed as dist
     import synth
