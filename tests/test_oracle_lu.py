@@ -3,7 +3,8 @@
 Each pin is fixed by something other than the oracle itself:
   * one tile (T = 1): GETRF is LAPACK's partial-pivoting LU, so scipy's getrf gives the
     same pivots and factors (after moving the multipliers of each block to LAPACK's row
-    order);
+    order); on column diagonally dominant matrices no interchange happens at any T, and the
+    tile factors are LAPACK's L and U across all tiles;
   * A = L U with dyadic L (|l| < 1) and integer U: no interchange can happen and every
     intermediate is exact, so the factors come back bitwise and integer solutions exactly;
   * the recorded transformations reduce A itself to U = triu(F) (the definition of what the
@@ -69,6 +70,22 @@ def test_dyadic_factor_and_solve_exact(n, nb, ib):
     X = synth.integer_vector(n, 3, seed=n)
     B = A @ X
     np.testing.assert_array_equal(lu.lu_solve(F, piv, Lw, nb, B, ib), X)
+
+
+@pytest.mark.parametrize("n,nb,ib", [(96, 32, 32), (150, 48, 16), (200, 64, 8), (130, 128, 32)])
+def test_column_dominant_matrices_match_lapack_across_tiles(n, nb, ib):
+    # strictly column diagonally dominant: the Schur complements stay so, every pivot search
+    # keeps the diagonal row, and the tile factors are LAPACK's unpivoted L and U
+    G = synth.general_matrix(n, seed=n).numpy()
+    A = G + np.diag(np.abs(G).sum(axis=0) + 1.0)
+    F, piv, Lw, info = lu.lu_incpiv(A, nb=nb, ib=ib)
+    P, L, U = scipy.linalg.lu(A)
+    np.testing.assert_array_equal(P, np.eye(n))
+    assert info == 0
+    assert np.abs(np.triu(F) - U).max() <= 1e-14 * np.abs(U).max()
+    assert np.abs(np.tril(F, -1) - np.tril(L, -1)).max() <= 1e-14
+    assert all((p == np.arange(len(p)) % ib).all() for p in piv.values())
+    assert not any(w.any() for w in Lw.values())
 
 
 @pytest.mark.parametrize("n,nb,ib", [(96, 32, 32), (100, 32, 8), (150, 48, 16), (77, 77, 32), (70, 16, 32)])
