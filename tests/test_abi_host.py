@@ -278,3 +278,22 @@ def test_lu_argument_errors_before_any_launch():
     assert s(100, 1, fake, 100, fake, fake, o, fake, 99, None) == -1           # ldb < n
     assert s(100, 1, fake, 100, fake, fake, big, fake, 100, None) == -1
     assert s(100, 0, None, 100, None, None, o, None, 100, None) == 0            # nothing to solve
+
+
+def test_batch_descriptor_host_logic():
+    # the pointer / order / leading-dimension arrays a batched call passes, built on the host
+    import torch
+    import paper_1402_6601_gb300 as chol
+    orders = [3, 0, 2]
+    flat = torch.arange(13, dtype=torch.float64)
+    offs = [0, 9, 9]
+    rhs = torch.arange(5, dtype=torch.float64)
+    b = chol.Batch(flat, offs, orders, rhs, [0, 3, 3])
+    assert b.batch == 3 and b.N.tolist() == orders and b.lda.tolist() == [3, 1, 2]
+    assert b.A.tolist() == [flat.data_ptr() + 8 * o for o in offs]
+    assert b.B.tolist() == [rhs.data_ptr() + 8 * o for o in (0, 3, 3)]
+    # member m is the column-major n x n block at its offset
+    assert b.matrix(0)[1, 0].item() == 1.0 and b.matrix(0)[0, 1].item() == 3.0
+    assert b.matrix(2).tolist() == [[9.0, 11.0], [10.0, 12.0]]
+    assert b.rhs(2).tolist() == [3.0, 4.0] and b.info.tolist() == [0, 0, 0]
+    assert b.work.numel() >= int(chol.lib.chol_batched_workspace_size(3))
