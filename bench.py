@@ -54,6 +54,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-n", type=int, default=10240)
+    p.add_argument("--cpu-one-thread-n", type=int, default=4096)
     p.add_argument("--seed", type=int, default=1)
     p.add_argument("--no-mixed", action="store_true")
     p.add_argument("--mixed-n", type=int, default=16384)
@@ -167,13 +168,34 @@ def oracle_step(n, nrhs, seed):
     return time.perf_counter() - t0, step_flops(n, nrhs)
 
 
+def oracle_one_thread(n, nrhs, seed, timeout_s=300):
+    """The oracle's factor + solve with one OpenMP thread, in a child process (the thread
+    count of the loaded oracle cannot change); None if it cannot be run."""
+    code = ("import sys; sys.path.insert(0, %r); import bench; t, f = bench.oracle_step(%d, %d, %d); "
+            "print('ONE_THREAD', t, f)" % (ROOT, n, nrhs, seed))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=dict(os.environ, OMP_NUM_THREADS="1"),
+                           capture_output=True, text=True, timeout=timeout_s)
+        line = [x for x in r.stdout.splitlines() if x.startswith("ONE_THREAD")][-1]
+        _, t, f = line.split()
+        return float(t), float(f)
+    except Exception:
+        return None
+
+
 def cpu_baseline(args):
     import oracle
     t, f = oracle_step(args.cpu_sample_n, args.nrhs, args.seed)
-    return {"value": round(f / t / 1e9, 3), "unit": "GFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "seconds": round(t, 2),
-            "sample": "oracle (plain C, FP64, unblocked) factor + solve of one n=%d Gram matrix with %d RHS, "
-                      "same generator as the GPU workload" % (args.cpu_sample_n, args.nrhs)}
+    out = {"value": round(f / t / 1e9, 3), "unit": "GFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+           "seconds": round(t, 2),
+           "sample": "oracle (plain C, FP64, unblocked) factor + solve of one n=%d Gram matrix with %d RHS, "
+                     "same generator as the GPU workload" % (args.cpu_sample_n, args.nrhs)}
+    one = oracle_one_thread(args.cpu_one_thread_n, args.nrhs, args.seed)
+    if one is not None:
+        out["one_thread"] = {"value": round(one[1] / one[0] / 1e9, 3), "unit": "GFLOP/s", "cores": 1,
+                             "seconds": round(one[0], 2),
+                             "sample": "the same with OMP_NUM_THREADS=1 on one n=%d matrix" % args.cpu_one_thread_n}
+    return out
 
 
 def run_reference(args):
