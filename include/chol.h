@@ -14,8 +14,8 @@
  *  - Matrices are column-major with a leading dimension (LAPACK), double precision.
  *  - Pointers named d... are DEVICE pointers on the current CUDA device; h... are host
  *    pointers. The caller owns all memory, including the workspaces; the library keeps no
- *    pointer after a call returns and allocates nothing on the device except inside
- *    chol_posv_host (which documents it).
+ *    pointer after a call returns and allocates no device memory (chol_posv_host, too,
+ *    works in a caller-provided device buffer).
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream). Calls
  *    that take a stream are asynchronous with respect to the host: the return value only
  *    reports argument checks and launch errors; numerical status is written to device
@@ -125,16 +125,18 @@ chol_status chol_solve(int n, int nrhs, const double *dL, int lda, double *dB, i
                        void *dWork, size_t work_bytes, int *dInfo, void *stream);
 
 /* Allocation-free chol_solve. The paper has no counterpart: this entry point is for callers
- * that cannot allocate device memory -- code that must not call cudaMalloc while a stream
- * is being captured into a CUDA graph, or that runs under a fixed device-memory budget in
- * which every allocation belongs to the host application -- and so cannot provide the
- * workspace chol_solve needs. Arguments and results are those of chol_solve.
+ * that cannot allocate device memory -- code that runs under a fixed device-memory budget in
+ * which every allocation belongs to the host application, or inside a framework that hands
+ * the library device pointers but no allocator -- and so cannot provide the workspace
+ * chol_solve needs. Arguments, argument checks and results are those of chol_solve.
  *  - The workspace is a fixed 256 KiB array of this library in device global memory
  *    (each GPU that loads the library holds it until the process exits). Problems whose
  *    chol_solve_workspace_size(n, nrhs) exceeds 256 KiB -- ceil(n/32) * ceil(nrhs/32) >
  *    32704 -- are rejected with CHOL_ERR_UNSUPPORTED before anything is launched.
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- *    with that device current; make that first call before any stream capture.
+ *    with that device current and keeps it for the process; make that first call before
+ *    any stream capture. After cudaDeviceReset the kept address is stale: do not call this
+ *    entry point on a device that was reset.
  *  - Every call shares the one array and clears what it needs before use; two calls whose
  *    work overlaps on the GPU (different streams, no ordering between them) race on it.
  *  - Calls no cudaMalloc, cudaFree or other allocating routine.
@@ -196,6 +198,9 @@ size_t chol_factor_lowp_workspace_size(int precision, int n, const chol_opts *op
  * dInfo device int: the low-precision factor's info (j > 0: A is not positive definite in
  *       that precision; X is then left at zero and *dBerr is +inf).
  * dIters, dBerr device int / double (nullable): steps taken and the final backward error.
+ *       ||A||_inf in eta is the largest FP32 sum of |a_ij| over a row (relative error below
+ *       n 2^-24, which scales eta by at most that factor). If those sums overflow FP32
+ *       (entries near FLT_MAX), no step is taken, X is left at zero and *dBerr is NaN.
  * All steps run on `stream` with no host synchronisation: every step's kernels return at
  * once after convergence, so the call is one fixed sequence of launches.
  */

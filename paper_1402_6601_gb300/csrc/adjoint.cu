@@ -80,12 +80,6 @@ __global__ void lower_scaled_kernel(const double *C, int64_t ldc, double *Out, i
   }
 }
 
-static std::once_flag g_adj_once;
-static void adj_attrs() {
-  std::call_once(g_adj_once, [] {
-    cudaFuncSetAttribute(nt_tiles_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_SMEM_BYTES);
-  });
-}
 
 static cudaError_t launch_transpose(const double *src, int64_t lds, double *dst, int64_t ldd, int rows, int cols,
                                     int mask, cudaStream_t s) {
@@ -96,7 +90,8 @@ static cudaError_t launch_transpose(const double *src, int64_t lds, double *dst,
 
 static cudaError_t launch_nt(double *C, int64_t ldc, const double *A, int64_t lda, const double *B, int64_t ldb,
                              int M, int N, int K, int lower, int ktri, cudaStream_t s) {
-  adj_attrs();
+  const cudaError_t e = set_smem_attr((const void *)nt_tiles_kernel, TILE_SMEM_BYTES);
+  if (e != cudaSuccess) return e;
   const dim3 grid((M + AT - 1) / AT, (N + AT - 1) / AT);
   nt_tiles_kernel<<<grid, NT, TILE_SMEM_BYTES, s>>>(C, ldc, A, lda, B, ldb, M, N, K, lower, ktri);
   return cudaGetLastError();

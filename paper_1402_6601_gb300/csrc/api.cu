@@ -1,6 +1,8 @@
 // Library-wide entry points: defaults, device queries, and host introspection of the task
 // graph and of the activate policies (the same code the persistent kernel runs).
 #include <mutex>
+#include <set>
+#include <tuple>
 #include <vector>
 #include "common.cuh"
 #include "dag.cuh"
@@ -33,6 +35,21 @@ DeviceInfo current_device_info() {
   if ((int)cache.size() <= dev) cache.resize(dev + 1);
   cache[dev] = di;
   return di;
+}
+
+cudaError_t set_smem_attr(const void *fn, int bytes) {
+  static std::mutex mu;
+  static std::set<std::tuple<const void *, int, int>> done;  // (kernel, device, bytes)
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const auto key = std::make_tuple(fn, dev, bytes);
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count(key)) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  done.insert(key);
+  return cudaSuccess;
 }
 
 // One thread of a warp-wide placement on the device, for chol_sched_activate_device.

@@ -175,10 +175,8 @@ static size_t batch_ws(int batch) { return 256 + align_up((size_t)std::max(1, ba
 template <class T, int MINB>
 static cudaError_t launch_batched(const BatchArgs &a, int grid, cudaStream_t s) {
   constexpr int smem = std::max(BatchTiles<T>::SMEM, BATCH_MAX_N * (int)sizeof(T));
-  static std::once_flag once;
-  std::call_once(once, [] {
-    cudaFuncSetAttribute(batched_kernel<T, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  });
+  const cudaError_t e = set_smem_attr((const void *)batched_kernel<T, MINB>, smem);
+  if (e != cudaSuccess) return e;
   batched_kernel<T, MINB><<<grid, NT, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -188,8 +186,8 @@ static int batch_blocks_per_sm(int wps) {
   int occ = 0;
   constexpr int smem = std::max(BatchTiles<T>::SMEM, BATCH_MAX_N * (int)sizeof(T));
   if (wps >= 2) {
-    cudaFuncSetAttribute(batched_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_kernel<T, 2>, NT, smem) != cudaSuccess) occ = 1;
+    if (set_smem_attr((const void *)batched_kernel<T, 2>, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_kernel<T, 2>, NT, smem) != cudaSuccess) occ = 1;
   } else {
     occ = 1;
   }

@@ -29,6 +29,12 @@ struct DeviceInfo {
 // Properties of the current device (queried once per device and cached).
 DeviceInfo current_device_info();
 
+// Allow kernel `fn` up to `bytes` of dynamic shared memory on the current device. Function
+// attributes belong to a device's context, so this is recorded per (kernel, device): the
+// first call for a pair sets the attribute, later calls return at once. Returns the error of
+// cudaGetDevice or cudaFuncSetAttribute (nothing is recorded after a failure).
+cudaError_t set_smem_attr(const void *fn, int bytes);
+
 }  // namespace chol
 
 #define CHOL_CUDA_TRY(expr)                         \

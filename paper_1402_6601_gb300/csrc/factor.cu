@@ -703,8 +703,6 @@ __global__ void copy_info_kernel(const Ctrl *ctrl, int *dInfo) {
 // ------------------------------------------------------------------------------------
 // host side
 
-static std::once_flag g_attr_once;
-
 static size_t tile_smem_bytes(int prec) {
   switch (prec) {
     case PREC_F64: return TilesF64::SMEM;
@@ -716,6 +714,15 @@ static size_t tile_smem_bytes(int prec) {
 }
 
 static size_t factor_smem_bytes(int prec, int T, int W) { return std::max(tile_smem_bytes(prec), sched_smem_bytes(T, W)); }
+
+// dynamic shared memory the factor kernel of each precision may request
+static int smem_limit(int prec) {
+  switch (prec) {
+    case PREC_F64: return 96 * 1024;
+    case PREC_LU_F64: return 112 * 1024;
+    default: return 200 * 1024;
+  }
+}
 
 static const void *kernel_for(int prec) {
   switch (prec) {
@@ -786,13 +793,8 @@ static bool resolve(int n, const chol_opts *opts, Resolved &r, int prec = PREC_F
 // Workers that will be launched: all SMs x workers per SM, limited by occupancy.
 static int launch_workers(const Resolved &r, const DeviceInfo &di) {
   if (di.sms <= 0) return 1024;
-  std::call_once(g_attr_once, [] {
-    cudaFuncSetAttribute(factor_kernel<TilesF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    cudaFuncSetAttribute(factor_kernel<TilesF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(factor_kernel<TilesTC<1>>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(factor_kernel<TilesTC<3>>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(factor_kernel<LuF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
-  });
+  // a failure shows in the occupancy query below and again, checked, in factor_impl
+  (void)set_smem_attr(kernel_for(r.prec), smem_limit(r.prec));
   const size_t smem = factor_smem_bytes(r.prec, r.T, 2 * di.sms);
   int per_sm = 0;
   const void *fn = kernel_for(r.prec);
@@ -916,6 +918,8 @@ chol_status factor_impl(int prec, int n, void *dA, int lda, const chol_opts *opt
   const size_t smem = factor_smem_bytes(prec, r.T, W);
   void *args[] = {(void *)&a};
   const void *fn = kernel_for(prec);
+  if (smem > (size_t)smem_limit(prec)) return CHOL_ERR_UNSUPPORTED;
+  CHOL_CUDA_TRY(set_smem_attr(fn, smem_limit(prec)));
   CHOL_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(W), dim3(NT), args, smem, s));
   copy_info_kernel<<<1, 32, 0, s>>>(a.ctrl, dInfo);
   CHOL_CUDA_TRY(cudaGetLastError());

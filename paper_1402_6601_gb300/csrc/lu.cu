@@ -241,10 +241,7 @@ extern "C" chol_status chol_lu_solve(int n, int nrhs, const double *dF, int lda,
   const DeviceInfo di = current_device_info();
   if (di.sms <= 0) return CHOL_ERR_CUDA;
   if (di.cc_major != 10 || di.cc_minor != 3) return CHOL_ERR_UNSUPPORTED;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    cudaFuncSetAttribute(lu_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, LU_SOLVE_SMEM_BYTES);
-  });
+  CHOL_CUDA_TRY(set_smem_attr((const void *)lu_solve_kernel, LU_SOLVE_SMEM_BYTES));
   LuSolveArgs a;
   a.n = n;
   a.nb = nb;

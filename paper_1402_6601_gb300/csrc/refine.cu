@@ -92,7 +92,16 @@ __global__ void norm_max_kernel(const float *rsum, int n, RefineCtrl *ctrl) {
     m = threadIdx.x < (blockDim.x >> 5) ? w[threadIdx.x] : 0.f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (threadIdx.x == 0) ctrl->normA = (double)m;
+    if (threadIdx.x == 0) {
+      ctrl->normA = (double)m;
+      // entries near FLT_MAX overflow the FP32 row sums: with an infinite (or NaN) norm every
+      // eta would read 0 and the first step would pass for convergence, so no step is taken
+      // and the backward error is reported as NaN (X stays zero)
+      if (!isfinite(m)) {
+        ctrl->done = 1;
+        ctrl->berr = __longlong_as_double(0x7ff8000000000000ll);
+      }
+    }
   }
 }
 

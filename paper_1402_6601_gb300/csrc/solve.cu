@@ -387,11 +387,9 @@ static cudaError_t launch_solve(const SolveArgs &a, int grid, cudaStream_t s) {
   // second block impossible
   constexpr int SBK = item_rows<T>();
   constexpr size_t bytes = SolveSmem<T, NC, SBK>::BYTES;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    cudaFuncSetAttribute(solve_kernel<T, NC, SBK, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    cudaFuncSetAttribute(solve_kernel<T, NC, SBK, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  });
+  const void *fn = a.trans ? (const void *)solve_kernel<T, NC, SBK, true> : (const void *)solve_kernel<T, NC, SBK, false>;
+  const cudaError_t e = set_smem_attr(fn, (int)bytes);
+  if (e != cudaSuccess) return e;
   if (a.trans) solve_kernel<T, NC, SBK, true><<<grid, SNT, bytes, s>>>(a);
   else solve_kernel<T, NC, SBK, false><<<grid, SNT, bytes, s>>>(a);
   return cudaGetLastError();
@@ -541,7 +539,14 @@ static void *noalloc_scratch(int dev, cudaError_t *err) {
 
 extern "C" chol_status chol_solve_noalloc(int n, int nrhs, const double *dL, int lda, double *dB,
                                           int ldb, int *dInfo, void *stream) {
+  // the argument rules of chol_solve first, then the size limit of the fixed array
   if (n < 0 || nrhs < 0) return CHOL_ERR_INVALID_ARG;
+  if (lda < std::max(1, n) || ldb < std::max(1, n)) return CHOL_ERR_INVALID_ARG;
+  if (n > 0 && nrhs > 0 && (!dL || !dB)) return CHOL_ERR_INVALID_ARG;
+  if (n == 0 || nrhs == 0) {
+    if (dInfo) CHOL_CUDA_TRY(cudaMemsetAsync(dInfo, 0, sizeof(int), (cudaStream_t)stream));
+    return CHOL_OK;
+  }
   if (solve_ws(n, nrhs) > SOLVE_NOALLOC_BYTES) return CHOL_ERR_UNSUPPORTED;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return CHOL_ERR_CUDA;

@@ -213,3 +213,21 @@ def test_tc_register_staged_path(chol, precision, n, nb):
         torch.cuda.synchronize()
         assert int(info.item()) == 0
         assert oracle.rel_frobenius(np.tril(Gd.cpu().numpy().astype(np.float64)), oracle.factor(G)) <= 2e-5
+
+
+def test_refine_overflowing_fp32_norm_reports_nan(chol):
+    # A = 2e37 (G G^T / n + I): every entry is finite in FP32 and so is the factor (L scales by
+    # ~4.5e18), but the FP32 row sums of |a_ij| (up to ~4.8e38 > FLT_MAX) overflow. The solver
+    # must not read the resulting eta = 0 as convergence: no step is taken, X stays zero and
+    # the backward error is NaN.
+    n = 512
+    A = 2e37 * synth.gram_spd(n, seed=9).numpy()
+    B = 2e37 * synth.rhs(n, 2, seed=10).numpy()
+    Ad = chol.colmajor(torch.from_numpy(A).to("cuda"))
+    Bd = chol.colmajor(torch.from_numpy(B).to("cuda"))
+    X, info, iters, berr = chol.solve_refine(Ad, Bd, tol=1e-14, max_iter=5, o=chol.opts(nb=128))
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    assert np.isnan(float(berr.item()))
+    assert int(iters.item()) == 0
+    assert not X.abs().max().item()
