@@ -36,6 +36,33 @@ FP64_PEAK_GFLOPS = SMS * FP64_FMA_PER_CLK_PER_SM * 2 * SM_MAX_MHZ / 1000.0  # 12
 # were not captured with the current kernel.
 MEASURED_FACTOR_TRAFFIC = {(32768, 256, "heft"): 1003565810432 + 201701767424}
 
+# two-sided 95 % quantiles of Student's t for 1..30 degrees of freedom
+_T975 = [12.706, 4.303, 3.182, 2.776, 2.571, 2.447, 2.365, 2.306, 2.262, 2.228, 2.201, 2.179, 2.160, 2.145,
+         2.131, 2.120, 2.110, 2.101, 2.093, 2.086, 2.080, 2.074, 2.069, 2.064, 2.060, 2.056, 2.052, 2.048,
+         2.045, 2.042]
+
+
+def mean_ci95(xs):
+    """(mean, half width of the 95 % confidence interval of the mean, count), Student's t; the
+    paper reports every point as a mean with its 95 % confidence interval (Section 4.1,
+    "Methodology"). The half width is None for a single sample."""
+    xs = [float(x) for x in xs]
+    m = sum(xs) / len(xs)
+    if len(xs) < 2:
+        return m, None, len(xs)
+    sd = statistics.stdev(xs)
+    df = len(xs) - 1
+    t = _T975[df - 1] if df <= len(_T975) else 1.96
+    return m, t * sd / len(xs) ** 0.5, len(xs)
+
+
+def stat(xs, digits=3):
+    m, h, k = mean_ci95(xs)
+    return {"mean": round(m, digits), "ci95": None if h is None else round(h, digits), "n": k}
+
+
+PROBE_KINDS = (("dfma", 0), ("mma_m8n8k4", 1), ("mma_m16n8k4", 2), ("mma_m16n8k8", 3), ("mma_m16n8k16", 4))
+
 
 def parse():
     p = argparse.ArgumentParser()
@@ -59,19 +86,26 @@ def parse():
     p.add_argument("--no-mixed", action="store_true")
     p.add_argument("--mixed-n", type=int, default=16384)
     p.add_argument("--mixed-nrhs", type=int, default=16)
-    p.add_argument("--mixed-steps", type=int, default=2)
+    p.add_argument("--mixed-steps", type=int, default=30)
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--batch", type=int, default=10000)
-    p.add_argument("--batched-steps", type=int, default=3)
+    p.add_argument("--batched-steps", type=int, default=30)
     p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--adj-n", type=int, default=1024)
     p.add_argument("--adj-batch", type=int, default=64)
-    p.add_argument("--adj-steps", type=int, default=2)
+    p.add_argument("--adj-steps", type=int, default=10)
     p.add_argument("--adj-streams", type=int, default=8)
+    p.add_argument("--no-probe", action="store_true", help="skip the FP64 throughput probe")
+    p.add_argument("--fp64-probe-only", action="store_true",
+                   help="run only the FP64 throughput probes (DFMA and the mma.sync .f64 shapes) and print them")
+    p.add_argument("--mixed-fp64-steps", type=int, default=3)
+    p.add_argument("--no-mixed-oracle", action="store_true",
+                   help="skip the oracle's FP64 solution of the mixed-precision configuration (about a minute "
+                        "on 16 host cores)")
     p.add_argument("--no-lu", action="store_true")
     p.add_argument("--lu-n", type=int, default=8192)
     p.add_argument("--lu-nb", type=int, default=0)
-    p.add_argument("--lu-steps", type=int, default=3)
+    p.add_argument("--lu-steps", type=int, default=10)
     p.add_argument("--lu-policy", default="heft")
     p.add_argument("--lu-sweep", action="store_true",
                    help="also time the LU leg under every ready-queue policy (HEFT, DADA(0/0.5/1), "
@@ -153,6 +187,53 @@ class ClockSampler:
                    reasons=sorted(reasons), samples=len(rows),
                    power_w_max=max([num(r[3]) for r in rows if num(r[3]) is not None] or [0.0]))
         return out
+
+
+# ----------------------------------------------------------------------------- FP64 peak
+def run_fp64_probe(chol, dev, target_ms=150.0, reps=5):
+    """Throughput of the FP64 units on this GPU: DFMA chains (the instruction of the factor's
+    tile bodies) and the FP64 warp MMA shapes, each launch sized to about target_ms, timed
+    with CUDA events on the launching stream (best and mean of `reps` launches after a
+    warm-up), with the SM clock sampled during the probe; `at_max_clock` scales the best rate
+    by sm_max_mhz / median sm_mhz (time x clock is constant for a pipe-bound kernel)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    out = torch.zeros(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    clocks = ClockSampler(dev.index if dev.index is not None else 0)
+    res = {}
+    clocks.start()
+
+    def once(kind, blocks, iters):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f = chol.probe_fp64(kind, blocks, 256, iters, out=out, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return f, e0.elapsed_time(e1)
+
+    for name, kind in PROBE_KINDS:
+        blocks = sms * (4 if kind == 0 else 2)
+        iters = 2000
+        _, t = once(kind, blocks, iters)
+        iters = max(1, int(iters * target_ms / max(t, 1e-3)))
+        once(kind, blocks, iters)
+        runs = [once(kind, blocks, iters) for _ in range(reps)]
+        f = runs[0][0]
+        ms = [t for _, t in runs]
+        res[name] = {"gflops_best": round(f / min(ms) / 1e6, 1), "gflops": stat([f / t / 1e6 for t in ms], 1),
+                     "ms": round(sum(ms) / len(ms), 2), "blocks": blocks, "threads": 256, "iters": iters,
+                     "flops_per_launch": f}
+    clk = clocks.stop()
+    med, mx = clk.get("sm_mhz"), clk.get("sm_max_mhz") or SM_MAX_MHZ
+    for v in res.values():
+        v["at_max_clock"] = round(v["gflops_best"] * mx / med, 1) if med else None
+    return {"kinds": res, "clocks": {"sm_mhz": med, "sm_max_mhz": mx, "reasons": clk.get("reasons"),
+                                      "samples": clk.get("samples")},
+            "derived_peak": round(FP64_PEAK_GFLOPS, 1),
+            "method": "each kind keeps every thread (DFMA) or warp (mma.sync .f64) on 8 independent "
+                      "accumulation chains; one launch of ~%d ms per repetition" % int(target_ms)}
 
 
 # ----------------------------------------------------------------------------- oracle arm
@@ -258,6 +339,13 @@ def main():
         if world > 1:
             dist.barrier()
 
+    if args.fp64_probe_only:
+        if rank == 0:
+            print(json.dumps({"fp64_probe": run_fp64_probe(chol, dev)}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
     n, nb, nrhs = args.n, args.nb, args.nrhs
     o = chol.opts(nb=nb, policy=args.policy, alpha=args.alpha, workers_per_sm=args.workers_per_sm,
                   use_cp=args.cp)
@@ -271,7 +359,9 @@ def main():
     stream = torch.cuda.current_stream(dev)
     launches_per_step = 7  # init, bottom levels, persistent factor, info copy; 2 sweeps, info copy
 
-    def step(ev=None):
+    def step(ev=None, start=None):
+        if start is not None:
+            start.record(stream)
         A.copy_(A0)
         B.copy_(B0)
         if ev is not None:
@@ -290,20 +380,20 @@ def main():
     clocks = ClockSampler(local)
     fac_events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                   for _ in range(args.steps)]
-    e_start = torch.cuda.Event(enable_timing=True)
-    e_end = torch.cuda.Event(enable_timing=True)
+    step_events = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    e_start, e_end = step_events[0], step_events[-1]
     clocks.start()
     barrier()
     torch.cuda.synchronize()
-    e_start.record(stream)
     for k in range(args.steps):
-        step(fac_events[k])
+        step(fac_events[k], start=step_events[k])
     e_end.record(stream)
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
     ms = e_start.elapsed_time(e_end)
     fac_ms = [a.elapsed_time(b) for a, b in fac_events]
+    step_ms = [step_events[k].elapsed_time(step_events[k + 1]) for k in range(args.steps)]
     ms, value = job_throughput(ms, step_flops(n, nrhs) * args.steps, device=dev)
 
     # correctness of the timed result (cheap O(n^2 nrhs) check on the device)
@@ -312,12 +402,18 @@ def main():
 
     fac_avg = sum(fac_ms) / len(fac_ms)
     achieved = n ** 3 / 3.0 / (fac_avg / 1000.0) / 1e9
+    fac_stat = stat(fac_ms, 2)
     roofline = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(FP64_PEAK_GFLOPS, 1),
                 "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
                 "traffic": MEASURED_FACTOR_TRAFFIC.get((n, nb, args.policy)),
                 "kernel": "factor_kernel (persistent data-flow, DFMA tile bodies)",
+                "launch_ms": fac_stat,
+                "achieved_ci95": None if fac_stat["ci95"] is None else round(
+                    achieved * fac_stat["ci95"] / fac_stat["mean"], 1),
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz (DFMA; FP64 mma.sync is "
-                               "slower on sm_103)"}
+                               "slower on sm_103, see fp64_probe)"}
+    if not args.no_probe and rank == 0:
+        roofline["fp64_probe"] = run_fp64_probe(chol, dev)
 
     e2e = None
     if not args.no_e2e and rank == 0:
@@ -348,7 +444,8 @@ def main():
             "ms_per_step": round(ms / args.steps, 2), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args),
-            "factor_ms": round(fac_avg, 2), "solve_backward_error": berr,
+            "factor_ms": round(fac_avg, 2), "factor_ms_ci95": fac_stat["ci95"],
+            "step_ms": stat(step_ms, 2), "solve_backward_error": berr,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "mixed_precision": mixed, "batched": batched,
             "adjoint": adjoint, "lu": lu,
             "gpu_launches": launches_per_step * args.steps,
@@ -400,33 +497,36 @@ def run_mixed(args, chol, dev):
         return chol.solve_refine(A_, B_, X=X, tol=1e-14, max_iter=30, o=o, work=rwork, stream=stream,
                                  precision=prec)
 
-    def timed(fn):
+    def timed(fn, steps):
         fn()
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
         out = None
-        for _ in range(args.mixed_steps):
+        for k in range(steps):
+            ev[k].record(stream)
             out = fn()
-        e1.record(stream)
+        ev[steps].record(stream)
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / args.mixed_steps, out
+        ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+        return sum(ms) / len(ms), out, stat(ms, 3)
 
-    t64, _ = timed(fp64_step)
+    t64, _, t64_stat = timed(fp64_step, args.mixed_fp64_steps)
     e64 = _backward_error(A, Bw, B)
+    sols = {"fp64": Bw.clone()}
     low = {"f32": "FP32 (FFMA) tile bodies",
            "bf16x3": "FP32 storage, GEMM updates on tcgen05 with three BF16 operand terms (FP32-accurate), "
                      "SYRK updates in FFMA, diagonal scaling",
            "bf16": "FP32 storage, SYRK/GEMM on tcgen05 with one BF16 operand term, diagonal scaling"}
     variants = {}
     for prec in ("f32", "bf16x3", "bf16"):
-        tmx, out = timed(lambda: mixed_step(prec, A, B))
+        tmx, out, tstat = timed(lambda: mixed_step(prec, A, B), args.mixed_steps)
         _, minfo, iters, berr = out
         finfo = int(minfo.item())
         emx = _backward_error(A, X, B) if finfo == 0 else float("inf")
         reached = bool(finfo == 0 and emx <= 1e-14)
-        v = {"low_precision": low[prec], "ms": round(tmx, 2),
+        if finfo == 0:
+            sols[prec] = X.clone()
+        v = {"low_precision": low[prec], "ms": round(tmx, 2), "ms_stat": tstat,
              "speedup": round(t64 / tmx, 2) if reached else None,  # only at the same backward error
              "iterations": int(iters.item()), "info": finfo,
              "backward_error": emx, "reported_backward_error": float(berr.item()),
@@ -439,18 +539,43 @@ def run_mixed(args, chol, dev):
         variants[prec] = v
     # plain BF16 on a well-conditioned matrix of the same order (A = sym(G G^T)/n + I), for context
     Ag = chol.colmajor(synth.gram_spd(n, seed=args.seed + 3, device=dev))
-    tg, out = timed(lambda: mixed_step("bf16", Ag, B))
+    tg, out, _ = timed(lambda: mixed_step("bf16", Ag, B), 3)
     _, ginfo, giters, gberr = out
     variants["bf16_well_conditioned"] = {
         "workload": "n=%d, %d RHS, A = sym(G G^T)/n + I (kappa <= 5)" % (n, nrhs), "ms": round(tg, 2),
         "iterations": int(giters.item()), "info": int(ginfo.item()),
         "backward_error": _backward_error(Ag, X, B) if int(ginfo.item()) == 0 else float("inf")}
+    # error against the oracle's FP64 solution (plain C Cholesky + substitutions on the host
+    # cores, same bytes of A and B), for every result: max over columns of
+    # ||x - x_oracle||_inf / ||x_oracle||_inf
+    oracle_err = None
+    if not args.no_mixed_oracle:
+        import numpy as np
+        import oracle
+        Ah = A.cpu().numpy()
+        Bh = B.cpu().numpy()
+        t0 = time.perf_counter()
+        Xo = oracle.solve(oracle.factor(Ah), Bh)
+        t_or = time.perf_counter() - t0
+
+        def rel(Xd):
+            Xh = Xd.cpu().numpy()
+            return float((np.abs(Xh - Xo).max(axis=0) / np.abs(Xo).max(axis=0)).max())
+
+        oracle_err = {"oracle_seconds": round(t_or, 1), "oracle_cores": oracle.num_threads(),
+                      "oracle_backward_error": oracle.backward_error(Ah, Xo, Bh),
+                      "kappa_2": 1e6,
+                      "x_rel_err_vs_oracle": {k: rel(v) for k, v in sols.items()}}
+        for k, v in sols.items():
+            if k in variants:
+                variants[k]["x_rel_err_vs_oracle"] = oracle_err["x_rel_err_vs_oracle"][k]
     ok = [p for p in ("f32", "bf16x3") if variants[p]["reached_target"]]
     best = min(ok, key=lambda p: variants[p]["ms"]) if ok else "f32"
     b = variants[best]
     return {"workload": "n=%d, %d RHS, A = Q diag(lambda) Q^T, lambda geometric 1..1e6 (32 Householder "
                         "reflectors), tile 256, HEFT" % (n, nrhs),
-            "fp64_ms": round(t64, 2), "fp64_tile": 128 if n <= 32768 else 256,
+            "fp64_ms": round(t64, 2), "fp64_ms_stat": t64_stat, "fp64_tile": 128 if n <= 32768 else 256,
+            "oracle": oracle_err,
             "mixed_ms": b["ms"], "speedup": b["speedup"], "best": best,
             "low_precision": b["low_precision"] + "; FP64 residual and update",
             "target_backward_error": 1e-14, "fp64_backward_error": e64, "mixed_backward_error": b["backward_error"],
@@ -518,7 +643,7 @@ def run_lu(args, chol, dev):
     return {"workload": "tile LU with incremental pivoting (GETRF/GESSM/TSTRF/SSSSM), n=%d, tile %s, inner "
                         "block 32, %s ready queues; A with i.i.d. N(0,1) entries" % (
                             n, o.nb or "auto", args.lu_policy.upper()),
-            "factor_ms": round(t, 2), "gflops": round(gf, 1), "flops": "2n^3/3",
+            "factor_ms": round(t, 2), "factor_ms_stat": stat(ms, 3), "gflops": round(gf, 1), "flops": "2n^3/3",
             "frac_of_fp64_peak": round(gf / FP64_PEAK_GFLOPS, 4), "tiles": T,
             "tasks": int(chol.lib.chol_lu_dag_task_count(T)),
             "solve_ms_1rhs": round(solve_ms, 2), "solve_backward_error": berr, "info": int(f.info.item()),
@@ -562,18 +687,18 @@ def run_batched(args, chol, dev):
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=stream):
             step()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.batched_steps + 1)]
         with torch.cuda.stream(stream):  # replay() launches on the current stream
             for _ in range(2):
                 graph.replay()
             torch.cuda.synchronize()
-            e0.record(stream)
-            for _ in range(args.batched_steps):
+            for k in range(args.batched_steps):
+                ev[k].record(stream)
                 graph.replay()
-            e1.record(stream)
+            ev[-1].record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.batched_steps
+        step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.batched_steps)]
+        ms = sum(step_ms) / len(step_ms)
         bad = int((work.info != 0).sum().item())
         berr = 0.0
         for m in range(0, len(orders), max(1, len(orders) // 16)):
@@ -582,7 +707,7 @@ def run_batched(args, chol, dev):
             x = work.rhs(m).to(torch.float64)
             r = b - A @ x
             berr = max(berr, float(r.abs().max() / (A.abs().sum(1).max() * x.abs().max() + b.abs().max())))
-        out[name] = {"ms": round(ms, 3), "gflops": round(flops / ms / 1e6, 1),
+        out[name] = {"ms": round(ms, 3), "ms_stat": stat(step_ms, 3), "gflops": round(flops / ms / 1e6, 1),
                      "matrices_per_s": round(len(orders) / ms * 1e3, 1), "failed": bad,
                      "backward_error_sample_max": berr,
                      "autotuned": {"workers_per_sm": best.workers_per_sm, "lpt_order": best.lpt_order,
@@ -641,14 +766,14 @@ def run_adjoint(args, chol, dev):
 
     step()
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(main)
-    for _ in range(args.adj_steps):
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.adj_steps + 1)]
+    for k in range(args.adj_steps):
+        ev[k].record(main)
         step()
-    e1.record(main)
+    ev[-1].record(main)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.adj_steps
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.adj_steps)]
+    ms = sum(step_ms) / len(step_ms)
     flops = m * (n ** 3 / 3.0 + 2.0 * n * n + n ** 3 / 3.0 + 2.0 * n ** 3)
     bad = sum(int(x.item()) != 0 for x in infos)
     # check (outside the timed region): Abar = -(lam x^T + x lam^T)/2 with lam = A^-1 w
@@ -661,7 +786,8 @@ def run_adjoint(args, chol, dev):
     return {"workload": "%d FP64 SPD matrices n=%d (A = sym(G G^T)/n + I), loss = sum(w * x), x = A^-1 b; "
                         "forward factor + solve and backward solve + Cholesky adjoints per matrix, tile 128, "
                         "%d streams, 32 factor workers per matrix" % (m, n, ns),
-            "ms": round(ms, 2), "ms_per_matrix": round(ms / m, 3), "flops_per_step": flops,
+            "ms": round(ms, 2), "ms_stat": stat(step_ms, 2), "ms_per_matrix": round(ms / m, 3),
+            "flops_per_step": flops,
             "gflops": round(flops / ms / 1e6, 1), "frac_of_fp64_peak": round(flops / ms / 1e6 / FP64_PEAK_GFLOPS, 4),
             "nonzero_info": bad, "grad_rel_diff_vs_closed_form": worst}
 

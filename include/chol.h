@@ -388,6 +388,19 @@ chol_status chol_sched_activate_device(int policy, double alpha, int max_iter, d
                                        int W, const long long *dload, int *dout_tid,
                                        int *dout_worker, int *dout_iters, void *stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Measurement support (not part of the method): throughput probes of the FP64 units, the
+ * denominator of the FP64 factor's roofline. Kind 0 keeps every thread on PROBE_CHAINS = 8
+ * independent DFMA chains (the instruction of the FP64 tile bodies); kinds 1-4 keep every warp
+ * on 8 independent chains of FP64 warp MMAs, mma.sync shapes m8n8k4, m16n8k4, m16n8k8 and
+ * m16n8k16. `iters` iterations per chain, grid `blocks` x `threads` (32..256, a multiple of
+ * 32). chol_probe_fp64_flops returns the flops of such a launch (-1 for invalid arguments);
+ * chol_probe_fp64 launches it on `stream` (dOut: one device double, written only by a
+ * condition that never holds, so the compiler keeps the work). Time the launch with events
+ * on the same stream. */
+long long chol_probe_fp64_flops(int kind, int blocks, int threads, long long iters);
+chol_status chol_probe_fp64(int kind, int blocks, int threads, long long iters, double *dOut, void *stream);
+
 /* Library version string and the number of workers chol_factor would launch on the
  * current device for these options (0 if no usable device). */
 const char *chol_version(void);

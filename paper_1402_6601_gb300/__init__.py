@@ -23,7 +23,7 @@ __all__ = [
     "cholesky", "cholesky_solve", "solve_spd", "BatchOpts", "Batch", "posv_batched", "factor_batched",
     "solve_batched", "batched_autotune", "lu_factor", "lu_solve", "lu_workspace_size", "LUFactors",
     "dag_describe", "dag_bottom_levels", "lu_dag_describe", "lu_dag_bottom_levels", "chrome_trace", "sched_activate", "sched_activate_device",
-    "CholeskyError",
+    "CholeskyError", "probe_fp64",
 ]
 
 POLICIES = {"heft": 0, "dada": 1, "steal": 2, "static": 3}
@@ -107,6 +107,8 @@ _SIGNATURES = {
     "chol_sched_activate": (_I, [_I, _D, _I, _D, _I, _P, _P, _P, _P, _P, _I, _P, _P, _P, _I, _P, _P, _P, _P]),
     "chol_sched_activate_device": (_I, [_I, _D, _I, _D, _I, _P, _P, _P, _P, _P, _I, _P, _P, _P, _I, _P, _P, _P,
                                         _P, _P]),
+    "chol_probe_fp64_flops": (_LL, [_I, _I, _I, _LL]),
+    "chol_probe_fp64": (_I, [_I, _I, _I, _LL, _P, _P]),
     "chol_version": (ctypes.c_char_p, []),
     "chol_num_workers": (_I, [_OPTS]),
 }
@@ -746,3 +748,20 @@ def lu_solve(f, B, stream=None):
                              f.lw.data_ptr(), ctypes.byref(f.opts), B.data_ptr(), ldb, _stream(stream)),
            "chol_lu_solve")
     return B
+
+
+PROBE_KINDS = {"dfma": 0, "mma_m8n8k4": 1, "mma_m16n8k4": 2, "mma_m16n8k8": 3, "mma_m16n8k16": 4}
+
+
+def probe_fp64(kind, blocks, threads=256, iters=1000, out=None, stream=None):
+    """Launch one FP64 throughput probe (measurement support: DFMA chains, or one of the
+    mma.sync .f64 shapes) on `stream` and return the flops of the launch; time it with CUDA
+    events on the same stream."""
+    k = PROBE_KINDS[kind] if isinstance(kind, str) else int(kind)
+    flops = int(lib.chol_probe_fp64_flops(k, blocks, threads, iters))
+    if flops < 0:
+        raise CholeskyError("chol_probe_fp64_flops: invalid arguments")
+    if out is None:
+        out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    _check(lib.chol_probe_fp64(k, blocks, threads, iters, out.data_ptr(), _stream(stream)), "chol_probe_fp64")
+    return flops

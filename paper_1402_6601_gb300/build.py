@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libchol_gb300.so")
 SOURCES = ["csrc/adjoint.cu", "csrc/api.cu", "csrc/batched.cu", "csrc/factor.cu", "csrc/lu.cu", "csrc/solve.cu",
-           "csrc/refine.cu"]
+           "csrc/refine.cu", "csrc/probe.cu"]
 HEADERS = ["csrc/blockacc.cuh", "csrc/common.cuh", "csrc/dag.cuh", "csrc/dag_lu.cuh", "csrc/internal.cuh", "csrc/sched.cuh",
            "csrc/tiles_f32.cuh", "csrc/tiles_f64.cuh", "csrc/tiles_lu.cuh", "csrc/tiles_tc.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -14,7 +14,8 @@ Recipes
   gram_spd(n)         A = sym(G G^T)/n + I, G n x n i.i.d. N(0,1) drawn in FP32, product in
                       FP32 (TF32 off), symmetrised and promoted to FP64; kappa(A) <~ 5.
   householder_spd(n)  A = Q diag(lambda) Q^T, lambda_i = 10^(6 i/(n-1)), Q = H_1 ... H_32,
-                      H = I - 2 v v^T / v^T v with v ~ N(0,1); kappa(A) = 1e6.
+                      H = I - 2 v v^T / v^T v with v ~ N(0,1); kappa(A) = 1e6 (and, with
+                      inverse=True, Q diag(1/lambda) Q^T from the same reflectors).
   integer_factor(n)   integer lower L, diag in [1, 8], off-diagonal in [-8, 8]; A = L L^T is
                       then exact in FP64 (|a_ij| <= 64 n < 2^53).
   pascal(n)           P_ij = C(i + j, i) (0-based).
@@ -67,12 +68,16 @@ def rhs(n, nrhs, seed=1, device="cpu"):
     return B.T  # n x nrhs view whose columns are contiguous
 
 
-def householder_spd(n, seed=0, device="cpu", n_reflectors=32, cond=1e6):
-    """A = Q diag(lambda) Q^T with geometrically spaced lambda in [1, cond]."""
+def householder_spd(n, seed=0, device="cpu", n_reflectors=32, cond=1e6, inverse=False):
+    """A = Q diag(lambda) Q^T with geometrically spaced lambda in [1, cond]. With inverse=True
+    the same reflectors (same seed) are applied to diag(1/lambda): the inverse of that A up to
+    rounding, for condition numbers in norms other than the 2-norm."""
     device = torch.device(device)
     g = _gen(seed, device)
     lam = torch.pow(torch.tensor(10.0, dtype=torch.float64, device=device),
                     torch.arange(n, dtype=torch.float64, device=device) * (math.log10(cond) / max(n - 1, 1)))
+    if inverse:
+        lam = 1.0 / lam
     A = torch.diag(lam)
     for _ in range(n_reflectors):
         v = torch.randn(n, generator=g, device=device, dtype=torch.float64)

@@ -11,9 +11,19 @@ FP64 factor + solve, n = 32768, 64 right-hand sides, tile 256 (HEFT) and 512 (DA
     (relative 1e-12);
   - info = 0 and a positive diagonal over the whole factor;
   - the normwise (Rigal-Gaches, infinity norm) backward error of sampled right-hand sides,
-    computed on the host in FP64 from A, x and b, is <= 1e-14.
+    computed on the host in FP64 from A, x and b, is <= 1e-14;
+  - the factor residual in four seeded random directions v, ||(A - L L^T) v||_inf /
+    (||A||_inf ||v||_inf), computed on the host in FP64 by row blocks, is <= n u (the bound
+    of a backward-stable Cholesky; an O(n^2) check of the whole factor).
+FP64 factor, n = 8192 (bench.py's policy-comparison size), tiles 256 and 128 under HEFT,
+DADA(0.5)+CP and work stealing: the whole L against the oracle's factor of the same A,
+relative Frobenius 1e-12 (kappa(A) <= 5).
 Mixed precision, n = 16384, kappa = 1e6, 16 right-hand sides: each form that reaches the
-target (FP32, three-term BF16) must report and have backward error <= 1e-14.
+target (FP32, three-term BF16) must report and have backward error <= 1e-14, and its X must
+agree with the oracle's FP64 solution of the same A and B within the forward-error bound
+that both backward errors imply, sum of 2 kappa_inf eta / (1 - kappa_inf eta) (Higham,
+Accuracy and Stability, Thm 7.2), with kappa_inf = ||A||_inf ||A^-1||_inf computed from
+A^-1 = Q diag(1/lambda) Q^T built from the same reflectors.
 Batched, 10,000 matrices of orders uniform in [16, 512] (FP64 and FP32): sampled members
 against the oracle's factor and their backward errors.
 Adjoint, 64 matrices of order 1024: sampled gradients against the oracle's gradient.
@@ -87,13 +97,71 @@ def test_factor_solve_n32768(chol, nb, policy, alpha):
     assert oracle.rel_frobenius(got, ref) <= 1e-12
     # backward error of sampled right-hand sides
     assert _berr_cols(A, X, B, [0, 17, 40, 63]) <= 1e-14
+    # factor residual in random directions
+    assert _factor_residual_dirs(A, F, nv=4, seed=11) <= n * 2.0 ** -53
+
+
+def _factor_residual_dirs(A_dev, F_dev, nv, seed, chunk=2048):
+    """max over nv random directions v of ||(A - L L^T) v||_inf / (||A||_inf ||v||_inf), on
+    the host in FP64: w = L^T v by column blocks of L, then A v - L w by row blocks."""
+    n = A_dev.shape[0]
+    V = np.random.default_rng(seed).standard_normal((n, nv))
+    W = np.zeros((n, nv))
+    for c0 in range(0, n, chunk):           # W[c0:c1] = L[:, c0:c1]^T V
+        c1 = min(n, c0 + chunk)
+        Lc = np.tril(F_dev[c0:, c0:c1].cpu().numpy())   # rows c0.. of columns c0..c1-1
+        W[c0:c1] = Lc.T @ V[c0:]
+    R = np.zeros((n, nv))
+    normA = 0.0
+    for r0 in range(0, n, chunk):           # R[r0:r1] = A[r0:r1] V - L[r0:r1, :r1] W[:r1]
+        r1 = min(n, r0 + chunk)
+        Ab = A_dev[r0:r1, :].cpu().numpy()
+        normA = max(normA, float(np.abs(Ab).sum(axis=1).max()))
+        Lb = F_dev[r0:r1, :r1].cpu().numpy()
+        Lb[:, r0:r1] = np.tril(Lb[:, r0:r1])
+        R[r0:r1] = Ab @ V - Lb @ W[:r1]
+    return float((np.abs(R).max(axis=0) / (normA * np.abs(V).max(axis=0))).max())
+
+
+@pytest.fixture(scope="module")
+def factor8192():
+    n, seed = 8192, 1
+    A = synth.gram_spd(n, seed=seed, device="cuda")
+    return A, oracle.factor(A.cpu().numpy())
+
+
+@pytest.mark.parametrize("nb", [256, 128])
+@pytest.mark.parametrize("policy,alpha,cp", [("heft", 0.5, False), ("dada", 0.5, True), ("steal", 0.5, False)])
+def test_factor_n8192_whole_L(chol, factor8192, nb, policy, alpha, cp):
+    A, Lo = factor8192
+    F = chol.colmajor(A)
+    info, _ = chol.factor(F, chol.opts(nb=nb, policy=policy, alpha=alpha, use_cp=cp))
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    assert oracle.rel_frobenius(np.tril(F.cpu().numpy()), Lo) <= 1e-12
+
+
+@pytest.fixture(scope="module")
+def mixed16384():
+    """bench.py's mixed-precision input, the oracle's FP64 solution and kappa_inf(A)."""
+    n, nrhs, seed = 16384, 16, 1
+    A = synth.householder_spd(n, seed=seed, cond=1e6, device="cuda")
+    B = synth.rhs(n, nrhs, seed=seed + 7, device="cuda")
+    Ai = synth.householder_spd(n, seed=seed, cond=1e6, device="cuda", inverse=True)
+    kinf = float(A.abs().sum(1).max() * Ai.abs().sum(1).max())
+    del Ai
+    Ah, Bh = A.cpu().numpy(), B.cpu().numpy()
+    Xo = oracle.solve(oracle.factor(Ah), Bh)
+    eta_o = [oracle.backward_error(Ah, Xo[:, c], Bh[:, c]) for c in range(nrhs)]
+    return A, B, Xo, eta_o, kinf
 
 
 @pytest.mark.parametrize("precision", ["f32", "bf16x3"])
-def test_mixed_precision_n16384(chol, precision):
-    n, nrhs, seed = 16384, 16, 1  # bench.py's mixed leg
-    A = chol.colmajor(synth.householder_spd(n, seed=seed, cond=1e6, device="cuda"))
-    B = chol.colmajor(synth.rhs(n, nrhs, seed=seed + 7, device="cuda"))
+def test_mixed_precision_n16384(chol, mixed16384, precision):
+    n, nrhs = 16384, 16  # bench.py's mixed leg
+    A0, B0, Xo, eta_o, kinf = mixed16384
+    A = chol.colmajor(A0)
+    B = chol.colmajor(B0)
     X, info, iters, berr = chol.solve_refine(A, B, tol=1e-14, max_iter=30, o=chol.opts(nb=256),
                                              precision=precision)
     torch.cuda.synchronize()
@@ -103,6 +171,14 @@ def test_mixed_precision_n16384(chol, precision):
     # FFMA; with them on the tensor cores it needed five)
     assert 2 <= int(iters.item()) <= 4
     assert _berr_cols(A, X, B, list(range(nrhs))) <= 1e-14
+    # X against the oracle's FP64 solution, column by column, within the forward-error bound
+    # that the two backward errors imply
+    Xh, Ah, Bh = X.cpu().numpy(), A.cpu().numpy(), B.cpu().numpy()
+    for c in range(nrhs):
+        eta_g = oracle.backward_error(Ah, Xh[:, c], Bh[:, c])
+        bound = sum(2 * kinf * e / (1 - kinf * e) for e in (eta_g, eta_o[c]))
+        err = np.abs(Xh[:, c] - Xo[:, c]).max() / np.abs(Xo[:, c]).max()
+        assert err <= bound, (c, err, bound, kinf)
 
 
 @pytest.mark.parametrize("dtype,tol_l,tol_b", [(torch.float64, 1e-12, 1e-14), (torch.float32, 2e-5, 1e-6)])
