@@ -330,9 +330,16 @@ chol_status chol_lu_factor(int n, double *dA, int lda, int *dPiv, double *dLw, c
 
 /* Solve A X = B with the outputs of chol_lu_factor (same n and opts, so the same tiles):
  * the recorded transformations applied to B in factorization order, then back substitution
- * with U. dB n x nrhs (ldb >= max(1, n)) is overwritten by X. One kernel; no workspace. */
+ * with U. dB n x nrhs (ldb >= max(1, n)) is overwritten by X. dWork: at least
+ * chol_lu_solve_workspace_size(n, nrhs, opts) bytes, 256-byte aligned (ready flags of the
+ * transformations and of the substitution). dInfo (device int, nullable): 0, or
+ * CHOL_INFO_TIMEOUT if a bounded wait expired (X is then undefined). Two kernels on `stream`:
+ * the transformations run as a wavefront over (tile row, tile column) nodes, the
+ * substitution as the backward sweep of chol_solve with U. */
+size_t chol_lu_solve_workspace_size(int n, int nrhs, const chol_opts *opts);
 chol_status chol_lu_solve(int n, int nrhs, const double *dF, int lda, const int *dPiv, const double *dLw,
-                          const chol_opts *opts, double *dB, int ldb, void *stream);
+                          const chol_opts *opts, double *dB, int ldb, void *dWork, size_t work_bytes,
+                          int *dInfo, void *stream);
 
 /* ---------------------------------------------------------------------------------------
  * Introspection of the task graph and of the activate policies. These run on the HOST,
@@ -390,8 +397,8 @@ chol_status chol_sched_activate_device(int policy, double alpha, int max_iter, d
 
 /* ---------------------------------------------------------------------------------------
  * Measurement support (not part of the method): throughput probes of the FP64 units, the
- * denominator of the FP64 factor's roofline. Kind 0 keeps every thread on PROBE_CHAINS = 8
- * independent DFMA chains (the instruction of the FP64 tile bodies); kinds 1-4 keep every warp
+ * denominator of the FP64 factor's roofline. Kind 0 keeps every thread on 16 independent
+ * DFMA chains, a 4 x 4 register tile as in the FP64 tile bodies; kinds 1-4 keep every warp
  * on 8 independent chains of FP64 warp MMAs, mma.sync shapes m8n8k4, m16n8k4, m16n8k8 and
  * m16n8k16. `iters` iterations per chain, grid `blocks` x `threads` (32..256, a multiple of
  * 32). chol_probe_fp64_flops returns the flops of such a launch (-1 for invalid arguments);

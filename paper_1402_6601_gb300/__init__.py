@@ -21,7 +21,8 @@ __all__ = [
     "posv_host", "workspace_size", "solve_workspace_size", "num_workers", "trace", "factor_f32",
     "solve_refine", "refine_workspace_size", "cholesky_backward", "solve_backward", "lower",
     "cholesky", "cholesky_solve", "solve_spd", "BatchOpts", "Batch", "posv_batched", "factor_batched",
-    "solve_batched", "batched_autotune", "lu_factor", "lu_solve", "lu_workspace_size", "LUFactors",
+    "solve_batched", "batched_autotune", "lu_factor", "lu_solve", "lu_workspace_size", "lu_solve_workspace_size",
+    "LUFactors",
     "dag_describe", "dag_bottom_levels", "lu_dag_describe", "lu_dag_bottom_levels", "chrome_trace", "sched_activate", "sched_activate_device",
     "CholeskyError", "probe_fp64",
 ]
@@ -96,7 +97,8 @@ _SIGNATURES = {
     "chol_lu_workspace_size": (_SZ, [_I, _OPTS]),
     "chol_lu_aux_size": (_I, [_I, _OPTS, _P, _P]),
     "chol_lu_factor": (_I, [_I, _P, _I, _P, _P, _OPTS, _P, _SZ, _P, _P]),
-    "chol_lu_solve": (_I, [_I, _I, _P, _I, _P, _P, _OPTS, _P, _I, _P]),
+    "chol_lu_solve_workspace_size": (_SZ, [_I, _I, _OPTS]),
+    "chol_lu_solve": (_I, [_I, _I, _P, _I, _P, _P, _OPTS, _P, _I, _P, _SZ, _P, _P]),
     "chol_lu_dag_task_count": (_LL, [_I]),
     "chol_lu_dag_describe": (_I, [_I, _P, _P, _P, _P, _P, _P, _P]),
     "chol_lu_dag_bottom_levels": (_I, [_I, _P, _P]),
@@ -740,15 +742,31 @@ def lu_factor(A, o=None, work=None, stream=None, check=False):
     return LUFactors(A, piv, lw, o, info)
 
 
-def lu_solve(f, B, stream=None):
-    """X = A^{-1} B in place on the column-major float64 CUDA matrix B, from lu_factor's output."""
+def lu_solve_workspace_size(n, nrhs, o=None):
+    o = o if o is not None else opts()
+    return int(lib.chol_lu_solve_workspace_size(n, nrhs, ctypes.byref(o)))
+
+
+def lu_solve(f, B, work=None, info=None, stream=None, check=False):
+    """X = A^{-1} B in place on the column-major float64 CUDA matrix B, from lu_factor's output.
+    Returns the device info tensor (0, or CHOL_INFO_TIMEOUT if a bounded wait expired)."""
     n = f.F.shape[0]
     ldb = _check_matrix(B, "B")
-    _check(lib.chol_lu_solve(n, B.shape[1], f.F.data_ptr(), _check_matrix(f.F, "F"), f.piv.data_ptr(),
-                             f.lw.data_ptr(), ctypes.byref(f.opts), B.data_ptr(), ldb, _stream(stream)),
+    nrhs = B.shape[1]
+    need = lu_solve_workspace_size(n, nrhs, f.opts)
+    if work is None:
+        work = _workspace(need, B.device)
+    if info is None:
+        info = torch.zeros(1, dtype=torch.int32, device=B.device)
+    _check(lib.chol_lu_solve(n, nrhs, f.F.data_ptr(), _check_matrix(f.F, "F"), f.piv.data_ptr(),
+                             f.lw.data_ptr(), ctypes.byref(f.opts), B.data_ptr(), ldb, work.data_ptr(),
+                             work.numel(), info.data_ptr(), _stream(stream)),
            "chol_lu_solve")
-    return B
-
+    if check:
+        torch.cuda.synchronize()
+        if int(info.item()) != 0:
+            raise CholeskyError("chol_lu_solve: info %d" % int(info.item()))
+    return info
 
 PROBE_KINDS = {"dfma": 0, "mma_m8n8k4": 1, "mma_m16n8k4": 2, "mma_m16n8k8": 3, "mma_m16n8k16": 4}
 

@@ -25,4 +25,11 @@ chol_status solve_f32(int n, int nrhs, const float *dL, int lda, float *dB, int 
 
 size_t solve_workspace_bytes(int n, int nrhs);
 
+// U X = B in place with the upper triangle of the tiles (the tile LU's U): one backward sweep
+// of the substitution kernel (workspace solve_workspace_bytes(n, nrhs)); its items are skipped
+// once *prev_abort (nullable) is set. solve_upper_info merges the sweep's status into *dInfo.
+chol_status solve_upper_f64(int n, int nrhs, const double *dU, int lda, double *dB, int ldb, void *dWork,
+                            const int *prev_abort, cudaStream_t s);
+chol_status solve_upper_info(void *dWork, int *dInfo, cudaStream_t s);
+
 }  // namespace chol

@@ -6,255 +6,304 @@
 // the upper triangle of the tiles (diagonal tiles' upper parts and the tiles right of the
 // diagonal); back substitution with U finishes the solve.
 //
-// One block per group of LU_SOLVE_COLS right-hand sides runs the whole sequence for its
-// columns (right-hand sides are independent). The tile row being transformed (Y_k) and the
-// one it is paired with (Y_i) are staged in shared memory; per inner block the interchanges
-// run one thread per column, the unit lower L11 solve one warp per column (lane = row), and
-// the elimination of the paired rows one thread per (row, column). The back substitution
-// sums U_kj Y_j with the columns split over the threads and four partial sums per thread,
-// then solves the diagonal tile's upper triangle block by block, one warp per column.
+// The transformations form a graph of their own: node (k, k) applies GETRF(k) to the tile
+// row Y_k, node (i, k), i > k, applies TSTRF(i, k) to [Y_k; Y_i]. Node (i, k) needs node
+// (i - 1, k) (the previous TSTRF of column k, or GETRF(k), left Y_k as it must be) and node
+// (i, k - 1) (the last transformation that touched Y_i); (k, k) needs (k, k - 1). Its longest
+// path has about 2T nodes against T(T + 1)/2 in all, so lu_fwd_kernel runs it as a wavefront:
+// thread blocks (one per SM) claim (node, group of right-hand sides) items from an atomic
+// counter in column-major node order, where every dependency comes earlier, wait on the
+// ready flags of the two predecessors (bounded), apply the node's inner blocks to the staged
+// rows and publish a flag. Everything that does not depend on Y -- the pivots, the L11
+// blocks, the first inner block's L21 rows -- is loaded before the wait. The back
+// substitution is the backward sweep of the Cholesky solve with U (solve_upper_f64).
 #include <algorithm>
-#include <mutex>
+#include <cmath>
 #include "common.cuh"
 #include "internal.cuh"
 #include "tiles_lu.cuh"
 
 namespace chol {
 
-constexpr int LU_SOLVE_COLS = 16;
-constexpr int LU_SOLVE_SMEM_BYTES = (2 * LU_NB_MAX * LU_SOLVE_COLS + LU_IB * DS_LD + LU_IB) * 8 + LU_IB * 4;
+constexpr int LG = 8;                       // right-hand sides per item
+constexpr int LNB = LU_NB_MAX / LU_IB;      // inner blocks per tile, at most
+constexpr int L11LD = LU_IB + 1;
+constexpr int LU_FWD_SMEM_BYTES =
+    (2 * LU_NB_MAX * LG + LNB * LU_IB * L11LD) * 8 + LU_NB_MAX * 4;
+constexpr int LU_FWD_EXCL_SMEM = 120 * 1024;  // request at least this much: one block per SM
+constexpr int LU_FWD_SMEM_REQ = LU_FWD_SMEM_BYTES > LU_FWD_EXCL_SMEM ? LU_FWD_SMEM_BYTES : LU_FWD_EXCL_SMEM;
 
-struct LuSolveArgs {
-  int n, nb, T, nrhs;
+struct LuFwdCtrl {
+  unsigned int next_item;
+  int abort;
+  int info;
+  int pad[61];
+};
+
+struct LuFwdArgs {
+  int n, nb, T, nrhs, ngroups;
+  int64_t nnodes, nitems;
   const double *F;
   int64_t lda;
   const int *piv;
   const double *lw;
   double *B;
   int64_t ldb;
+  LuFwdCtrl *ctrl;
+  int *flags;  // per (node, group): 1 once the node's transformation of that group is stored
+  int64_t timeout_ns;
 };
 
-struct LuSolveSmem {
-  double *yk, *yi, *l11, *rinv;
-  int *piv;
-};
-
-__device__ __forceinline__ LuSolveSmem lu_solve_smem(unsigned char *raw) {
-  LuSolveSmem s;
-  double *d = reinterpret_cast<double *>(raw);
-  s.yk = d;
-  s.yi = d + LU_NB_MAX * LU_SOLVE_COLS;
-  s.l11 = s.yi + LU_NB_MAX * LU_SOLVE_COLS;
-  s.rinv = s.l11 + LU_IB * DS_LD;
-  s.piv = reinterpret_cast<int *>(s.rinv + LU_IB);
-  return s;
+// nodes of the columns before k: sum over k' < k of (T - k')
+__host__ __device__ __forceinline__ int64_t lu_col_offset(int T, int k) {
+  return (int64_t)k * T - (int64_t)k * (k - 1) / 2;
+}
+__device__ __forceinline__ void lu_node_decode(int T, int64_t node, int &i, int &k) {
+  // largest k with lu_col_offset(T, k) <= node, from the quadratic, then corrected
+  const double b = 2.0 * T + 1.0;
+  int kk = (int)floor((b - sqrt(fmax(b * b - 8.0 * (double)node, 0.0))) * 0.5);
+  kk = max(0, min(T - 1, kk));
+  while (kk > 0 && lu_col_offset(T, kk) > node) --kk;
+  while (kk + 1 < T && lu_col_offset(T, kk + 1) <= node) ++kk;
+  k = kk;
+  i = k + (int)(node - lu_col_offset(T, k));
 }
 
-constexpr int SLD = LU_NB_MAX;  // staged rows are column-major with this leading dimension
-
-// rows [r0, r0 + m) of g columns of Y (global, ld) <-> staged rows S[c * SLD + r]
-__device__ __forceinline__ void lu_stage_in(const double *Y, int64_t ldy, int r0, int m, int g, double *S) {
-  for (int e = threadIdx.x; e < m * g; e += NT) {
-    const int c = e / m, r = e - c * m;
-    S[c * SLD + r] = ldcg(Y + (int64_t)c * ldy + r0 + r);
-  }
-}
-__device__ __forceinline__ void lu_stage_out(double *Y, int64_t ldy, int r0, int m, int g, const double *S) {
-  for (int e = threadIdx.x; e < m * g; e += NT) {
-    const int c = e / m, r = e - c * m;
-    stcg(Y + (int64_t)c * ldy + r0 + r, S[c * SLD + r]);
-  }
-}
-
-// One inner block's transformation on staged rows: X1s (w rows), X2s (mA rows), g columns;
-// piv and L11 in shared memory, L21 (mA x w) in global memory. Ends synchronised.
-__device__ void lu_solve_block(double *X1s, double *X2s, int w, int mA, const int *piv, const double *L11,
-                               const double *L21, int64_t ldl, int g) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid < g) {
-    double *x1 = X1s + tid * SLD, *x2 = X2s + tid * SLD;
-    for (int j = 0; j < w; ++j) {
-      const int q = piv[j];
-      if (q == j || q < 0 || q >= w + mA) continue;
-      double *o = q < w ? x1 + q : x2 + (q - w);
-      const double t = x1[j];
-      x1[j] = *o;
-      *o = t;
+// Wait (thread 0) until flag f is set; returns false if the run aborted or the wait expired.
+__device__ bool lu_wait_flag(const LuFwdArgs &a, const int *f) {
+  const uint64_t t0 = globaltimer_ns();
+  int64_t spins = 0;
+  unsigned slp = 32;
+  while (ld_volatile(f) == 0) {
+    if (ld_volatile(&a.ctrl->abort)) return false;
+    if (globaltimer_ns() - t0 > (uint64_t)a.timeout_ns || ++spins > (a.timeout_ns >> 7) + 100000) {
+      atomicCAS(&a.ctrl->info, 0, CHOL_INFO_TIMEOUT);
+      atomicExch(&a.ctrl->abort, 1);
+      return false;
     }
+    __nanosleep(slp);
+    slp = slp < 256 ? slp * 2 : 256;
   }
-  __syncthreads();
-  for (int c = warp; c < g; c += NT / 32) {
-    double y = lane < w ? X1s[c * SLD + lane] : 0.0;
-    for (int j = 0; j + 1 < w; ++j) {
-      const double yj = __shfl_sync(0xffffffffu, y, j);
-      if (lane > j && lane < w) y = fma(-L11[lane * DS_LD + j], yj, y);
-    }
-    if (lane < w) X1s[c * SLD + lane] = y;
-  }
-  __syncthreads();
-  for (int e = tid; e < mA * g; e += NT) {
-    const int c = e / mA, r = e - c * mA;
-    double t = X2s[c * SLD + r];
-    // the row of L21 is loaded in groups of eight before the products that use it
-#pragma unroll
-    for (int j0 = 0; j0 < LU_IB; j0 += 8) {
-      double l[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) l[u] = j0 + u < w ? ldcg(L21 + (int64_t)(j0 + u) * ldl + r) : 0.0;
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (j0 + u < w) t = fma(-l[u], X1s[c * SLD + j0 + u], t);
-    }
-    X2s[c * SLD + r] = t;
-  }
-  __syncthreads();
+  return true;
 }
 
-__global__ void __launch_bounds__(NT) lu_solve_kernel(const __grid_constant__ LuSolveArgs a) {
+__global__ void __launch_bounds__(NT, 1) lu_fwd_kernel(const __grid_constant__ LuFwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const LuSolveSmem s = lu_solve_smem(smem_raw);
-  constexpr int G = LU_SOLVE_COLS;
-  static_assert(SLD * G <= LU_NB_MAX * LU_SOLVE_COLS, "staging buffers");
+  double *Yk = reinterpret_cast<double *>(smem_raw);    // [LG][LU_NB_MAX] column-major
+  double *Yi = Yk + LU_NB_MAX * LG;
+  double *L11 = Yi + LU_NB_MAX * LG;                     // [LNB][LU_IB][L11LD] row-major
+  int *spiv = reinterpret_cast<int *>(L11 + LNB * LU_IB * L11LD);
+  __shared__ long long s_item;
+  __shared__ int s_ok;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int g0 = blockIdx.x * G;
-  const int g = min(G, a.nrhs - g0);
-  double *Y = a.B + (int64_t)g0 * a.ldb;
   const int nb = a.nb, T = a.T;
   const int64_t lda = a.lda, ldb = a.ldb;
-  auto tile = [&](int i, int j) { return a.F + (int64_t)j * nb * lda + (int64_t)i * nb; };
+  auto tile = [&](int r, int c) { return a.F + (int64_t)c * nb * lda + (int64_t)r * nb; };
   auto dim = [&](int t) { return min(nb, a.n - t * nb); };
+  while (true) {
+    if (tid == 0) s_item = ld_volatile(&a.ctrl->abort) ? -1 : (long long)atomicAdd(&a.ctrl->next_item, 1u);
+    __syncthreads();
+    const long long item = s_item;
+    if (item < 0 || item >= a.nitems) break;
+    const int64_t node = item / a.ngroups;
+    const int g = (int)(item - node * a.ngroups);
+    int i, k;
+    lu_node_decode(T, node, i, k);
+    const bool getrf = i == k;
+    const int nk = dim(k), mi = getrf ? 0 : dim(i);
+    const int c0g = g * LG, gc = min(LG, a.nrhs - c0g);
+    const int nblk = (nk + LU_IB - 1) / LU_IB;
+    const double *Akk = tile(k, k);
+    const double *Aik = getrf ? nullptr : tile(i, k);
+    const double *lwp = getrf ? nullptr : a.lw + ((int64_t)k * T + i) * LU_IB * nb;
+    // --- independent of Y: pivots, L11 of every inner block, L21 rows of the first block
+    const int *pv = a.piv + ((int64_t)k * T + i) * nb;
+    for (int e = tid; e < nk; e += NT) spiv[e] = __ldcg(pv + e);
+    for (int e = tid; e < nblk * LU_IB * LU_IB; e += NT) {
+      const int b = e / (LU_IB * LU_IB), q = e - b * LU_IB * LU_IB;
+      const int r = q & (LU_IB - 1), c = q >> 5;
+      const int w = min(LU_IB, nk - b * LU_IB);
+      double v = 0.0;
+      if (r < w && c < r)
+        v = getrf ? __ldcg(Akk + (int64_t)(b * LU_IB + c) * lda + b * LU_IB + r)
+                  : __ldcg(lwp + (int64_t)(b * LU_IB + c) * LU_IB + r);
+      L11[(b * LU_IB + r) * L11LD + c] = v;
+    }
+    // row of X2 this thread eliminates in block b: GETRF rows c1 + tid of the diagonal tile,
+    // TSTRF row tid of A_ik; its L21 row (w values) is held in registers, the next block's
+    // loaded while the current one is applied
+    double lcur[LU_IB], lnext[LU_IB];
+    auto load_l21 = [&](int b, double (&l)[LU_IB]) {
+      const int c0 = b * LU_IB, w = min(LU_IB, nk - c0), c1 = c0 + w;
+      const int m2 = getrf ? nk - c1 : mi;
+      const double *base = getrf ? Akk + (int64_t)c0 * lda + c1 : Aik + (int64_t)c0 * lda;
+#pragma unroll
+      for (int j = 0; j < LU_IB; ++j) l[j] = (tid < m2 && j < w) ? __ldcg(base + (int64_t)j * lda + tid) : 0.0;
+    };
+    load_l21(0, lcur);
+    // --- wait for the predecessors: (i - 1, k) and (i, k - 1)
+    if (tid == 0) {
+      bool ok = true;
+      if (!getrf) ok = lu_wait_flag(a, &a.flags[(node - 1) * a.ngroups + g]);
+      if (ok && k > 0) {
+        const int64_t pred = lu_col_offset(T, k - 1) + (i - (k - 1));
+        ok = lu_wait_flag(a, &a.flags[pred * a.ngroups + g]);
+      }
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    __threadfence();
+    // --- stage the rows (column-major, ld LU_NB_MAX)
+    for (int e = tid; e < nk * gc; e += NT) {
+      const int c = e / nk, r = e - c * nk;
+      Yk[c * LU_NB_MAX + r] = __ldcg(a.B + (int64_t)(c0g + c) * ldb + (int64_t)k * nb + r);
+    }
+    for (int e = tid; e < mi * gc; e += NT) {
+      const int c = e / mi, r = e - c * mi;
+      Yi[c * LU_NB_MAX + r] = __ldcg(a.B + (int64_t)(c0g + c) * ldb + (int64_t)i * nb + r);
+    }
+    __syncthreads();
+    for (int b = 0; b < nblk; ++b) {
+      const int c0 = b * LU_IB, w = min(LU_IB, nk - c0), c1 = c0 + w;
+      const int m2 = getrf ? nk - c1 : mi;
+      double *X1 = Yk + c0;                      // w rows
+      double *X2 = getrf ? Yk + c1 : Yi;         // m2 rows
+      if (b + 1 < nblk) load_l21(b + 1, lnext);
+      // interchanges in order, one thread per right-hand side
+      if (tid < gc) {
+        double *x1 = X1 + tid * LU_NB_MAX, *x2 = X2 + tid * LU_NB_MAX;
+        for (int j = 0; j < w; ++j) {
+          const int q = spiv[c0 + j];
+          if (q == j || q < 0 || q >= w + m2) continue;
+          double *o = q < w ? x1 + q : x2 + (q - w);
+          const double t = x1[j];
+          x1[j] = *o;
+          *o = t;
+        }
+      }
+      __syncthreads();
+      // unit lower L11 solve, one warp per right-hand side (lane = row)
+      const double *l11 = L11 + (size_t)b * LU_IB * L11LD;
+      for (int c = warp; c < gc; c += NT / 32) {
+        double y = lane < w ? X1[c * LU_NB_MAX + lane] : 0.0;
+        for (int j = 0; j + 1 < w; ++j) {
+          const double yj = __shfl_sync(0xffffffffu, y, j);
+          if (lane > j) y = fma(-l11[lane * L11LD + j], yj, y);
+        }
+        if (lane < w) X1[c * LU_NB_MAX + lane] = y;
+      }
+      __syncthreads();
+      // X2 -= L21 X1, one thread per row of X2, four partial sums per right-hand side
+      if (tid < m2) {
+        for (int c = 0; c < gc; ++c) {
+          const double *x1 = X1 + c * LU_NB_MAX;
+          double t[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+          for (int j = 0; j < LU_IB; ++j) t[j & 3] = fma(lcur[j], x1[j], t[j & 3]);
+          X2[c * LU_NB_MAX + tid] -= (t[0] + t[1]) + (t[2] + t[3]);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < LU_IB; ++j) lcur[j] = lnext[j];
+    }
+    // --- store and publish
+    for (int e = tid; e < nk * gc; e += NT) {
+      const int c = e / nk, r = e - c * nk;
+      __stcg(a.B + (int64_t)(c0g + c) * ldb + (int64_t)k * nb + r, Yk[c * LU_NB_MAX + r]);
+    }
+    for (int e = tid; e < mi * gc; e += NT) {
+      const int c = e / mi, r = e - c * mi;
+      __stcg(a.B + (int64_t)(c0g + c) * ldb + (int64_t)i * nb + r, Yi[c * LU_NB_MAX + r]);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) *(volatile int *)&a.flags[node * a.ngroups + g] = 1;
+  }
+}
 
-  // Y <- M Y: the recorded transformations in factorization order
-  for (int k = 0; k < T; ++k) {
-    const int nk = dim(k);
-    const double *Akk = tile(k, k);
-    const int *pk = a.piv + ((int64_t)k * T + k) * nb;
-    lu_stage_in(Y, ldb, k * nb, nk, g, s.yk);
-    for (int c0 = 0; c0 < nk; c0 += LU_IB) {
-      const int w = min(LU_IB, nk - c0), c1 = c0 + w;
-      if (tid < w) s.piv[tid] = pk[c0 + tid];
-      lu_load_l11(Akk + (int64_t)c0 * lda + c0, lda, w, s.l11);
-      lu_solve_block(s.yk + c0, s.yk + c1, w, nk - c1, s.piv, s.l11, Akk + (int64_t)c0 * lda + c1, lda, g);
-    }
-    for (int i = k + 1; i < T; ++i) {
-      const int mi = dim(i);
-      const int *pik = a.piv + ((int64_t)k * T + i) * nb;
-      const double *lw = a.lw + ((int64_t)k * T + i) * LU_IB * nb;
-      const double *Aik = tile(i, k);
-      lu_stage_in(Y, ldb, i * nb, mi, g, s.yi);
-      for (int c0 = 0; c0 < nk; c0 += LU_IB) {
-        const int w = min(LU_IB, nk - c0);
-        if (tid < w) s.piv[tid] = pik[c0 + tid];
-        lu_load_l11(lw + (int64_t)c0 * LU_IB, LU_IB, w, s.l11);
-        lu_solve_block(s.yk + c0, s.yi, w, mi, s.piv, s.l11, Aik + (int64_t)c0 * lda, lda, g);
-      }
-      lu_stage_out(Y, ldb, i * nb, mi, g, s.yi);
-      __syncthreads();
-    }
-    lu_stage_out(Y, ldb, k * nb, nk, g, s.yk);
-    __syncthreads();
-  }
-  // U X = Y by tile rows from the bottom
-  double *part = s.yi;  // partial sums, [part][row][col]
-  for (int k = T - 1; k >= 0; --k) {
-    const int nk = dim(k);
-    const double *Akk = tile(k, k);
-    lu_stage_in(Y, ldb, k * nb, nk, g, s.yk);
-    const int q0 = (k + 1) * nb, nq = a.n - q0;  // columns of U right of the diagonal tile
-    const int pairs = nk * g;
-    const int parts = pairs >= NT ? 1 : min(NT / pairs, LU_NB_MAX * G / pairs);
-    if (nq > 0) {
-      for (int idx = tid; idx < pairs * parts; idx += NT) {
-        const int p = idx / pairs, e = idx - p * pairs;
-        const int c = e / nk, r = e - c * nk;
-        const double *urow = a.F + (int64_t)q0 * lda + (int64_t)k * nb + r;  // U(k nb + r, q0 + q)
-        const double *ycol = Y + (int64_t)c * ldb + q0;
-        // eight products in flight per thread, four partial sums
-        double t[4] = {0.0, 0.0, 0.0, 0.0};
-        int q = p;
-        for (; q + 7 * parts < nq; q += 8 * parts) {
-          double u[8], y[8];
-#pragma unroll
-          for (int v = 0; v < 8; ++v) {
-            u[v] = ldcg(urow + (int64_t)(q + v * parts) * lda);
-            y[v] = ldcg(ycol + q + v * parts);
-          }
-#pragma unroll
-          for (int v = 0; v < 8; ++v) t[v & 3] = fma(u[v], y[v], t[v & 3]);
-        }
-        for (; q < nq; q += parts) t[0] = fma(ldcg(urow + (int64_t)q * lda), ldcg(ycol + q), t[0]);
-        part[p * pairs + e] = (t[0] + t[1]) + (t[2] + t[3]);
-      }
-      __syncthreads();
-      for (int e = tid; e < pairs; e += NT) {
-        const int c = e / nk, r = e - c * nk;
-        double t = 0.0;
-        for (int p = 0; p < parts; ++p) t += part[p * pairs + e];
-        s.yk[c * SLD + r] -= t;
-      }
-      __syncthreads();
-    }
-    for (int c0 = ((nk - 1) / LU_IB) * LU_IB; c0 >= 0; c0 -= LU_IB) {
-      const int w = min(LU_IB, nk - c0);
-      const double *U = Akk + (int64_t)c0 * lda + c0;
-      for (int e = tid; e < LU_IB * LU_IB; e += NT) {
-        const int r = e & (LU_IB - 1), c = e >> 5;
-        s.l11[r * DS_LD + c] = (r < w && c < w && c >= r) ? ldcg(U + (int64_t)c * lda + r) : 0.0;
-      }
-      __syncthreads();
-      if (tid < w) s.rinv[tid] = 1.0 / s.l11[tid * DS_LD + tid];
-      __syncthreads();
-      for (int c = warp; c < g; c += NT / 32) {
-        double x = lane < w ? s.yk[c * SLD + c0 + lane] : 0.0;
-        for (int j = w - 1; j >= 0; --j) {
-          if (lane == j) x = quot(x, s.l11[j * DS_LD + j], s.rinv[j]);
-          const double xj = __shfl_sync(0xffffffffu, x, j);
-          if (lane < j) x = fma(-s.l11[lane * DS_LD + j], xj, x);
-        }
-        if (lane < w) s.yk[c * SLD + c0 + lane] = x;
-      }
-      __syncthreads();
-      for (int e = tid; e < c0 * g; e += NT) {  // rows above the block inside the tile
-        const int c = e / c0, r = e - c * c0;
-        double t = s.yk[c * SLD + r];
-        for (int j = 0; j < w; ++j) t = fma(-ldcg(Akk + (int64_t)(c0 + j) * lda + r), s.yk[c * SLD + c0 + j], t);
-        s.yk[c * SLD + r] = t;
-      }
-      __syncthreads();
-    }
-    lu_stage_out(Y, ldb, k * nb, nk, g, s.yk);
-    __syncthreads();
-  }
+__global__ void lu_info_kernel(const LuFwdCtrl *c, int *dInfo) {
+  if (threadIdx.x == 0) *dInfo = c->info;
+}
+
+struct LuSolveLayout {
+  size_t ctrl, flags, sweep, total;
+  int64_t nnodes;
+  int ngroups;
+};
+
+static LuSolveLayout lu_solve_layout(int n, int nrhs, int nb) {
+  LuSolveLayout L;
+  const int T = n > 0 ? (n + nb - 1) / nb : 0;
+  L.nnodes = (int64_t)T * (T + 1) / 2;
+  L.ngroups = (nrhs + LG - 1) / LG;
+  size_t o = 0;
+  L.ctrl = o; o += 256;
+  L.flags = o; o += align_up((size_t)std::max<int64_t>(1, L.nnodes * L.ngroups) * 4, 256);
+  L.sweep = o; o += solve_workspace_bytes(n, nrhs);
+  L.total = o;
+  return L;
 }
 
 }  // namespace chol
 
 using namespace chol;
 
+extern "C" size_t chol_lu_solve_workspace_size(int n, int nrhs, const chol_opts *opts) {
+  if (n < 0 || nrhs < 0) return 0;
+  const int nb = lu_tile_size(n, opts);
+  if (nb <= 0) return 0;
+  return lu_solve_layout(n, nrhs, nb).total;
+}
+
 extern "C" chol_status chol_lu_solve(int n, int nrhs, const double *dF, int lda, const int *dPiv, const double *dLw,
-                                     const chol_opts *opts, double *dB, int ldb, void *stream) {
+                                     const chol_opts *opts, double *dB, int ldb, void *dWork, size_t work_bytes,
+                                     int *dInfo, void *stream) {
   if (n < 0 || nrhs < 0) return CHOL_ERR_INVALID_ARG;
   const int nb = lu_tile_size(n, opts);
   if (nb <= 0) return CHOL_ERR_INVALID_ARG;
-  if (n == 0 || nrhs == 0) return CHOL_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n == 0 || nrhs == 0) {
+    if (dInfo) CHOL_CUDA_TRY(cudaMemsetAsync(dInfo, 0, sizeof(int), s));
+    return CHOL_OK;
+  }
   if (lda < n || ldb < n || !dF || !dPiv || !dLw || !dB) return CHOL_ERR_INVALID_ARG;
+  const LuSolveLayout L = lu_solve_layout(n, nrhs, nb);
+  if (!dWork || work_bytes < L.total || ((uintptr_t)dWork & 255)) return CHOL_ERR_WORKSPACE;
   const DeviceInfo di = current_device_info();
   if (di.sms <= 0) return CHOL_ERR_CUDA;
   if (di.cc_major != 10 || di.cc_minor != 3) return CHOL_ERR_UNSUPPORTED;
-  CHOL_CUDA_TRY(set_smem_attr((const void *)lu_solve_kernel, LU_SOLVE_SMEM_BYTES));
-  LuSolveArgs a;
+  CHOL_CUDA_TRY(set_smem_attr((const void *)lu_fwd_kernel, LU_FWD_SMEM_REQ));
+  unsigned char *ws = static_cast<unsigned char *>(dWork);
+  LuFwdArgs a;
   a.n = n;
   a.nb = nb;
   a.T = (n + nb - 1) / nb;
   a.nrhs = nrhs;
+  a.ngroups = L.ngroups;
+  a.nnodes = L.nnodes;
+  a.nitems = L.nnodes * L.ngroups;
   a.F = dF;
   a.lda = lda;
   a.piv = dPiv;
   a.lw = dLw;
   a.B = dB;
   a.ldb = ldb;
-  const int grid = (nrhs + LU_SOLVE_COLS - 1) / LU_SOLVE_COLS;
-  lu_solve_kernel<<<grid, NT, LU_SOLVE_SMEM_BYTES, (cudaStream_t)stream>>>(a);
+  a.ctrl = reinterpret_cast<LuFwdCtrl *>(ws + L.ctrl);
+  a.flags = reinterpret_cast<int *>(ws + L.flags);
+  a.timeout_ns = 10000000000ll;
+  CHOL_CUDA_TRY(cudaMemsetAsync(ws, 0, L.sweep, s));  // control block and flags
+  const int grid = (int)std::min<int64_t>(a.nitems, (int64_t)di.sms);
+  lu_fwd_kernel<<<grid, NT, LU_FWD_SMEM_REQ, s>>>(a);
   CHOL_CUDA_TRY(cudaGetLastError());
+  // U X = Y, skipped if the transformation aborted
+  const chol_status st = solve_upper_f64(n, nrhs, dF, lda, dB, ldb, ws + L.sweep, &a.ctrl->abort, s);
+  if (st != CHOL_OK) return st;
+  if (dInfo) {
+    lu_info_kernel<<<1, 32, 0, s>>>(a.ctrl, dInfo);
+    CHOL_CUDA_TRY(cudaGetLastError());
+    return solve_upper_info(ws + L.sweep, dInfo, s);
+  }
   return CHOL_OK;
 }

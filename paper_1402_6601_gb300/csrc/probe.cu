@@ -4,29 +4,42 @@
 // others issue the FP64 warp-level MMA shapes (mma.sync ... .f64) back to back. The host
 // times a launch on its stream; chol_probe_fp64_flops gives the flops of that launch.
 //
-// Every thread (DFMA) or warp (MMA) runs PROBE_CHAINS independent accumulation chains, so the
-// pipe, not the latency of one chain, bounds the rate. The operands are runtime values and
-// the accumulators are stored (under a condition the compiler cannot decide), so no work is
-// folded away. x = 1 - 2^-20 and y = 2^-20 keep every chain at the fixed point 1 of
-// a <- a x + y, far from overflow.
+// Every thread (DFMA: 16 chains) or warp (MMA: PROBE_CHAINS chains) runs independent
+// accumulation chains, so the pipe, not the latency of one chain, bounds the rate. The
+// operands are runtime values and the accumulators are stored (under a condition the compiler
+// cannot decide), so no work is folded away; every product is about 2^-40, so the
+// accumulators stay near 1 for any iteration count.
 #include "common.cuh"
 
 namespace chol {
 
 constexpr int PROBE_CHAINS = 8;
 
+// DFMA in the pattern of the factor's register tile: 4 x 4 accumulators acc[i][j] +=
+// a[i] b[j], sixteen independent chains per thread with distinct operand registers.
 __global__ void __launch_bounds__(256) probe_dfma_kernel(long long iters, double x, double y, double *out) {
-  double a[PROBE_CHAINS];
+  double a[4], b[4], acc[4][4];
 #pragma unroll
-  for (int c = 0; c < PROBE_CHAINS; ++c) a[c] = 1.0 + 1e-3 * c + 1e-7 * threadIdx.x;
-  for (long long i = 0; i < iters; ++i) {
+  for (int i = 0; i < 4; ++i) {
+    a[i] = y * (1.0 + 0.125 * i);
+    b[i] = x * y * (1.0 + 0.0625 * i + 1e-9 * threadIdx.x);
+  }
 #pragma unroll
-    for (int c = 0; c < PROBE_CHAINS; ++c) a[c] = fma(a[c], x, y);
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 1.0;
+  for (long long it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
   }
   double s = 0.0;
 #pragma unroll
-  for (int c = 0; c < PROBE_CHAINS; ++c) s += a[c];
-  if (s == -1.0) out[0] = s;  // never true (every chain stays near 1)
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s += acc[i][j];
+  if (s == -1.0) out[0] = s;  // never true (every accumulator stays >= 1)
 }
 
 // Per shape: fragment sizes (doubles per thread) of A, B and C/D, and M, N, K.
@@ -115,7 +128,7 @@ using namespace chol;
 
 extern "C" long long chol_probe_fp64_flops(int kind, int blocks, int threads, long long iters) {
   if (blocks < 1 || threads < 32 || threads > 256 || threads % 32 || iters < 0) return -1;
-  if (kind == 0) return 2ll * PROBE_CHAINS * iters * threads * (long long)blocks;
+  if (kind == 0) return 2ll * 16 * iters * threads * (long long)blocks;
   const long long per = mma_flops_per_warp_iter(kind);
   if (per == 0) return -1;
   return per * iters * (threads / 32) * (long long)blocks;

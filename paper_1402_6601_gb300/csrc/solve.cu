@@ -51,7 +51,8 @@ struct SolveArgs {
   int64_t ldb;
   int n, nrhs, nrb, ngroups;
   int64_t nitems;
-  int trans;  // 0: L Y = B (forward), 1: L^T X = B (backward)
+  int trans;  // 0: L Y = B (forward), 1: L^T X = B (backward), 2: U X = B (backward, U upper,
+              //    the LU solve's back substitution)
   int64_t timeout_ns;
   SolveCtrl *ctrl;
   const int *prev_abort;  // abort flag of the sweep that produced B (nullable)
@@ -104,14 +105,19 @@ __device__ __forceinline__ void vload(const T *p, T (&v)[V]) {
 }
 
 // SBK rows per item: 32 (lane = row) or, in FP32, 64 (lane = rows lane and lane + 32), which
-// halves the number of links in the chain of block rows. TRANS: the backward sweep (a.trans).
-template <class T, int NC, int SBK, bool TRANS>
+// halves the number of links in the chain of block rows. MODE (a.trans): 0 forward with the
+// lower L, 1 backward with L^T, 2 backward with an upper U whose blocks are read like L's in
+// the forward sweep (row block r, column block m > r: U(r0 + i, m0 + k) at (m0 + k) lda + r0 + i).
+template <class T, int NC, int SBK, int MODE>
 __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ SolveArgs a) {
   using S = SolveSmem<T, NC, SBK>;
   constexpr int V = S::V, YLD = S::YLD, DLD = S::DLD, MLD = S::MLD;
   constexpr int RPL = SBK / 32;         // rows per lane
   constexpr bool INV = sizeof(T) == 4;  // FP32: multiply by the inverted diagonal block
+  constexpr bool TRANS = MODE == 1;     // blocks of L read transposed
+  constexpr bool REV = MODE != 0;       // blocks solved from the last one up
   static_assert(SBK == 32 || (SBK == 64 && INV), "64-row items are for the FP32 sweeps");
+  static_assert(MODE != 2 || !INV, "the upper sweep is FP64");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *Yw = reinterpret_cast<T *>(smem_raw);
   T *Lt = Yw + S::YW;
@@ -137,16 +143,17 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
     if (item < 0 || item >= a.nitems) break;
     const int g = (int)(item % a.ngroups);
     const int ord = (int)(item / a.ngroups);
-    const int r = TRANS ? a.nrb - 1 - ord : ord;
+    const int r = REV ? a.nrb - 1 - ord : ord;
     const int r0 = r * SBK, rows = min(SBK, a.n - r0);
     const int c0 = g * SG, cols = min(SG, a.nrhs - c0);
     // the diagonal block and its reciprocals do not depend on other items: load them now,
     // off the chain of waits. Rows past the end of the matrix get an identity block, so the
     // substitution runs over a fixed SBK rows with register-resident data.
+    // (MODE 2 stores U^T, so that the backward substitution reads it as it reads L)
     for (int e = tid; e < SBK * SBK; e += SNT) {
       const int i = e % SBK, j = e / SBK;
-      Ld[i * DLD + j] = (i < rows && j < rows && i >= j) ? __ldcg(L + (int64_t)(r0 + j) * a.lda + r0 + i)
-                                                          : (i == j ? T(1) : T(0));
+      const int64_t at = MODE == 2 ? (int64_t)(r0 + i) * a.lda + r0 + j : (int64_t)(r0 + j) * a.lda + r0 + i;
+      Ld[i * DLD + j] = (i < rows && j < rows && i >= j) ? __ldcg(L + at) : (i == j ? T(1) : T(0));
     }
     if (tid < SBK) Rs[tid] = tid < rows ? T(1) / __ldcg(L + (int64_t)(r0 + tid) * a.lda + r0 + tid) : T(1);
     if constexpr (INV) {
@@ -182,7 +189,7 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
     for (int rr = 0; rr < RPL; ++rr)
 #pragma unroll
       for (int q = 0; q < NC; ++q) acc[rr][q] = T(0);
-    const int nsteps = TRANS ? a.nrb - 1 - r : r;
+    const int nsteps = REV ? a.nrb - 1 - r : r;
     // the solved blocks are consumed in 32-row chunks, one chunk per warp step: chunk kc of
     // block m is step m * RPL + kc, so the chunks of the newest block go to different warps
     const int nchunks = nsteps * RPL;
@@ -193,7 +200,7 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
     int mbase = warp;
     for (int step = warp; step < nchunks; step += SNW) {
       const int mi = step / RPL, kc = step % RPL;
-      const int m = TRANS ? a.nrb - 1 - mi : mi;
+      const int m = REV ? a.nrb - 1 - mi : mi;
       const int k0 = m * SBK + SB * kc, krows = min(SB, a.n - k0);  // this 32-row chunk of block m
       // L chunk, issued before any wait (it does not depend on other items). Forward: lane =
       // row of the item, lr[rr][k] = L(r0 + lane + 32 rr, k0 + k). Backward: lane = row k0 +
@@ -217,7 +224,7 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
         const int sl = step + SNW * lane;
         int f = 1;
         if (sl < nchunks) {
-          const int ml = TRANS ? a.nrb - 1 - sl / RPL : sl / RPL;
+          const int ml = REV ? a.nrb - 1 - sl / RPL : sl / RPL;
           f = ld_volatile(&a.flags[(int64_t)ml * a.ngroups + g]) != 0;
         }
         ready = __ballot_sync(0xffffffffu, f);
@@ -333,7 +340,7 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
       for (int i = 0; i < SBK; ++i) x[i] = Ys[i * YLD + c];
       // right-looking: once x_k is known every later row is updated at once, so each x_k
       // is one quotient and one multiply-add after x_{k-1}
-      if (!TRANS) {
+      if (!REV) {
 #pragma unroll
         for (int k = 0; k < SBK; ++k) {
           x[k] = squot(x[k], Ld[k * DLD + k], Rs[k]);
@@ -366,6 +373,9 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
 __global__ void solve_info_kernel(const SolveCtrl *c0, const SolveCtrl *c1, int *dInfo) {
   if (threadIdx.x == 0) *dInfo = c0->info ? c0->info : (c1 ? c1->info : 0);
 }
+__global__ void solve_info_merge_kernel(const SolveCtrl *c0, int *dInfo) {
+  if (threadIdx.x == 0 && *dInfo == 0) *dInfo = c0->info;
+}
 
 // workspace: two control blocks (one per sweep) and two flag arrays
 static size_t flags_bytes(int n, int nrhs) {
@@ -381,23 +391,29 @@ size_t solve_workspace_bytes(int n, int nrhs) { return solve_ws(n, nrhs); }
 template <class T>
 constexpr int item_rows() { return sizeof(T) == 4 ? 64 : 32; }
 
-template <class T, int NC>
-static cudaError_t launch_solve(const SolveArgs &a, int grid, cudaStream_t s) {
+template <class T, int NC, int MODE>
+static cudaError_t launch_solve_mode(const SolveArgs &a, int grid, cudaStream_t s) {
   // one block per SM: the dynamic shared memory request (more than half an SM's) makes a
   // second block impossible
   constexpr int SBK = item_rows<T>();
   constexpr size_t bytes = SolveSmem<T, NC, SBK>::BYTES;
-  const void *fn = a.trans ? (const void *)solve_kernel<T, NC, SBK, true> : (const void *)solve_kernel<T, NC, SBK, false>;
-  const cudaError_t e = set_smem_attr(fn, (int)bytes);
+  const cudaError_t e = set_smem_attr((const void *)solve_kernel<T, NC, SBK, MODE>, (int)bytes);
   if (e != cudaSuccess) return e;
-  if (a.trans) solve_kernel<T, NC, SBK, true><<<grid, SNT, bytes, s>>>(a);
-  else solve_kernel<T, NC, SBK, false><<<grid, SNT, bytes, s>>>(a);
+  solve_kernel<T, NC, SBK, MODE><<<grid, SNT, bytes, s>>>(a);
   return cudaGetLastError();
+}
+
+template <class T, int NC>
+static cudaError_t launch_solve(const SolveArgs &a, int grid, cudaStream_t s) {
+  if (a.trans == 0) return launch_solve_mode<T, NC, 0>(a, grid, s);
+  if (a.trans == 1) return launch_solve_mode<T, NC, 1>(a, grid, s);
+  if constexpr (sizeof(T) == 8) return launch_solve_mode<T, NC, 2>(a, grid, s);
+  return cudaErrorInvalidValue;
 }
 
 template <class T>
 static chol_status launch_sweep(int trans, int slot, int n, int nrhs, const T *dL, int lda, T *dB, int ldb,
-                                void *dWork, const int *skip, cudaStream_t s) {
+                                void *dWork, const int *skip, cudaStream_t s, const int *prev_abort = nullptr) {
   SolveArgs a;
   a.L = dL; a.lda = lda; a.B = dB; a.ldb = ldb; a.n = n; a.nrhs = nrhs;
   a.nrb = (n + item_rows<T>() - 1) / item_rows<T>();  // flags are sized for 32-row blocks: enough
@@ -408,7 +424,7 @@ static chol_status launch_sweep(int trans, int slot, int n, int nrhs, const T *d
   a.skip = skip;
   unsigned char *ws = static_cast<unsigned char *>(dWork);
   a.ctrl = reinterpret_cast<SolveCtrl *>(ws + 256 * slot);
-  a.prev_abort = slot == 1 ? &reinterpret_cast<SolveCtrl *>(ws)->abort : nullptr;
+  a.prev_abort = prev_abort ? prev_abort : slot == 1 ? &reinterpret_cast<SolveCtrl *>(ws)->abort : nullptr;
   a.flags = reinterpret_cast<int *>(ws + 512 + flags_bytes(n, nrhs) * slot);
   CHOL_CUDA_TRY(cudaMemsetAsync(a.ctrl, 0, 256, s));
   CHOL_CUDA_TRY(cudaMemsetAsync(a.flags, 0, flags_bytes(n, nrhs), s));
@@ -458,6 +474,22 @@ chol_status solve_f32(int n, int nrhs, const float *dL, int lda, float *dB, int 
   chol_status r = launch_sweep<float>(0, 0, n, nrhs, dL, lda, dB, ldb, dWork, skip, s);
   if (r != CHOL_OK) return r;
   return launch_sweep<float>(1, 1, n, nrhs, dL, lda, dB, ldb, dWork, skip, s);
+}
+
+// U X = B in place (one backward sweep, U read from the upper triangle of the tiles, as the
+// tile LU leaves it). The sweep's items are skipped once *prev_abort is set (nullable).
+chol_status solve_upper_f64(int n, int nrhs, const double *dU, int lda, double *dB, int ldb, void *dWork,
+                            const int *prev_abort, cudaStream_t s) {
+  if (n == 0 || nrhs == 0) return CHOL_OK;
+  return launch_sweep<double>(2, 0, n, nrhs, dU, lda, dB, ldb, dWork, nullptr, s, prev_abort);
+}
+
+// *dInfo = the upper sweep's info (0 or CHOL_INFO_TIMEOUT), unless it is already nonzero.
+chol_status solve_upper_info(void *dWork, int *dInfo, cudaStream_t s) {
+  unsigned char *ws = static_cast<unsigned char *>(dWork);
+  solve_info_merge_kernel<<<1, 32, 0, s>>>(reinterpret_cast<const SolveCtrl *>(ws), dInfo);
+  CHOL_CUDA_TRY(cudaGetLastError());
+  return CHOL_OK;
 }
 
 }  // namespace chol

@@ -274,10 +274,14 @@ def test_lu_argument_errors_before_any_launch():
     assert f(100, fake, 99, fake, fake, o, fake, 1 << 20, fake, None) == -1    # lda < n
     assert f(100, fake, 100, None, fake, o, fake, 1 << 20, fake, None) == -1   # no pivot array
     assert f(100, fake, 100, fake, fake, big, fake, 1 << 20, fake, None) == -1  # tile above 256
-    assert s(-1, 1, None, 1, None, None, o, None, 1, None) == -1
-    assert s(100, 1, fake, 100, fake, fake, o, fake, 99, None) == -1           # ldb < n
-    assert s(100, 1, fake, 100, fake, fake, big, fake, 100, None) == -1
-    assert s(100, 0, None, 100, None, None, o, None, 100, None) == 0            # nothing to solve
+    assert s(-1, 1, None, 1, None, None, o, None, 1, None, 0, None, None) == -1
+    assert s(100, 1, fake, 100, fake, fake, o, fake, 99, fake, 1 << 20, None, None) == -1   # ldb < n
+    assert s(100, 1, fake, 100, fake, fake, big, fake, 100, fake, 1 << 20, None, None) == -1
+    assert s(100, 0, None, 100, None, None, o, None, 100, None, 0, None, None) == 0        # nothing to solve
+    assert s(100, 1, fake, 100, fake, fake, o, fake, 100, None, 0, None, None) == -3      # no workspace
+    need = chol.lib.chol_lu_solve_workspace_size(100, 1, o)
+    assert need > 0 and chol.lib.chol_lu_solve_workspace_size(100, 1, big) == 0
+    assert s(100, 1, fake, 100, fake, fake, o, fake, 100, fake, need - 1, None, None) == -3  # too small
 
 
 def test_batch_descriptor_host_logic():

@@ -57,8 +57,10 @@ def test_noalloc_solve_matches_solve_on_two_calls(n, nrhs):
 
 def test_noalloc_rejects_problems_beyond_its_array():
     chol, f = _fn()
-    # ceil(n/32) * ceil(nrhs/32) above 32704 does not fit; rejected before any launch
-    st = f(32705 * 32, 1, None, 32705 * 32, None, 32705 * 32, None, None)
+    # ceil(n/32) * ceil(nrhs/32) above 32704 does not fit; rejected before any launch (the
+    # pointers pass the argument checks and are never dereferenced)
+    fake = ctypes.c_void_p(256)
+    st = f(32705 * 32, 1, fake, 32705 * 32, fake, 32705 * 32, None, None)
     assert st == -5
     st = f(-1, 1, None, 1, None, 1, None, None)
     assert st == -1
