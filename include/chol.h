@@ -82,9 +82,20 @@ typedef struct {
                              a task placed on a worker that did not write one of its input
                              tiles last pays that tile's bytes / cp_gbs (Section 4.1) */
   double cp_gbs;          /* bandwidth per worker for that prediction, GB/s; 0 = 40 */
+  int split;              /* FP64 factor: 0 = every task runs on one worker; 1 (default) = the
+                             TRSM and SYRK tasks of the next panel (tile row k + 1, the tasks on
+                             the critical path) are cut into 64-row / 64 x 64 units that idle
+                             workers take before their own queues; 2 = every TRSM and SYRK.
+                             The factor is bitwise the same in every mode */
+  int keep_next;          /* HEFT and DADA with priority queues: 1 (default) = a worker that
+                             completes a task runs the most urgent task it made ready next when
+                             that task outranks everything queued on it (it would be popped
+                             first there anyway); 0 = every ready task is placed and queued */
 } chol_opts;
 
 void chol_opts_default(chol_opts *opts);
+/* sizeof(chol_opts) as compiled into the library (for bindings that mirror the struct). */
+size_t chol_opts_size(void);
 
 /* ---------------------------------------------------------------------------------------
  * Factorization A = L L^T (Section 4.1: tile Cholesky DPOTRF; Section 2: data-flow

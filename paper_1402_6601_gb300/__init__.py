@@ -55,6 +55,8 @@ class ChOpts(ctypes.Structure):
         ("hold_task", ctypes.c_longlong),
         ("use_cp", ctypes.c_int),
         ("cp_gbs", ctypes.c_double),
+        ("split", ctypes.c_int),
+        ("keep_next", ctypes.c_int),
     ]
 
 
@@ -68,6 +70,7 @@ _OPTS = ctypes.POINTER(ChOpts)
 
 _SIGNATURES = {
     "chol_opts_default": (None, [_OPTS]),
+    "chol_opts_size": (_SZ, []),
     "chol_factor_workspace_size": (_SZ, [_I, _OPTS]),
     "chol_factor": (_I, [_I, _P, _I, _OPTS, _P, _SZ, _P, _P]),
     "chol_factor_trace_offset": (_LL, [_I, _OPTS]),
@@ -137,7 +140,7 @@ for _name in _SIGNATURES:
 
 def opts(nb=0, policy="heft", alpha=0.5, steal=None, workers_per_sm=2, num_workers=0,
          queue_order=None, dada_max_iter=16, dada_eps=0.01, cost_ns=None, timeout_ns=0, trace=False,
-         hold_task=-1, use_cp=False, cp_gbs=40.0):
+         hold_task=-1, use_cp=False, cp_gbs=40.0, split=1, keep_next=1):
     o = ChOpts()
     lib.chol_opts_default(ctypes.byref(o))
     o.nb = nb
@@ -157,6 +160,8 @@ def opts(nb=0, policy="heft", alpha=0.5, steal=None, workers_per_sm=2, num_worke
     o.hold_task = int(hold_task)
     o.use_cp = int(bool(use_cp))
     o.cp_gbs = float(cp_gbs)
+    o.split = int(split)
+    o.keep_next = int(keep_next)
     return o
 
 

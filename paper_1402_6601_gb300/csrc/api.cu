@@ -123,7 +123,11 @@ extern "C" void chol_opts_default(chol_opts *o) {
   o->hold_task = -1;
   o->use_cp = 0;
   o->cp_gbs = 40.0;
+  o->split = 1;
+  o->keep_next = 1;
 }
+
+extern "C" size_t chol_opts_size(void) { return sizeof(chol_opts); }
 
 extern "C" long long chol_dag_task_count(int T) {
   if (T < 1 || T > 1024) return -1;

@@ -45,7 +45,20 @@ struct Ctrl {
   int spills;
   int queued;    // tasks in all queues
   int free_sms;  // SMs that host a worker and run no task
-  int pad[57];
+  int help_open; // split tasks with units not yet claimed
+  int pad[56];
+};
+
+// A task cut into units that idle workers help with (one slot per worker, written by the
+// worker that runs the task). `word` holds the slot's generation (bits 40..63), the number
+// of units (bits 32..39) and the next unit to hand out (bits 0..31): the owner takes units
+// with an atomic add, a helper with a compare-and-swap that also checks the generation, so a
+// helper holding an old view of the slot can never take a unit of a later task.
+struct __align__(128) HelpSlot {
+  unsigned long long word;
+  int done;  // units finished
+  int kind, i, j, k;
+  int pad[26];
 };
 
 struct FactorArgs {
@@ -75,6 +88,9 @@ struct FactorArgs {
   int64_t split_tile;    // bytes per panel tile in `split`
   int *lu_piv;           // LU: pivots of GETRF(k) / TSTRF(i, k) at ((k T + i) nb), nb per tile
   double *lu_lw;         // LU: L11 blocks of TSTRF(i, k) at ((k T + i) LU_IB nb)
+  HelpSlot *board;       // one help slot per worker
+  int split_mode;        // 0 off, 1 the next panel's TRSM and SYRK, 2 every TRSM and SYRK
+  int keep_next;         // the finishing worker runs the most urgent task it made ready
 };
 
 struct Resolved {
@@ -85,10 +101,13 @@ struct Resolved {
   int64_t hold_task;
   int use_cp;
   int64_t comm_ns;
+  int split;
+  int keep_next;
 };
 
 struct Layout {
-  size_t ctrl, trace, zero_begin, qhead, qcount, qcost, run_end, sm_busy, slots, zero_end, cnt, owner, bl, split, total;
+  size_t ctrl, trace, zero_begin, qhead, qcount, qcost, run_end, sm_busy, board, slots, zero_end, cnt, owner, bl,
+      split, total;
   size_t split_tile;
   int C;
   int64_t ntasks;
@@ -123,6 +142,7 @@ static Layout make_layout(int n, const Resolved &r, int W) {
   L.qcost = o; o += align_up((size_t)W * 8, 256);
   L.run_end = o; o += align_up((size_t)W * 8, 256);
   L.sm_busy = o; o += align_up((size_t)2 * SM_SLOTS * 4, 256);
+  L.board = o; o += align_up((size_t)W * sizeof(HelpSlot), 256);
   L.slots = o; o += align_up((size_t)W * L.C * 8, 256);
   L.zero_end = o;
   L.cnt = o; o += align_up((size_t)L.ntasks * 4, 256);
@@ -238,9 +258,59 @@ __device__ __forceinline__ void raise_abort(const FactorArgs &a, int info) {
   atomicExch(&a.ctrl->abort, 1);
 }
 
+constexpr int64_t HELP_ID = -3;  // acquire's answer when the worker is to run a unit of a split task
+
+__device__ __forceinline__ unsigned long long help_word(unsigned long long gen, int units, int next) {
+  return (gen << 40) | ((unsigned long long)units << 32) | (unsigned long long)(unsigned)next;
+}
+
+// Take the next unit of slot h, whose word was last seen as w; -1 if none is left or the slot
+// has moved on to another task (generation changed).
+__device__ int help_claim(HelpSlot *h, unsigned long long w) {
+  const unsigned long long gen = w >> 40;
+  while (true) {
+    if ((w >> 40) != gen) return -1;
+    const int units = (int)((w >> 32) & 0xffull), next = (int)(w & 0xffffffffull);
+    if (next >= units) return -1;
+    const unsigned long long old = atomicCAS(&h->word, w, w + 1ull);
+    if (old == w) return next;
+    w = old;
+  }
+}
+
+// One warp scans the help board for a split task with units left and takes one.
+__device__ bool help_scan(const FactorArgs &a, int &slot, int &unit) {
+  const int lane = threadIdx.x & 31;
+  for (int q0 = 0; q0 < a.W; q0 += 32) {
+    const int q = q0 + lane;
+    unsigned long long w = 0;
+    bool open = false;
+    if (q < a.W) {
+      w = ld_volatile(&a.board[q].word);
+      open = (w >> 40) != 0 && (int)((w >> 32) & 0xffull) > (int)(w & 0xffffffffull);
+    }
+    unsigned m = __ballot_sync(0xffffffffu, open);
+    while (m) {
+      const int src = __ffs(m) - 1;
+      int got = -1;
+      if (lane == src) got = help_claim(&a.board[q], w);
+      got = __shfl_sync(0xffffffffu, got, src);
+      if (got >= 0) {
+        slot = q0 + src;
+        unit = got;
+        return true;
+      }
+      m &= m - 1;
+    }
+  }
+  return false;
+}
+
 // Get the next task for worker wid (warp 0). Returns -1 when all tasks are done or the run
-// was aborted. `from` receives the queue the task came from.
-__device__ int64_t acquire(const FactorArgs &a, int wid, int smid, uint32_t &rng, int &from) {
+// was aborted, HELP_ID when the worker is to run unit `hunit` of the task in help slot
+// `hslot`. `from` receives the queue the task came from.
+__device__ int64_t acquire(const FactorArgs &a, int wid, int smid, uint32_t &rng, int &from, int &hslot,
+                           int &hunit) {
   const int lane = threadIdx.x & 31;
   int last_done = -1;
   uint64_t t_last = 0;
@@ -258,6 +328,13 @@ __device__ int64_t acquire(const FactorArgs &a, int wid, int smid, uint32_t &rng
     done_ = __shfl_sync(0xffffffffu, done_, 0);
     now = __shfl_sync(0xffffffffu, now, 0);
     if (abort_ || done_ >= a.ntasks) return -1;
+    // units of split tasks come first: those tasks are on the critical path
+    if (a.split_mode) {
+      int open = 0;
+      if (lane == 0) open = ld_volatile(&a.ctrl->help_open);
+      open = __shfl_sync(0xffffffffu, open, 0);
+      if (open > 0 && help_scan(a, hslot, hunit)) return HELP_ID;
+    }
     // while the SM's other worker runs a task, take one only if the queued work exceeds what
     // the SMs with no running task can start: two tasks on one SM each run at about half
     // speed, which lengthens the critical path when work is scarce
@@ -289,10 +366,36 @@ __device__ int64_t acquire(const FactorArgs &a, int wid, int smid, uint32_t &rng
   }
 }
 
-// Activate the successors of a finished task and place the ready ones (warp 0).
+// Largest entry in queue q (0 if it is empty); all lanes of one warp.
+__device__ unsigned long long queue_top(const FactorArgs &a, int q) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long *s = a.slots + (size_t)q * a.C;
+  unsigned long long best = 0ull;
+  for (int i0 = 0; i0 < a.C; i0 += 128) {
+    unsigned long long v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + 32 * u + lane;
+      v[u] = i < a.C ? ld_volatile(&s[i]) : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) best = v[u] > best ? v[u] : best;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long ov = __shfl_xor_sync(0xffffffffu, best, o);
+    best = ov > best ? ov : best;
+  }
+  return best;
+}
+
+// Activate the successors of a finished task and place the ready ones (warp 0). With
+// keep_next, the most urgent of the newly ready tasks is not placed when it outranks every
+// task queued on this worker: the worker, free at this moment, runs it next (*s_next, else
+// -1). Under HEFT's own rule this worker is then the earliest-finishing one for that task,
+// since a queue is served in priority order and the task would be taken from it first.
 template <class G>
 __device__ void complete(const FactorArgs &a, int wid, const TaskDesc &d, unsigned char *smem_raw,
-                         int *s_nready) {
+                         int *s_nready, long long *s_next) {
   const int lane = threadIdx.x & 31;
   const int T = a.T;
   ReadyTask *LR = reinterpret_cast<ReadyTask *>(smem_raw);
@@ -314,6 +417,7 @@ __device__ void complete(const FactorArgs &a, int wid, const TaskDesc &d, unsign
     *(volatile int *)&a.owner[ti * T + tj] = wid;
     *(volatile unsigned long long *)&a.run_end[wid] = 0ull;
     *s_nready = 0;
+    *s_next = -1;
   }
   __syncwarp();
   const int ns = G::nsucc(T, d);
@@ -326,7 +430,33 @@ __device__ void complete(const FactorArgs &a, int wid, const TaskDesc &d, unsign
   }
   __syncwarp();
   __threadfence();
-  const int m = *(volatile int *)s_nready;
+  int m = *(volatile int *)s_nready;
+  if (m > 0 && a.keep_next) {
+    // the most urgent ready task: highest bottom level, then lowest id (warp argmax)
+    int bi = -1;
+    int64_t bp = 0;
+    int bt = 0;
+    for (int i = lane; i < m; i += 32) {
+      const int t = LR[i].tid;
+      const int64_t p = a.bl[t];
+      if (bi < 0 || p > bp || (p == bp && t < bt)) { bi = i; bp = p; bt = t; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      const int64_t op = __shfl_xor_sync(0xffffffffu, bp, o);
+      const int ot = __shfl_xor_sync(0xffffffffu, bt, o);
+      if (oi >= 0 && (bi < 0 || op > bp || (op == bp && ot < bt))) { bi = oi; bp = op; bt = ot; }
+    }
+    const unsigned long long top = queue_top(a, wid);
+    if (make_entry(prio_key(bp), bt) > top) {
+      if (lane == 0) {
+        *s_next = bt;
+        LR[bi].tid = LR[m - 1].tid;  // the rest are placed as usual
+      }
+      __syncwarp();
+      m -= 1;
+    }
+  }
   if (m > 0) {
     for (int i = lane; i < m; i += 32) {
       const TaskDesc sd = G::desc(T, LR[i].tid);
@@ -401,6 +531,7 @@ __device__ void complete(const FactorArgs &a, int wid, const TaskDesc &d, unsign
 struct TilesF64 {
   using T = double;
   using Graph = CholGraph;
+  static constexpr bool CAN_SPLIT = true;  // TRSM and SYRK tasks can be cut into units
   static constexpr int SMEM = TILE_SMEM_BYTES;
   static constexpr int MIN_BLOCKS = 2;  // two workers per SM share the FP64 pipe
   __device__ static int potrf(T *G, int64_t ld, int nk, T *s) { return potrf_tile(G, ld, nk, s); }
@@ -418,6 +549,7 @@ struct TilesF64 {
 struct TilesF32 {
   using T = float;
   using Graph = CholGraph;
+  static constexpr bool CAN_SPLIT = false;
   static constexpr int SMEM = f32::PANEL_SMEM_BYTES > f32::TILE_SMEM_BYTES ? f32::PANEL_SMEM_BYTES
                                                                             : f32::TILE_SMEM_BYTES;
   static constexpr int MIN_BLOCKS = 1;  // the 8x8 register tiles need more than 128 registers
@@ -492,6 +624,7 @@ __device__ __forceinline__ unsigned char *split_ptr(const FactorArgs &a, int i, 
 struct LuF64 {
   using T = double;
   using Graph = LuGraph;
+  static constexpr bool CAN_SPLIT = false;
   static constexpr int SMEM = LU_SMEM_BYTES;
   static constexpr int MIN_BLOCKS = 2;
   __device__ static void begin() {}
@@ -501,12 +634,111 @@ struct LuF64 {
 // Run one tile task with the whole block. Returns 0 or a 1-based failing global column.
 template <class P>
 struct Runner {
-  __device__ static int run(const FactorArgs &a, const TaskDesc &d, typename P::T *smem);
+  __device__ static int run(const FactorArgs &a, const TaskDesc &d, typename P::T *smem, int wid);
+  __device__ static void unit(const FactorArgs &a, const TaskDesc &d, int u, typename P::T *smem);
 };
 
+// Split tasks (FP64 bodies): a TRSM is cut into bands of 64 rows of the panel tile (the rows
+// of X L^T = B are independent), a SYRK into the 64 x 64 blocks of the lower triangle of its
+// diagonal tile. Every element is computed by the same operations in the same order as in
+// the whole-task bodies, so the factor is bitwise the same with and without splitting.
+constexpr int SPLIT_ROWS = 64;
+
+__device__ __forceinline__ int split_units(const FactorArgs &a, const TaskDesc &d) {
+  const int nbk = (tile_dim(a, d.i) + SPLIT_ROWS - 1) / SPLIT_ROWS;
+  return d.kind == K_TRSM ? nbk : nbk * (nbk + 1) / 2;
+}
+
+__device__ __forceinline__ bool should_split(const FactorArgs &a, const TaskDesc &d) {
+  if (!a.split_mode || (d.kind != K_TRSM && d.kind != K_SYRK)) return false;
+  if (tile_dim(a, d.i) <= SPLIT_ROWS) return false;
+  return a.split_mode == 2 || d.i == d.k + 1;
+}
+
 template <class P>
-__device__ int Runner<P>::run(const FactorArgs &a, const TaskDesc &d, typename P::T *smem) {
+__device__ __noinline__ void Runner<P>::unit(const FactorArgs &a, const TaskDesc &d, int u, typename P::T *smem) {
+  if constexpr (P::CAN_SPLIT) {
+    using T = typename P::T;
+    const int mi = tile_dim(a, d.i), nk = tile_dim(a, d.k);
+    if (d.kind == K_TRSM) {
+      const int r0 = SPLIT_ROWS * u;
+      P::trsm(tile_ptr<T>(a, d.i, d.k) + r0, a.lda, tile_ptr<T>(a, d.k, d.k), a.lda, min(SPLIT_ROWS, mi - r0), nk,
+              smem, nullptr);
+    } else {
+      int bm = (int)((sqrtf(8.f * (float)u + 1.f) - 1.f) * 0.5f);
+      while (bm * (bm + 1) / 2 > u) --bm;
+      while ((bm + 1) * (bm + 2) / 2 <= u) ++bm;
+      const int bn = u - bm * (bm + 1) / 2;
+      const int r0 = SPLIT_ROWS * bm, c0 = SPLIT_ROWS * bn;
+      const T *A = tile_ptr<T>(a, d.i, d.k);
+      P::update(tile_ptr<T>(a, d.i, d.i) + (int64_t)c0 * a.lda + r0, a.lda, A + r0, a.lda, A + c0, a.lda,
+                min(SPLIT_ROWS, mi - r0), min(SPLIT_ROWS, mi - c0), nk, bm == bn, smem, nullptr, nullptr);
+    }
+  }
+}
+
+// Run task d as units: publish it on this worker's help slot, take units until none is
+// left, then wait (bounded) for the units other workers took. Returns 0 or CHOL_INFO_TIMEOUT.
+template <class P>
+__device__ __noinline__ int run_split(const FactorArgs &a, const TaskDesc &d, typename P::T *smem, int wid) {
+  __shared__ int s_unit;
+  HelpSlot *h = a.board + wid;
+  const int units = split_units(a, d);
+  if (threadIdx.x == 0) {
+    const unsigned long long gen = (ld_volatile(&h->word) >> 40) + 1ull;
+    h->kind = d.kind;
+    h->i = d.i;
+    h->j = d.j;
+    h->k = d.k;
+    h->done = 0;
+    __threadfence();
+    atomicExch(&h->word, help_word(gen, units, 0));
+    atomicAdd(&a.ctrl->help_open, 1);
+  }
+  while (true) {
+    if (threadIdx.x == 0) {
+      const unsigned long long old = atomicAdd(&h->word, 1ull);
+      const int next = (int)(old & 0xffffffffull);
+      s_unit = next < units ? next : -1;
+    }
+    __syncthreads();
+    const int u = s_unit;
+    __syncthreads();
+    if (u < 0) break;
+    Runner<P>::unit(a, d, u, smem);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(&h->done, 1);
+  }
+  if (threadIdx.x == 0) {
+    atomicSub(&a.ctrl->help_open, 1);
+    // the units other workers took: they run tile bodies only, with no waits
+    int fail = 0;
+    const uint64_t t0 = globaltimer_ns();
+    int64_t spins = 0;
+    unsigned slp = 32;
+    while (ld_volatile(&h->done) < units) {
+      if (ld_volatile(&a.ctrl->abort)) break;
+      if (globaltimer_ns() - t0 > (uint64_t)a.timeout_ns || ++spins > a.iter_limit) {
+        fail = CHOL_INFO_TIMEOUT;
+        break;
+      }
+      __nanosleep(slp);
+      slp = slp < 256 ? slp * 2 : 256;
+    }
+    __threadfence();
+    s_unit = fail;
+  }
+  __syncthreads();
+  return s_unit;
+}
+
+template <class P>
+__device__ int Runner<P>::run(const FactorArgs &a, const TaskDesc &d, typename P::T *smem, int wid) {
   using T = typename P::T;
+  if constexpr (P::CAN_SPLIT) {
+    if (should_split(a, d)) return run_split<P>(a, d, smem, wid);
+  }
   switch (d.kind) {
     case K_POTRF: {
       const int f = P::potrf(tile_ptr<T>(a, d.k, d.k), a.lda, tile_dim(a, d.k), smem);
@@ -539,7 +771,7 @@ __device__ __forceinline__ double *lu_lw_ptr(const FactorArgs &a, int i, int k) 
 }
 
 template <>
-__device__ int Runner<LuF64>::run(const FactorArgs &a, const TaskDesc &d, double *smem) {
+__device__ int Runner<LuF64>::run(const FactorArgs &a, const TaskDesc &d, double *smem, int) {
   const int64_t ld = a.lda;
   switch (d.kind) {
     case K_GETRF: {
@@ -571,6 +803,8 @@ __global__ void __launch_bounds__(NT, P::MIN_BLOCKS) factor_kernel(const __grid_
   __shared__ long long s_id;
   __shared__ int s_from;
   __shared__ int s_nready;
+  __shared__ int s_hslot, s_hunit;
+  __shared__ long long s_next;
   const int wid = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t rng = 0x9E3779B9u ^ ((uint32_t)wid * 0x85EBCA6Bu + 1u);
@@ -588,28 +822,52 @@ __global__ void __launch_bounds__(NT, P::MIN_BLOCKS) factor_kernel(const __grid_
     atomicAdd(&a.qcost[0], (unsigned long long)a.cost[G::KIND0]);
     if (push_task(a, 0, make_entry(key, 0)) < 0) raise_abort(a, CHOL_INFO_QUEUE_FULL);
   }
+  if (threadIdx.x == 0) s_next = -1;
+  __syncthreads();
   while (true) {
     if (warp == 0) {
-      int from = -1;
-      const int64_t id = acquire(a, wid, smid, rng, from);
+      int from = -1, hs = -1, hu = -1;
+      const long long kept = s_next;  // a task this worker made ready and keeps (not queued)
+      int64_t id;
+      if (kept >= 0) {
+        id = ld_volatile(&a.ctrl->abort) ? -1 : kept;
+        from = wid;
+      } else {
+        id = acquire(a, wid, smid, rng, from, hs, hu);
+      }
       if (id >= 0 && lane == 0 && smid >= 0 && atomicAdd(&a.sm_busy[smid], 1) == 0)
         atomicSub(&a.ctrl->free_sms, 1);
       if (id >= 0 && lane == 0) {
         const TaskDesc d = G::desc(a.T, id);
         const int64_t c = a.cost[d.kind];
-        atomicAdd(&a.qcost[from], (unsigned long long)(-c));
+        if (kept < 0) atomicAdd(&a.qcost[from], (unsigned long long)(-c));
         *(volatile unsigned long long *)&a.run_end[wid] = globaltimer_ns() + (uint64_t)c;
       }
-      if (lane == 0) { s_id = id; s_from = from; }
+      if (lane == 0) { s_id = id; s_from = from; s_hslot = hs; s_hunit = hu; }
     }
     __syncthreads();
     const int64_t id = s_id;
+    if (id == HELP_ID) {
+      // one unit of another worker's split task
+      __threadfence();
+      const HelpSlot *h = a.board + s_hslot;
+      TaskDesc hd;
+      hd.kind = ld_volatile(&h->kind);
+      hd.i = ld_volatile(&h->i);
+      hd.j = ld_volatile(&h->j);
+      hd.k = ld_volatile(&h->k);
+      Runner<P>::unit(a, hd, s_hunit, smem);
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) atomicAdd(&a.board[s_hslot].done, 1);
+      continue;
+    }
     if (id < 0) break;
     __threadfence();
     const TaskDesc d = G::desc(a.T, id);
     unsigned long long t0 = 0;
     if (a.trace && threadIdx.x == 0) t0 = globaltimer_ns();
-    const int fail = Runner<P>::run(a, d, smem);
+    const int fail = Runner<P>::run(a, d, smem, wid);
     __threadfence();
     __syncthreads();
     if (warp == 0) {
@@ -618,9 +876,12 @@ __global__ void __launch_bounds__(NT, P::MIN_BLOCKS) factor_kernel(const __grid_
       unsigned long long t1 = 0;
       if (a.trace && lane == 0) t1 = globaltimer_ns();
       if (fail) {
-        if (lane == 0) raise_abort(a, fail);
+        if (lane == 0) {
+          raise_abort(a, fail);
+          s_next = -1;
+        }
       } else {
-        complete<G>(a, wid, d, smem_raw, &s_nready);
+        complete<G>(a, wid, d, smem_raw, &s_nready, &s_next);
       }
       if (lane == 0 && smid >= 0 && atomicSub(&a.sm_busy[smid], 1) == 1) atomicAdd(&a.ctrl->free_sms, 1);
       if (a.trace && lane == 0) {
@@ -787,6 +1048,9 @@ static bool resolve(int n, const chol_opts *opts, Resolved &r, int prec = PREC_F
     r.comm_ns = std::max<int64_t>(1, (int64_t)(tile_bytes / gbs));
   }
   if (r.hold_task >= (r.lu ? LuGraph::count(r.T) : CholGraph::count(r.T))) return false;
+  if (o.split < 0 || o.split > 2) return false;
+  r.keep_next = o.keep_next ? 1 : 0;
+  r.split = prec == PREC_F64 ? o.split : 0;  // the FP64 bodies can be cut into units
   return true;
 }
 
@@ -899,6 +1163,9 @@ chol_status factor_impl(int prec, int n, void *dA, int lda, const chol_opts *opt
   a.split_tile = (int64_t)L.split_tile;
   a.lu_piv = lu_piv;
   a.lu_lw = lu_lw;
+  a.board = reinterpret_cast<HelpSlot *>(ws + L.board);
+  a.split_mode = r.split;
+  a.keep_next = r.keep_next && r.queue_order == 0 && (r.policy == P_HEFT || r.policy == P_DADA);
 
   CHOL_CUDA_TRY(cudaMemsetAsync(ws + L.ctrl, 0, sizeof(Ctrl), s));
   CHOL_CUDA_TRY(cudaMemsetAsync(ws + L.zero_begin, 0, L.zero_end - L.zero_begin, s));

@@ -163,6 +163,15 @@ __global__ void __launch_bounds__(NT, 1) lu_fwd_kernel(const __grid_constant__ L
       const int c = e / mi, r = e - c * mi;
       Yi[c * LU_NB_MAX + r] = __ldcg(a.B + (int64_t)(c0g + c) * ldb + (int64_t)i * nb + r);
     }
+    // rows of Y_k past the tile, up to the last inner block's end, are read (times a zero
+    // multiplier) by the eliminations below: they must hold finite values
+    {
+      const int pad = nblk * LU_IB - nk;
+      for (int e = tid; e < pad * gc; e += NT) {
+        const int c = e / pad, r = e - c * pad;
+        Yk[c * LU_NB_MAX + nk + r] = 0.0;
+      }
+    }
     __syncthreads();
     for (int b = 0; b < nblk; ++b) {
       const int c0 = b * LU_IB, w = min(LU_IB, nk - c0), c1 = c0 + w;

@@ -38,7 +38,8 @@ def test_opts_struct_layout_matches_header():
     assert o.nb == 0 and o.policy == 0 and o.alpha == 0.5 and o.steal == 1
     assert o.dada_max_iter == 16 and abs(o.dada_eps - 0.01) < 1e-15
     assert o.timeout_ns == 10_000_000_000 and o.trace == 0
-    assert ctypes.sizeof(chol.ChOpts) == 120 and o.hold_task == -1 and o.use_cp == 0 and o.cp_gbs == 40.0
+    assert ctypes.sizeof(chol.ChOpts) == chol.lib.chol_opts_size() == 128
+    assert o.hold_task == -1 and o.use_cp == 0 and o.cp_gbs == 40.0 and o.split == 1 and o.keep_next == 1
 
 
 @pytest.mark.parametrize("T", [1, 2, 3, 5, 8, 11])

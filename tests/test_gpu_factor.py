@@ -90,6 +90,35 @@ def test_schedule_invariance_bitwise(chol):
             np.testing.assert_array_equal(np.tril(F), ref)
 
 
+@pytest.mark.parametrize("nb", [256, 512])
+def test_split_units_and_kept_successors_bitwise(chol, nb):
+    # TRSM/SYRK tasks cut into 64-row / 64 x 64 units that other workers help with, and the
+    # finishing worker keeping the most urgent successor, change who computes what, not how:
+    # every element is computed by the same operations in the same order
+    n = 1100
+    A = synth.gram_spd(n, seed=23).numpy()
+    ref = None
+    for split in (0, 1, 2):
+        for keep in (0, 1):
+            for nw in (0, 1, 3):
+                o = chol.opts(nb=nb, split=split, keep_next=keep, num_workers=nw)
+                F, info, _ = _factor(chol, A, o)
+                assert info == 0
+                if ref is None:
+                    ref = np.tril(F)
+                    assert oracle.rel_frobenius(ref, oracle.factor(A)) <= REL_L
+                else:
+                    np.testing.assert_array_equal(np.tril(F), ref, err_msg=str((split, keep, nw)))
+
+
+@pytest.mark.parametrize("policy", ["heft", "dada", "steal"])
+def test_integer_factor_bitwise_split_every_task(chol, policy):
+    L, A = synth.integer_factor(700, seed=6)
+    F, info, _ = _factor(chol, A, chol.opts(nb=256, policy=policy, split=2))
+    assert info == 0
+    np.testing.assert_array_equal(np.tril(F), L)
+
+
 @pytest.mark.parametrize("bad", [1, 200, 511, 512, 700])
 def test_not_spd_info(chol, bad):
     n = 768
