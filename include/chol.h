@@ -84,9 +84,11 @@ typedef struct {
   double cp_gbs;          /* bandwidth per worker for that prediction, GB/s; 0 = 40 */
   int split;              /* FP64 factor: 0 = every task runs on one worker; 1 (default) = the
                              TRSM and SYRK tasks of the next panel (tile row k + 1, the tasks on
-                             the critical path) are cut into 64-row / 64 x 64 units that idle
-                             workers take before their own queues; 2 = every TRSM and SYRK.
-                             The factor is bitwise the same in every mode */
+                             the critical path), and any TRSM, SYRK or GEMM that starts while
+                             SMs idle with no queued task for them, are cut into 64-row (TRSM)
+                             or 64 x 64 (SYRK, GEMM) units that idle workers take before their
+                             own queues; 2 = every TRSM, SYRK and GEMM. The factor is bitwise
+                             the same in every mode */
   int keep_next;          /* HEFT and DADA with priority queues: 1 (default) = a worker that
                              completes a task runs the most urgent task it made ready next when
                              that task outranks everything queued on it (it would be popped

@@ -394,7 +394,7 @@ __device__ unsigned long long queue_top(const FactorArgs &a, int q) {
 // -1). Under HEFT's own rule this worker is then the earliest-finishing one for that task,
 // since a queue is served in priority order and the task would be taken from it first.
 template <class G>
-__device__ void complete(const FactorArgs &a, int wid, const TaskDesc &d, unsigned char *smem_raw,
+__device__ void complete(const FactorArgs &a, int wid, int smid, const TaskDesc &d, unsigned char *smem_raw,
                          int *s_nready, long long *s_next) {
   const int lane = threadIdx.x & 31;
   const int T = a.T;
@@ -431,7 +431,16 @@ __device__ void complete(const FactorArgs &a, int wid, const TaskDesc &d, unsign
   __syncwarp();
   __threadfence();
   int m = *(volatile int *)s_nready;
-  if (m > 0 && a.keep_next) {
+  // keep a task only on an SM that runs nothing else (this worker's own task still counts in
+  // sm_busy): next to a running task it would run at half speed, and the co-scheduling rule
+  // would not have let this worker take it
+  bool alone = true;
+  if (a.keep_next && m > 0 && smid >= 0) {
+    int b = 0;
+    if (lane == 0) b = ld_volatile(&a.sm_busy[smid]);
+    alone = __shfl_sync(0xffffffffu, b, 0) <= 1;
+  }
+  if (m > 0 && a.keep_next && alone) {
     // the most urgent ready task: highest bottom level, then lowest id (warp argmax)
     int bi = -1;
     int64_t bp = 0;
@@ -634,25 +643,33 @@ struct LuF64 {
 // Run one tile task with the whole block. Returns 0 or a 1-based failing global column.
 template <class P>
 struct Runner {
-  __device__ static int run(const FactorArgs &a, const TaskDesc &d, typename P::T *smem, int wid);
+  __device__ static int run(const FactorArgs &a, const TaskDesc &d, typename P::T *smem, int wid, bool starving);
   __device__ static void unit(const FactorArgs &a, const TaskDesc &d, int u, typename P::T *smem);
 };
 
 // Split tasks (FP64 bodies): a TRSM is cut into bands of 64 rows of the panel tile (the rows
 // of X L^T = B are independent), a SYRK into the 64 x 64 blocks of the lower triangle of its
-// diagonal tile. Every element is computed by the same operations in the same order as in
-// the whole-task bodies, so the factor is bitwise the same with and without splitting.
+// diagonal tile, a GEMM into the 64 x 64 blocks of its tile. Every element is computed by the
+// same operations in the same order as in the whole-task bodies, so the factor is bitwise the
+// same with and without splitting.
 constexpr int SPLIT_ROWS = 64;
 
 __device__ __forceinline__ int split_units(const FactorArgs &a, const TaskDesc &d) {
-  const int nbk = (tile_dim(a, d.i) + SPLIT_ROWS - 1) / SPLIT_ROWS;
-  return d.kind == K_TRSM ? nbk : nbk * (nbk + 1) / 2;
+  const int nbi = (tile_dim(a, d.i) + SPLIT_ROWS - 1) / SPLIT_ROWS;
+  if (d.kind == K_TRSM) return nbi;
+  if (d.kind == K_SYRK) return nbi * (nbi + 1) / 2;
+  return nbi * ((tile_dim(a, d.j) + SPLIT_ROWS - 1) / SPLIT_ROWS);
 }
 
-__device__ __forceinline__ bool should_split(const FactorArgs &a, const TaskDesc &d) {
-  if (!a.split_mode || (d.kind != K_TRSM && d.kind != K_SYRK)) return false;
-  if (tile_dim(a, d.i) <= SPLIT_ROWS) return false;
-  return a.split_mode == 2 || d.i == d.k + 1;
+// Mode 1: the next panel's TRSM and SYRK (tile row k + 1, on the critical path), and any
+// TRSM, SYRK or GEMM that starts while SMs run no task and no queued task is left for them
+// (`starving`: the end of the factor, or small matrices). Mode 2: every TRSM, SYRK and GEMM.
+__device__ __forceinline__ bool should_split(const FactorArgs &a, const TaskDesc &d, bool starving) {
+  if (!a.split_mode || d.kind == K_POTRF) return false;
+  if (tile_dim(a, d.i) <= SPLIT_ROWS || split_units(a, d) > 255) return false;
+  if (a.split_mode == 2) return true;
+  if ((d.kind == K_TRSM || d.kind == K_SYRK) && d.i == d.k + 1) return true;
+  return starving;
 }
 
 template <class P>
@@ -664,6 +681,12 @@ __device__ __noinline__ void Runner<P>::unit(const FactorArgs &a, const TaskDesc
       const int r0 = SPLIT_ROWS * u;
       P::trsm(tile_ptr<T>(a, d.i, d.k) + r0, a.lda, tile_ptr<T>(a, d.k, d.k), a.lda, min(SPLIT_ROWS, mi - r0), nk,
               smem, nullptr);
+    } else if (d.kind == K_GEMM) {
+      const int mj = tile_dim(a, d.j), nbj = (mj + SPLIT_ROWS - 1) / SPLIT_ROWS;
+      const int r0 = SPLIT_ROWS * (u / nbj), c0 = SPLIT_ROWS * (u % nbj);
+      P::update(tile_ptr<T>(a, d.i, d.j) + (int64_t)c0 * a.lda + r0, a.lda, tile_ptr<T>(a, d.i, d.k) + r0, a.lda,
+                tile_ptr<T>(a, d.j, d.k) + c0, a.lda, min(SPLIT_ROWS, mi - r0), min(SPLIT_ROWS, mj - c0), nk, false,
+                smem, nullptr, nullptr);
     } else {
       int bm = (int)((sqrtf(8.f * (float)u + 1.f) - 1.f) * 0.5f);
       while (bm * (bm + 1) / 2 > u) --bm;
@@ -734,10 +757,11 @@ __device__ __noinline__ int run_split(const FactorArgs &a, const TaskDesc &d, ty
 }
 
 template <class P>
-__device__ int Runner<P>::run(const FactorArgs &a, const TaskDesc &d, typename P::T *smem, int wid) {
+__device__ int Runner<P>::run(const FactorArgs &a, const TaskDesc &d, typename P::T *smem, int wid,
+                              bool starving) {
   using T = typename P::T;
   if constexpr (P::CAN_SPLIT) {
-    if (should_split(a, d)) return run_split<P>(a, d, smem, wid);
+    if (should_split(a, d, starving)) return run_split<P>(a, d, smem, wid);
   }
   switch (d.kind) {
     case K_POTRF: {
@@ -771,7 +795,7 @@ __device__ __forceinline__ double *lu_lw_ptr(const FactorArgs &a, int i, int k) 
 }
 
 template <>
-__device__ int Runner<LuF64>::run(const FactorArgs &a, const TaskDesc &d, double *smem, int) {
+__device__ int Runner<LuF64>::run(const FactorArgs &a, const TaskDesc &d, double *smem, int, bool) {
   const int64_t ld = a.lda;
   switch (d.kind) {
     case K_GETRF: {
@@ -805,6 +829,7 @@ __global__ void __launch_bounds__(NT, P::MIN_BLOCKS) factor_kernel(const __grid_
   __shared__ int s_nready;
   __shared__ int s_hslot, s_hunit;
   __shared__ long long s_next;
+  __shared__ int s_starving;
   const int wid = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t rng = 0x9E3779B9u ^ ((uint32_t)wid * 0x85EBCA6Bu + 1u);
@@ -843,7 +868,13 @@ __global__ void __launch_bounds__(NT, P::MIN_BLOCKS) factor_kernel(const __grid_
         if (kept < 0) atomicAdd(&a.qcost[from], (unsigned long long)(-c));
         *(volatile unsigned long long *)&a.run_end[wid] = globaltimer_ns() + (uint64_t)c;
       }
-      if (lane == 0) { s_id = id; s_from = from; s_hslot = hs; s_hunit = hu; }
+      if (lane == 0) {
+        s_id = id;
+        s_from = from;
+        s_hslot = hs;
+        s_hunit = hu;
+        s_starving = a.split_mode && id >= 0 && ld_volatile(&a.ctrl->free_sms) > ld_volatile(&a.ctrl->queued);
+      }
     }
     __syncthreads();
     const int64_t id = s_id;
@@ -867,7 +898,7 @@ __global__ void __launch_bounds__(NT, P::MIN_BLOCKS) factor_kernel(const __grid_
     const TaskDesc d = G::desc(a.T, id);
     unsigned long long t0 = 0;
     if (a.trace && threadIdx.x == 0) t0 = globaltimer_ns();
-    const int fail = Runner<P>::run(a, d, smem, wid);
+    const int fail = Runner<P>::run(a, d, smem, wid, s_starving != 0);
     __threadfence();
     __syncthreads();
     if (warp == 0) {
@@ -881,7 +912,7 @@ __global__ void __launch_bounds__(NT, P::MIN_BLOCKS) factor_kernel(const __grid_
           s_next = -1;
         }
       } else {
-        complete<G>(a, wid, d, smem_raw, &s_nready, &s_next);
+        complete<G>(a, wid, smid, d, smem_raw, &s_nready, &s_next);
       }
       if (lane == 0 && smid >= 0 && atomicSub(&a.sm_busy[smid], 1) == 1) atomicAdd(&a.ctrl->free_sms, 1);
       if (a.trace && lane == 0) {

@@ -12,9 +12,11 @@
 // (i, k - 1) (the last transformation that touched Y_i); (k, k) needs (k, k - 1). Its longest
 // path has about 2T nodes against T(T + 1)/2 in all, so lu_fwd_kernel runs it as a wavefront:
 // thread blocks (one per SM) claim (node, group of right-hand sides) items from an atomic
-// counter in column-major node order, where every dependency comes earlier, wait on the
-// ready flags of the two predecessors (bounded), apply the node's inner blocks to the staged
-// rows and publish a flag. Everything that does not depend on Y -- the pivots, the L11
+// counter with the nodes ordered by anti-diagonal s = i + k (then by k), wait on the ready
+// flags of the two predecessors (both on diagonal s - 1, so claimed earlier; bounded waits),
+// apply the node's inner blocks to the staged rows and publish a flag. Claiming along the
+// diagonals keeps the in-flight items on the front of the wavefront; in column order the
+// blocks would hold a few tile columns at a time and every later column would start late. Everything that does not depend on Y -- the pivots, the L11
 // blocks, the first inner block's L21 rows -- is loaded before the wait. The back
 // substitution is the backward sweep of the Cholesky solve with U (solve_upper_f64).
 #include <algorithm>
@@ -54,19 +56,28 @@ struct LuFwdArgs {
   int64_t timeout_ns;
 };
 
-// nodes of the columns before k: sum over k' < k of (T - k')
-__host__ __device__ __forceinline__ int64_t lu_col_offset(int T, int k) {
-  return (int64_t)k * T - (int64_t)k * (k - 1) / 2;
+// Nodes (i, k), 0 <= k <= i < T, ordered by s = i + k, then by k. lu_diag_offset(T, s) is the
+// number of nodes with i + k < s: sum over s' < s of (floor(s'/2) + 1 - max(0, s' - T + 1)).
+__host__ __device__ __forceinline__ int64_t lu_diag_offset(int T, int s) {
+  const int64_t h = s / 2;
+  const int64_t a = (int64_t)s + (s % 2 == 0 ? h * (h - 1) : h * h);
+  const int64_t e = s > T ? (int64_t)(s - T) * (s - T + 1) / 2 : 0;
+  return a - e;
+}
+__device__ __forceinline__ int64_t lu_node_index(int T, int i, int k) {
+  const int s = i + k;
+  return lu_diag_offset(T, s) + (k - max(0, s - T + 1));
 }
 __device__ __forceinline__ void lu_node_decode(int T, int64_t node, int &i, int &k) {
-  // largest k with lu_col_offset(T, k) <= node, from the quadratic, then corrected
-  const double b = 2.0 * T + 1.0;
-  int kk = (int)floor((b - sqrt(fmax(b * b - 8.0 * (double)node, 0.0))) * 0.5);
-  kk = max(0, min(T - 1, kk));
-  while (kk > 0 && lu_col_offset(T, kk) > node) --kk;
-  while (kk + 1 < T && lu_col_offset(T, kk + 1) <= node) ++kk;
-  k = kk;
-  i = k + (int)(node - lu_col_offset(T, k));
+  // largest s with lu_diag_offset(T, s) <= node (binary search over 0 .. 2T - 2)
+  int lo = 0, hi = 2 * T - 2;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (lu_diag_offset(T, mid) <= node) lo = mid; else hi = mid - 1;
+  }
+  const int s = lo;
+  k = max(0, s - T + 1) + (int)(node - lu_diag_offset(T, s));
+  i = s - k;
 }
 
 // Wait (thread 0) until flag f is set; returns false if the run aborted or the wait expired.
@@ -144,11 +155,8 @@ __global__ void __launch_bounds__(NT, 1) lu_fwd_kernel(const __grid_constant__ L
     // --- wait for the predecessors: (i - 1, k) and (i, k - 1)
     if (tid == 0) {
       bool ok = true;
-      if (!getrf) ok = lu_wait_flag(a, &a.flags[(node - 1) * a.ngroups + g]);
-      if (ok && k > 0) {
-        const int64_t pred = lu_col_offset(T, k - 1) + (i - (k - 1));
-        ok = lu_wait_flag(a, &a.flags[pred * a.ngroups + g]);
-      }
+      if (!getrf) ok = lu_wait_flag(a, &a.flags[lu_node_index(T, i - 1, k) * a.ngroups + g]);
+      if (ok && k > 0) ok = lu_wait_flag(a, &a.flags[lu_node_index(T, i, k - 1) * a.ngroups + g]);
       s_ok = ok;
     }
     __syncthreads();

@@ -53,6 +53,7 @@ CHOL_HD int64_t cost_on(const ReadyTask &t, int w, bool cp) {
 }
 
 struct HostExec {
+  static constexpr bool WARP = false;
   CHOL_HD static bool leader() { return true; }
   CHOL_HD static void sync() {}
   CHOL_HD static int lane() { return 0; }
@@ -78,6 +79,7 @@ struct HostExec {
 
 #ifdef __CUDACC__
 struct WarpExec {
+  static constexpr bool WARP = true;
   __device__ static bool leader() { return (threadIdx.x & 31) == 0; }
   __device__ static void sync() { __syncwarp(); }
   __device__ static int lane() { return threadIdx.x & 31; }
@@ -141,6 +143,11 @@ CHOL_HD bool before_lpt(const ReadyTask &a, const ReadyTask &b) {
   return before_prio(a, b);
 }
 
+template <int KEY>
+CHOL_HD bool before_key(const ReadyTask &a, const ReadyTask &b) {
+  return KEY == 0 ? before_prio(a, b) : KEY == 1 ? before_aff(a, b) : before_lpt(a, b);
+}
+
 // Insertion sort of indices; m is at most T - 1 and this runs once per activation.
 template <int KEY>
 CHOL_HD void sort_indices(int *ord, const ReadyTask *LR, int m) {
@@ -157,6 +164,25 @@ CHOL_HD void sort_indices(int *ord, const ReadyTask *LR, int m) {
       --j;
     }
     ord[j + 1] = v;
+  }
+}
+
+// The same order from the whole warp (device): every lane ranks its tasks against all the
+// others -- the comparisons are a strict total order (ties end at the task id), so the ranks
+// are a permutation, the one the insertion sort produces. O(m^2 / 32) comparisons per lane
+// with broadcast reads instead of O(m^2) on one lane: this sort sits on every activation,
+// so on the factor's critical path.
+template <int KEY, class X>
+CHOL_HD void sort_ready(int *ord, const ReadyTask *LR, int m) {
+  if constexpr (X::WARP) {
+    for (int i = X::lane(); i < m; i += X::width()) {
+      const ReadyTask t = LR[i];
+      int r = 0;
+      for (int j = 0; j < m; ++j) r += before_key<KEY>(LR[j], t) ? 1 : 0;
+      ord[r] = i;
+    }
+  } else {
+    sort_indices<KEY>(ord, LR, m);
   }
 }
 
@@ -224,7 +250,7 @@ template <class X>
 CHOL_HD int place(int policy, double alpha, int max_iter, double eps, const ReadyTask *LR, int m,
                   int64_t *load, int W, PlaceScratch &s, bool cp = false) {
   if (m <= 0) return 0;
-  if (X::leader()) sort_indices<0>(s.ord_prio, LR, m);
+  sort_ready<0, X>(s.ord_prio, LR, m);
   X::sync();
   int iters = 0;
   if (policy == P_HEFT) {
@@ -241,10 +267,8 @@ CHOL_HD int place(int policy, double alpha, int max_iter, double eps, const Read
     return 0;
   }
   // DADA
-  if (X::leader()) {
-    sort_indices<1>(s.ord_aff, LR, m);
-    sort_indices<2>(s.ord_lpt, LR, m);
-  }
+  sort_ready<1, X>(s.ord_aff, LR, m);
+  sort_ready<2, X>(s.ord_lpt, LR, m);
   X::sync();
   int64_t lower = 0;
   int64_t upper = X::sum_p(LR, m, cp) + X::maxval(load, W);
