@@ -540,17 +540,29 @@ __device__ void complete(const FactorArgs &a, int wid, int smid, const TaskDesc 
 struct TilesF64 {
   using T = double;
   using Graph = CholGraph;
-  static constexpr bool CAN_SPLIT = true;  // TRSM and SYRK tasks can be cut into units
+  static constexpr bool CAN_SPLIT = true;  // TRSM, SYRK and GEMM tasks can be cut into units
+  static constexpr int UPD_UNIT = 64;       // SYRK / GEMM units: the update's 64 x 64 blocks
+  static constexpr bool SPLIT_SYRK = true, SPLIT_GEMM = true;
   static constexpr int SMEM = TILE_SMEM_BYTES;
   static constexpr int MIN_BLOCKS = 2;  // two workers per SM share the FP64 pipe
   __device__ static int potrf(T *G, int64_t ld, int nk, T *s) { return potrf_tile(G, ld, nk, s); }
   __device__ static void trsm(T *B, int64_t ldb, const T *L, int64_t ldl, int mb, int nk, T *s, unsigned char *) {
     trsm_tile(B, ldb, L, ldl, mb, nk, s);
   }
+  // rows [r0, r0 + rows) of the panel tile B (a unit of a split TRSM)
+  __device__ static void trsm_rows(T *B, int64_t ldb, const T *L, int64_t ldl, int r0, int rows, int nk, T *s,
+                                   unsigned char *) {
+    trsm_tile(B + r0, ldb, L, ldl, rows, nk, s);
+  }
   __device__ static int update(T *C, int64_t ldc, const T *A, int64_t lda, const T *B, int64_t ldb, int M,
                                int N, int K, bool lower, T *s, const unsigned char *, const unsigned char *) {
     update_nt(C, ldc, A, lda, B, ldb, M, N, K, lower, s);
     return 0;
+  }
+  // one block of a split SYRK, with the body the whole SYRK runs on
+  __device__ static void syrk_part(T *C, int64_t ldc, const T *A, int64_t lda, const T *B, int64_t ldb, int M,
+                                   int N, int K, bool lower, T *s) {
+    update_nt(C, ldc, A, lda, B, ldb, M, N, K, lower, s);
   }
   __device__ static void begin() {}
   __device__ static void end() {}
@@ -558,7 +570,9 @@ struct TilesF64 {
 struct TilesF32 {
   using T = float;
   using Graph = CholGraph;
-  static constexpr bool CAN_SPLIT = false;
+  static constexpr bool CAN_SPLIT = true;
+  static constexpr int UPD_UNIT = 128;      // the FFMA update's 128 x 128 blocks
+  static constexpr bool SPLIT_SYRK = true, SPLIT_GEMM = true;
   static constexpr int SMEM = f32::PANEL_SMEM_BYTES > f32::TILE_SMEM_BYTES ? f32::PANEL_SMEM_BYTES
                                                                             : f32::TILE_SMEM_BYTES;
   static constexpr int MIN_BLOCKS = 1;  // the 8x8 register tiles need more than 128 registers
@@ -570,10 +584,20 @@ struct TilesF32 {
     if (nk <= f32::PANEL_MAX_N) f32::trsm_tile_rows(B, ldb, L, ldl, mb, nk, s);
     else f32::trsm_tile(B, ldb, L, ldl, mb, nk, s);
   }
+  __device__ static void trsm_rows(T *B, int64_t ldb, const T *L, int64_t ldl, int r0, int rows, int nk, T *s,
+                                   unsigned char *) {
+    trsm(B + r0, ldb, L, ldl, rows, nk, s, nullptr);
+  }
   __device__ static int update(T *C, int64_t ldc, const T *A, int64_t lda, const T *B, int64_t ldb, int M,
                                int N, int K, bool lower, T *s, const unsigned char *, const unsigned char *) {
     f32::update_nt(C, ldc, A, lda, B, ldb, M, N, K, lower, s);
     return 0;
+  }
+  // one block of a split SYRK: FFMA, also in the three-term tensor-core form (whose SYRKs run
+  // on this body)
+  __device__ static void syrk_part(T *C, int64_t ldc, const T *A, int64_t lda, const T *B, int64_t ldb, int M,
+                                   int N, int K, bool lower, T *s) {
+    f32::update_nt(C, ldc, A, lda, B, ldb, M, N, K, lower, s);
   }
   __device__ static void begin() {}
   __device__ static void end() {}
@@ -583,6 +607,9 @@ struct TilesF32 {
 // worker for the whole launch.
 template <int NTERM>
 struct TilesTC : TilesF32 {
+  // split units: TRSM bands, and the SYRKs that run on the FFMA body (three-term form); the
+  // tensor-core updates are one MMA tile each
+  static constexpr bool SPLIT_SYRK = NTERM > 1, SPLIT_GEMM = false;
   static constexpr int SMEM = tc::Cfg<NTERM>::SMEM > TilesF32::SMEM ? tc::Cfg<NTERM>::SMEM : TilesF32::SMEM;
   static constexpr int EMIT_OFF = (f32::TRSM_ROWS_SMEM_BYTES + 127) / 128 * 128;
   static_assert(EMIT_OFF + 2 * tc::Split<NTERM>::CHUNK <= SMEM, "TRSM split buffers must fit");
@@ -602,6 +629,14 @@ struct TilesTC : TilesF32 {
                           tc::SplitEmit<NTERM>{split, reinterpret_cast<unsigned char *>(s) + EMIT_OFF});
     else
       TilesF32::trsm(B, ldb, L, ldl, mb, nk, s, nullptr);
+  }
+  __device__ static void trsm_rows(T *B, int64_t ldb, const T *L, int64_t ldl, int r0, int rows, int nk, T *s,
+                                   unsigned char *split) {
+    if (split && nk <= f32::PANEL_MAX_N)
+      f32::trsm_tile_rows(B + r0, ldb, L, ldl, rows, nk, s,
+                          tc::SplitEmitRows<NTERM>{split, reinterpret_cast<unsigned char *>(s) + EMIT_OFF, r0});
+    else
+      TilesF32::trsm(B + r0, ldb, L, ldl, rows, nk, s, nullptr);
   }
   // SYRK updates (C -= A A^T on a diagonal tile, rows of A that lie close together in the
   // matrix) add products that mostly share one sign, and the errors of the tensor cores' FP32
@@ -633,7 +668,9 @@ __device__ __forceinline__ unsigned char *split_ptr(const FactorArgs &a, int i, 
 struct LuF64 {
   using T = double;
   using Graph = LuGraph;
-  static constexpr bool CAN_SPLIT = false;
+  static constexpr bool CAN_SPLIT = false;  // (the LU graph has its own runner)
+  static constexpr int UPD_UNIT = 64;
+  static constexpr bool SPLIT_SYRK = false, SPLIT_GEMM = false;
   static constexpr int SMEM = LU_SMEM_BYTES;
   static constexpr int MIN_BLOCKS = 2;
   __device__ static void begin() {}
@@ -652,21 +689,24 @@ struct Runner {
 // diagonal tile, a GEMM into the 64 x 64 blocks of its tile. Every element is computed by the
 // same operations in the same order as in the whole-task bodies, so the factor is bitwise the
 // same with and without splitting.
-constexpr int SPLIT_ROWS = 64;
+constexpr int SPLIT_ROWS = 64;  // rows of a TRSM unit (FP32 updates use 128 x 128 units)
 
+template <class P>
 __device__ __forceinline__ int split_units(const FactorArgs &a, const TaskDesc &d) {
-  const int nbi = (tile_dim(a, d.i) + SPLIT_ROWS - 1) / SPLIT_ROWS;
-  if (d.kind == K_TRSM) return nbi;
+  if (d.kind == K_TRSM) return (tile_dim(a, d.i) + SPLIT_ROWS - 1) / SPLIT_ROWS;
+  const int nbi = (tile_dim(a, d.i) + P::UPD_UNIT - 1) / P::UPD_UNIT;
   if (d.kind == K_SYRK) return nbi * (nbi + 1) / 2;
-  return nbi * ((tile_dim(a, d.j) + SPLIT_ROWS - 1) / SPLIT_ROWS);
+  return nbi * ((tile_dim(a, d.j) + P::UPD_UNIT - 1) / P::UPD_UNIT);
 }
 
 // Mode 1: the next panel's TRSM and SYRK (tile row k + 1, on the critical path), and any
 // TRSM, SYRK or GEMM that starts while SMs run no task and no queued task is left for them
 // (`starving`: the end of the factor, or small matrices). Mode 2: every TRSM, SYRK and GEMM.
+template <class P>
 __device__ __forceinline__ bool should_split(const FactorArgs &a, const TaskDesc &d, bool starving) {
   if (!a.split_mode || d.kind == K_POTRF) return false;
-  if (tile_dim(a, d.i) <= SPLIT_ROWS || split_units(a, d) > 255) return false;
+  if ((d.kind == K_SYRK && !P::SPLIT_SYRK) || (d.kind == K_GEMM && !P::SPLIT_GEMM)) return false;
+  if (split_units<P>(a, d) < 2 || split_units<P>(a, d) > 255) return false;
   if (a.split_mode == 2) return true;
   if ((d.kind == K_TRSM || d.kind == K_SYRK) && d.i == d.k + 1) return true;
   return starving;
@@ -677,25 +717,26 @@ __device__ __noinline__ void Runner<P>::unit(const FactorArgs &a, const TaskDesc
   if constexpr (P::CAN_SPLIT) {
     using T = typename P::T;
     const int mi = tile_dim(a, d.i), nk = tile_dim(a, d.k);
+    constexpr int U = P::UPD_UNIT;
     if (d.kind == K_TRSM) {
       const int r0 = SPLIT_ROWS * u;
-      P::trsm(tile_ptr<T>(a, d.i, d.k) + r0, a.lda, tile_ptr<T>(a, d.k, d.k), a.lda, min(SPLIT_ROWS, mi - r0), nk,
-              smem, nullptr);
+      P::trsm_rows(tile_ptr<T>(a, d.i, d.k), a.lda, tile_ptr<T>(a, d.k, d.k), a.lda, r0, min(SPLIT_ROWS, mi - r0),
+                   nk, smem, split_ptr(a, d.i, d.k));
     } else if (d.kind == K_GEMM) {
-      const int mj = tile_dim(a, d.j), nbj = (mj + SPLIT_ROWS - 1) / SPLIT_ROWS;
-      const int r0 = SPLIT_ROWS * (u / nbj), c0 = SPLIT_ROWS * (u % nbj);
+      const int mj = tile_dim(a, d.j), nbj = (mj + U - 1) / U;
+      const int r0 = U * (u / nbj), c0 = U * (u % nbj);
       P::update(tile_ptr<T>(a, d.i, d.j) + (int64_t)c0 * a.lda + r0, a.lda, tile_ptr<T>(a, d.i, d.k) + r0, a.lda,
-                tile_ptr<T>(a, d.j, d.k) + c0, a.lda, min(SPLIT_ROWS, mi - r0), min(SPLIT_ROWS, mj - c0), nk, false,
-                smem, nullptr, nullptr);
+                tile_ptr<T>(a, d.j, d.k) + c0, a.lda, min(U, mi - r0), min(U, mj - c0), nk, false, smem, nullptr,
+                nullptr);
     } else {
       int bm = (int)((sqrtf(8.f * (float)u + 1.f) - 1.f) * 0.5f);
       while (bm * (bm + 1) / 2 > u) --bm;
       while ((bm + 1) * (bm + 2) / 2 <= u) ++bm;
       const int bn = u - bm * (bm + 1) / 2;
-      const int r0 = SPLIT_ROWS * bm, c0 = SPLIT_ROWS * bn;
+      const int r0 = U * bm, c0 = U * bn;
       const T *A = tile_ptr<T>(a, d.i, d.k);
-      P::update(tile_ptr<T>(a, d.i, d.i) + (int64_t)c0 * a.lda + r0, a.lda, A + r0, a.lda, A + c0, a.lda,
-                min(SPLIT_ROWS, mi - r0), min(SPLIT_ROWS, mi - c0), nk, bm == bn, smem, nullptr, nullptr);
+      P::syrk_part(tile_ptr<T>(a, d.i, d.i) + (int64_t)c0 * a.lda + r0, a.lda, A + r0, a.lda, A + c0, a.lda,
+                   min(U, mi - r0), min(U, mi - c0), nk, bm == bn, smem);
     }
   }
 }
@@ -706,7 +747,7 @@ template <class P>
 __device__ __noinline__ int run_split(const FactorArgs &a, const TaskDesc &d, typename P::T *smem, int wid) {
   __shared__ int s_unit;
   HelpSlot *h = a.board + wid;
-  const int units = split_units(a, d);
+  const int units = split_units<P>(a, d);
   if (threadIdx.x == 0) {
     const unsigned long long gen = (ld_volatile(&h->word) >> 40) + 1ull;
     h->kind = d.kind;
@@ -761,7 +802,7 @@ __device__ int Runner<P>::run(const FactorArgs &a, const TaskDesc &d, typename P
                               bool starving) {
   using T = typename P::T;
   if constexpr (P::CAN_SPLIT) {
-    if (should_split(a, d, starving)) return run_split<P>(a, d, smem, wid);
+    if (should_split<P>(a, d, starving)) return run_split<P>(a, d, smem, wid);
   }
   switch (d.kind) {
     case K_POTRF: {
@@ -1081,7 +1122,7 @@ static bool resolve(int n, const chol_opts *opts, Resolved &r, int prec = PREC_F
   if (r.hold_task >= (r.lu ? LuGraph::count(r.T) : CholGraph::count(r.T))) return false;
   if (o.split < 0 || o.split > 2) return false;
   r.keep_next = o.keep_next ? 1 : 0;
-  r.split = prec == PREC_F64 ? o.split : 0;  // the FP64 bodies can be cut into units
+  r.split = r.lu ? 0 : o.split;  // the Cholesky tile bodies can be cut into units
   return true;
 }
 

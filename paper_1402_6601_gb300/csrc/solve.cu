@@ -332,6 +332,33 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
 #pragma unroll
         for (int u = 0; u < RPT; ++u) Xo[(i0 + u) * YLD + q] = t[u];
       }
+    } else if (cols <= SNW) {
+      // diagonal block, few right-hand sides: one warp per right-hand side, lane = row. Each
+      // step takes x_k on lane k and updates the rows below it with one warp-wide FMA (an FP64
+      // instruction costs the SM sub-partition's FP64 pipe the same time with one active lane
+      // as with 32, so a single thread would pay for 32 lanes on every one of its 496 FMAs).
+      // Every x_i sees the same operations in the same order as in the thread-per-column form.
+      const int c = warp;
+      if (c < cols) {
+        T x = Ys[lane * YLD + c];
+        const T lrow_inv = Rs[lane];
+        if (!REV) {
+#pragma unroll
+          for (int k = 0; k < SBK; ++k) {
+            if (lane == k) x = squot(x, Ld[k * DLD + k], lrow_inv);
+            const T xk = __shfl_sync(0xffffffffu, x, k);
+            if (lane > k) x = fma(-Ld[lane * DLD + k], xk, x);
+          }
+        } else {
+#pragma unroll
+          for (int k = SBK - 1; k >= 0; --k) {
+            if (lane == k) x = squot(x, Ld[k * DLD + k], lrow_inv);
+            const T xk = __shfl_sync(0xffffffffu, x, k);
+            if (lane < k) x = fma(-Ld[k * DLD + lane], xk, x);
+          }
+        }
+        Ys[lane * YLD + c] = x;
+      }
     } else if (tid < cols) {
       // diagonal block: one thread per right-hand side runs the substitution
       const int c = tid;

@@ -405,6 +405,51 @@ struct SplitEmit {
   }
 };
 
+// The same for a band of 64 rows [r0, r0 + 64) of the panel tile (a unit of a split TRSM):
+// rows are stored at their place in a band-sized part of the stage buffers, and since the 64
+// rows of one term form one contiguous 4 KiB range of a chunk (8-row groups of 512 bytes),
+// each flush copies NTERM ranges. Rows of the band past the tile are zero.
+template <int NTERM>
+struct SplitEmitRows {
+  static constexpr int ROWS = 64;
+  static constexpr int BAND = ROWS / 8 * 512;  // bytes of one term of the band
+  unsigned char *tile;  // global: the tile's chunks
+  unsigned char *buf;   // shared: 2 x CHUNK bytes, 16-byte aligned
+  int r0;               // first row of the band (a multiple of 64)
+  __device__ void row(int r, int c, const float (&v)[32]) const {
+    if (r < ROWS) store_row<NTERM>(buf + (c & 1) * Split<NTERM>::CHUNK, v, r);
+  }
+  __device__ void zero(int r, int c) const {
+    if (r >= ROWS) return;
+    float z[32];
+#pragma unroll
+    for (int e = 0; e < 32; ++e) z[e] = 0.f;
+    store_row<NTERM>(buf + (c & 1) * Split<NTERM>::CHUNK, z, r);
+  }
+  __device__ void flush(int c) const {
+    fence_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int t = 0; t < NTERM; ++t) {
+        const size_t go = (size_t)c * Split<NTERM>::CHUNK + (size_t)t * Cfg<NTERM>::OPB + (size_t)(r0 / 8) * 512;
+        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(tile + go),
+                     "r"(smem_u32(buf + (c & 1) * Split<NTERM>::CHUNK + t * Cfg<NTERM>::OPB)), "r"((uint32_t)BAND)
+                     : "memory");
+      }
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+    }
+    __syncthreads();
+  }
+  __device__ void finish() const {
+    if (threadIdx.x == 0) {
+      asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
+    __syncthreads();
+  }
+};
+
 // C[M x N] -= A B^T with both operands pre-split (sa, sb: their tiles in the side buffer), K a
 // multiple of 32, M, N <= 256. Same accumulators and epilogue as update_nt. Returns 0, or -1
 // when a wait expired.

@@ -231,3 +231,27 @@ def test_refine_overflowing_fp32_norm_reports_nan(chol):
     assert np.isnan(float(berr.item()))
     assert int(iters.item()) == 0
     assert not X.abs().max().item()
+
+
+@pytest.mark.parametrize("precision", ["f32", "bf16x3", "bf16"])
+def test_lowp_factor_split_and_kept_bitwise(chol, precision):
+    # split TRSM bands (with their BF16 terms written band by band), split FFMA SYRK / GEMM
+    # blocks and kept successors change who computes what, not how
+    n = 1100  # ragged last tile
+    A = synth.gram_spd(n, seed=31).numpy()
+    ref = None
+    for split in (0, 1, 2):
+        for keep in (0, 1):
+            for nw in (0, 3):
+                Ad = _f32(chol, A)
+                info, _ = chol.factor_f32(Ad, chol.opts(nb=256, split=split, keep_next=keep, num_workers=nw),
+                                          precision=precision)
+                torch.cuda.synchronize()
+                assert int(info.item()) == 0
+                L = np.tril(Ad.cpu().numpy())
+                if ref is None:
+                    ref = L
+                    tol = 16 * 2.0 ** -9 if precision == "bf16" else 2e-5  # as in the parity tests above
+                    assert oracle.rel_frobenius(L.astype(np.float64), oracle.factor(A)) <= tol
+                else:
+                    np.testing.assert_array_equal(L, ref, err_msg=str((split, keep, nw)))
