@@ -157,6 +157,12 @@ chol_status chol_solve(int n, int nrhs, const double *dL, int lda, double *dB, i
 chol_status chol_solve_noalloc(int n, int nrhs, const double *dL, int lda, double *dB, int ldb,
                                int *dInfo, void *stream);
 
+/* chol_solve with an FP32 factor (from chol_factor_f32 / chol_factor_lowp) and FP32
+ * right-hand sides: the substitutions the mixed-precision refinement runs for each
+ * correction (64-row blocks, inverted diagonal blocks). Workspace chol_solve_workspace_size. */
+chol_status chol_solve_f32(int n, int nrhs, const float *dL, int lda, float *dB, int ldb, void *dWork,
+                           size_t work_bytes, int *dInfo, void *stream);
+
 /* One sweep only: uplo_t = 0 solves L Y = B, uplo_t = 1 solves L^T X = B, in place on dB. */
 chol_status chol_trsm_sweep(int uplo_t, int n, int nrhs, const double *dL, int lda, double *dB,
                             int ldb, void *dWork, size_t work_bytes, int *dInfo, void *stream);

@@ -77,6 +77,7 @@ _SIGNATURES = {
     "chol_solve_workspace_size": (_SZ, [_I, _I]),
     "chol_solve": (_I, [_I, _I, _P, _I, _P, _I, _P, _SZ, _P, _P]),
     "chol_trsm_sweep": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _SZ, _P, _P]),
+    "chol_solve_f32": (_I, [_I, _I, _P, _I, _P, _I, _P, _SZ, _P, _P]),
     "chol_solve_noalloc": (_I, [_I, _I, _P, _I, _P, _I, _P, _P]),
     "chol_factor_f32": (_I, [_I, _P, _I, _OPTS, _P, _SZ, _P, _P]),
     "chol_factor_lowp": (_I, [_I, _I, _P, _I, _OPTS, _P, _SZ, _P, _P]),
@@ -186,9 +187,9 @@ def colmajor(x):
     return y
 
 
-def _check_matrix(A, name):
-    if not (A.is_cuda and A.dtype == torch.float64 and A.dim() == 2):
-        raise ValueError("%s must be a 2-D float64 CUDA tensor" % name)
+def _check_matrix(A, name, dtype=torch.float64):
+    if not (A.is_cuda and A.dtype == dtype and A.dim() == 2):
+        raise ValueError("%s must be a 2-D %s CUDA tensor" % (name, str(dtype).replace("torch.", "")))
     if A.shape[0] > 0 and A.shape[1] > 0 and A.stride(0) != 1:
         raise ValueError("%s must be column-major (stride(0) == 1); use colmajor()" % name)
     return max(1, A.stride(1) if A.shape[1] > 1 else A.shape[0])
@@ -311,6 +312,20 @@ def solve(L, B, work=None, info=None, stream=None):
     st = lib.chol_solve(n, nrhs, L.data_ptr(), lda, B.data_ptr(), ldb, work.data_ptr(), work.numel(),
                         info.data_ptr() if info is not None else None, _stream(stream))
     _check(st, "chol_solve")
+    return B
+
+
+def solve_f32(L, B, work=None, info=None, stream=None):
+    """X = (L L^T)^{-1} B in place on the column-major float32 CUDA matrix B, with an FP32 factor."""
+    n = L.shape[0]
+    lda = _check_matrix(L, "L", torch.float32)
+    ldb = _check_matrix(B, "B", torch.float32)
+    nrhs = B.shape[1]
+    if work is None:
+        work = _workspace(solve_workspace_size(n, nrhs), L.device)
+    st = lib.chol_solve_f32(n, nrhs, L.data_ptr(), lda, B.data_ptr(), ldb, work.data_ptr(), work.numel(),
+                            info.data_ptr() if info is not None else None, _stream(stream))
+    _check(st, "chol_solve_f32")
     return B
 
 

@@ -542,7 +542,7 @@ struct TilesF64 {
   using Graph = CholGraph;
   static constexpr bool CAN_SPLIT = true;  // TRSM, SYRK and GEMM tasks can be cut into units
   static constexpr int UPD_UNIT = 64;       // SYRK / GEMM units: the update's 64 x 64 blocks
-  static constexpr bool SPLIT_SYRK = true, SPLIT_GEMM = true;
+  static constexpr bool SPLIT_TRSM = true, SPLIT_SYRK = true, SPLIT_GEMM = true;
   static constexpr int SMEM = TILE_SMEM_BYTES;
   static constexpr int MIN_BLOCKS = 2;  // two workers per SM share the FP64 pipe
   __device__ static int potrf(T *G, int64_t ld, int nk, T *s) { return potrf_tile(G, ld, nk, s); }
@@ -572,7 +572,10 @@ struct TilesF32 {
   using Graph = CholGraph;
   static constexpr bool CAN_SPLIT = true;
   static constexpr int UPD_UNIT = 128;      // the FFMA update's 128 x 128 blocks
-  static constexpr bool SPLIT_SYRK = true, SPLIT_GEMM = true;
+  static constexpr bool SPLIT_TRSM = true, SPLIT_SYRK = true, SPLIT_GEMM = true;
+  static_assert(f32::TRSM_BAND_SMEM_BYTES <= (f32::PANEL_SMEM_BYTES > f32::TILE_SMEM_BYTES ? f32::PANEL_SMEM_BYTES
+                                                                                         : f32::TILE_SMEM_BYTES),
+                "the band TRSM must fit the FP32 bodies' shared memory");
   static constexpr int SMEM = f32::PANEL_SMEM_BYTES > f32::TILE_SMEM_BYTES ? f32::PANEL_SMEM_BYTES
                                                                             : f32::TILE_SMEM_BYTES;
   static constexpr int MIN_BLOCKS = 1;  // the 8x8 register tiles need more than 128 registers
@@ -580,13 +583,19 @@ struct TilesF32 {
   __device__ static int potrf(T *G, int64_t ld, int nk, T *s) {
     return nk <= f32::PANEL_MAX_N ? f32::potrf_tile_smem(G, ld, nk, s) : f32::potrf_tile(G, ld, nk, s);
   }
+  // bands of 64 rows (f32::trsm_band); a split TRSM hands the bands to helpers
   __device__ static void trsm(T *B, int64_t ldb, const T *L, int64_t ldl, int mb, int nk, T *s, unsigned char *) {
-    if (nk <= f32::PANEL_MAX_N) f32::trsm_tile_rows(B, ldb, L, ldl, mb, nk, s);
-    else f32::trsm_tile(B, ldb, L, ldl, mb, nk, s);
+    if (nk <= f32::PANEL_MAX_N) {
+      for (int r0 = 0; r0 < mb; r0 += f32::BAND_ROWS)
+        f32::trsm_band(B + r0, ldb, L, ldl, min(f32::BAND_ROWS, mb - r0), nk, s);
+    } else {
+      f32::trsm_tile(B, ldb, L, ldl, mb, nk, s);
+    }
   }
   __device__ static void trsm_rows(T *B, int64_t ldb, const T *L, int64_t ldl, int r0, int rows, int nk, T *s,
                                    unsigned char *) {
-    trsm(B + r0, ldb, L, ldl, rows, nk, s, nullptr);
+    if (nk <= f32::PANEL_MAX_N) f32::trsm_band(B + r0, ldb, L, ldl, rows, nk, s);
+    else f32::trsm_tile(B + r0, ldb, L, ldl, rows, nk, s);
   }
   __device__ static int update(T *C, int64_t ldc, const T *A, int64_t lda, const T *B, int64_t ldb, int M,
                                int N, int K, bool lower, T *s, const unsigned char *, const unsigned char *) {
@@ -609,10 +618,10 @@ template <int NTERM>
 struct TilesTC : TilesF32 {
   // split units: TRSM bands, and the SYRKs that run on the FFMA body (three-term form); the
   // tensor-core updates are one MMA tile each
-  static constexpr bool SPLIT_SYRK = NTERM > 1, SPLIT_GEMM = false;
+  static constexpr bool SPLIT_TRSM = true, SPLIT_SYRK = NTERM > 1, SPLIT_GEMM = false;
   static constexpr int SMEM = tc::Cfg<NTERM>::SMEM > TilesF32::SMEM ? tc::Cfg<NTERM>::SMEM : TilesF32::SMEM;
-  static constexpr int EMIT_OFF = (f32::TRSM_ROWS_SMEM_BYTES + 127) / 128 * 128;
-  static_assert(EMIT_OFF + 2 * tc::Split<NTERM>::CHUNK <= SMEM, "TRSM split buffers must fit");
+  static constexpr int EMIT_OFF = (f32::TRSM_BAND_SMEM_BYTES + 127) / 128 * 128;
+  static_assert(EMIT_OFF + tc::SplitEmitBand<NTERM>::BYTES <= SMEM, "TRSM split buffers must fit");
   // one worker per SM: a second one would wait in tcgen05.alloc for columns the first holds
   static_assert(2 * SMEM > 228 * 1024, "tensor-core workers must not share an SM");
   __device__ static tc::State &state() {
@@ -623,20 +632,20 @@ struct TilesTC : TilesF32 {
   // them; without one the updates split their FP32 operands themselves
   __device__ static void trsm(T *B, int64_t ldb, const T *L, int64_t ldl, int mb, int nk, T *s,
                               unsigned char *split) {
-    // the chunk buffers sit past the TRSM's own shared memory
-    if (split && nk <= f32::PANEL_MAX_N)
-      f32::trsm_tile_rows(B, ldb, L, ldl, mb, nk, s,
-                          tc::SplitEmit<NTERM>{split, reinterpret_cast<unsigned char *>(s) + EMIT_OFF});
-    else
+    if (split && nk <= f32::PANEL_MAX_N) {
+      for (int r0 = 0; r0 < mb; r0 += f32::BAND_ROWS) trsm_rows(B, ldb, L, ldl, r0, min(f32::BAND_ROWS, mb - r0), nk, s, split);
+    } else {
       TilesF32::trsm(B, ldb, L, ldl, mb, nk, s, nullptr);
+    }
   }
+  // one band of 64 rows, its BF16 terms staged past the band body's shared memory
   __device__ static void trsm_rows(T *B, int64_t ldb, const T *L, int64_t ldl, int r0, int rows, int nk, T *s,
                                    unsigned char *split) {
     if (split && nk <= f32::PANEL_MAX_N)
-      f32::trsm_tile_rows(B + r0, ldb, L, ldl, rows, nk, s,
-                          tc::SplitEmitRows<NTERM>{split, reinterpret_cast<unsigned char *>(s) + EMIT_OFF, r0});
+      f32::trsm_band(B + r0, ldb, L, ldl, rows, nk, s,
+                     tc::SplitEmitBand<NTERM>{split, reinterpret_cast<unsigned char *>(s) + EMIT_OFF, r0});
     else
-      TilesF32::trsm(B + r0, ldb, L, ldl, rows, nk, s, nullptr);
+      TilesF32::trsm_rows(B, ldb, L, ldl, r0, rows, nk, s, nullptr);
   }
   // SYRK updates (C -= A A^T on a diagonal tile, rows of A that lie close together in the
   // matrix) add products that mostly share one sign, and the errors of the tensor cores' FP32
@@ -670,7 +679,7 @@ struct LuF64 {
   using Graph = LuGraph;
   static constexpr bool CAN_SPLIT = false;  // (the LU graph has its own runner)
   static constexpr int UPD_UNIT = 64;
-  static constexpr bool SPLIT_SYRK = false, SPLIT_GEMM = false;
+  static constexpr bool SPLIT_TRSM = false, SPLIT_SYRK = false, SPLIT_GEMM = false;
   static constexpr int SMEM = LU_SMEM_BYTES;
   static constexpr int MIN_BLOCKS = 2;
   __device__ static void begin() {}
@@ -705,7 +714,9 @@ __device__ __forceinline__ int split_units(const FactorArgs &a, const TaskDesc &
 template <class P>
 __device__ __forceinline__ bool should_split(const FactorArgs &a, const TaskDesc &d, bool starving) {
   if (!a.split_mode || d.kind == K_POTRF) return false;
-  if ((d.kind == K_SYRK && !P::SPLIT_SYRK) || (d.kind == K_GEMM && !P::SPLIT_GEMM)) return false;
+  if ((d.kind == K_TRSM && !P::SPLIT_TRSM) || (d.kind == K_SYRK && !P::SPLIT_SYRK) ||
+      (d.kind == K_GEMM && !P::SPLIT_GEMM))
+    return false;
   if (split_units<P>(a, d) < 2 || split_units<P>(a, d) > 255) return false;
   if (a.split_mode == 2) return true;
   if ((d.kind == K_TRSM || d.kind == K_SYRK) && d.i == d.k + 1) return true;

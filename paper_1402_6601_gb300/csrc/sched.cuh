@@ -244,6 +244,47 @@ CHOL_HD bool dada_trial(const ReadyTask *LR, int m, const int64_t *load, int W, 
   return (double)mx <= (2.0 + alpha) * (double)lam;
 }
 
+#ifdef __CUDACC__
+// HEFT without communication prediction on the device: every task, in priority order, goes to
+// the least-loaded worker (ties to the lowest index), as eft_worker decides. Each lane keeps
+// the minimum over its own workers (w = lane, lane + 32, ...) as one key (load << 11 | w);
+// after a placement only the lane owning the chosen worker rescans its workers, and a 5-step
+// shuffle minimum gives the next choice, instead of a scan of all W loads per task.
+// Returns false (nothing placed) if a load is negative or too large for the key.
+__device__ __forceinline__ bool heft_place_warp(const ReadyTask *LR, int m, int64_t *load, int W, PlaceScratch &s) {
+  const int lane = threadIdx.x & 31;
+  bool bad = false;
+  for (int w = lane; w < W; w += 32) bad |= load[w] < 0 || load[w] >= (int64_t(1) << 51);  // + m p < 2^51 + 2^50: keys stay below 2^63
+  for (int i = lane; i < m; i += 32) bad |= LR[i].p < 0 || LR[i].p >= (int64_t(1) << 40);
+  if (__any_sync(0xffffffffu, bad)) return false;
+  auto local_min = [&]() {
+    unsigned long long best = ~0ull;
+    for (int w = lane; w < W; w += 32) {
+      const unsigned long long key = ((unsigned long long)load[w] << 11) | (unsigned)w;
+      best = key < best ? key : best;
+    }
+    return best;
+  };
+  unsigned long long mine = local_min();
+  for (int q = 0; q < m; ++q) {
+    unsigned long long k = mine;
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long ok = __shfl_xor_sync(0xffffffffu, k, o);
+      k = ok < k ? ok : k;
+    }
+    const int w = (int)(k & 2047ull);
+    const int i = s.ord_prio[q];
+    if (lane == (w & 31)) {
+      load[w] += LR[i].p;
+      mine = local_min();
+    }
+    if (lane == 0) s.assign[i] = w;
+  }
+  __syncwarp();
+  return true;
+}
+#endif
+
 // Place the m ready tasks. load[W] is updated with the chosen placement. Returns the number
 // of bisection steps taken (DADA) or 0.
 template <class X>
@@ -254,6 +295,11 @@ CHOL_HD int place(int policy, double alpha, int max_iter, double eps, const Read
   X::sync();
   int iters = 0;
   if (policy == P_HEFT) {
+#ifdef __CUDA_ARCH__
+    if constexpr (X::WARP) {
+      if (!cp && W <= 2048 && heft_place_warp(LR, m, load, W, s)) return 0;
+    }
+#endif
     for (int q = 0; q < m; ++q) {
       const int i = s.ord_prio[q];
       const int w = eft_worker<X>(load, W, LR[i], cp);

@@ -332,32 +332,52 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
 #pragma unroll
         for (int u = 0; u < RPT; ++u) Xo[(i0 + u) * YLD + q] = t[u];
       }
-    } else if (cols <= SNW) {
-      // diagonal block, few right-hand sides: one warp per right-hand side, lane = row. Each
-      // step takes x_k on lane k and updates the rows below it with one warp-wide FMA (an FP64
-      // instruction costs the SM sub-partition's FP64 pipe the same time with one active lane
-      // as with 32, so a single thread would pay for 32 lanes on every one of its 496 FMAs).
-      // Every x_i sees the same operations in the same order as in the thread-per-column form.
-      const int c = warp;
-      if (c < cols) {
-        T x = Ys[lane * YLD + c];
-        const T lrow_inv = Rs[lane];
+    } else if (cols <= 2 * SNW) {
+      // diagonal block, few right-hand sides: one warp per pair of right-hand sides (columns
+      // warp and warp + 8), lane = row. Each step takes x_k on lane k and updates the rows
+      // below it with one warp-wide FMA per column (an FP64 instruction costs the SM
+      // sub-partition's FP64 pipe the same time with one active lane as with 32, so a single
+      // thread would pay for 32 lanes on every one of its 496 FMAs). Every x_i sees the same
+      // operations in the same order as in the thread-per-column form.
+      const int c0 = warp, c1 = warp + SNW;
+      if (c0 < cols) {
+        const bool two = c1 < cols;
+        T x0 = Ys[lane * YLD + c0];
+        T x1 = two ? Ys[lane * YLD + c1] : T(0);
+        const T rinv = Rs[lane];
         if (!REV) {
 #pragma unroll
           for (int k = 0; k < SBK; ++k) {
-            if (lane == k) x = squot(x, Ld[k * DLD + k], lrow_inv);
-            const T xk = __shfl_sync(0xffffffffu, x, k);
-            if (lane > k) x = fma(-Ld[lane * DLD + k], xk, x);
+            if (lane == k) {
+              x0 = squot(x0, Ld[k * DLD + k], rinv);
+              if (two) x1 = squot(x1, Ld[k * DLD + k], rinv);
+            }
+            const T y0 = __shfl_sync(0xffffffffu, x0, k);
+            const T y1 = __shfl_sync(0xffffffffu, x1, k);
+            if (lane > k) {
+              const T l = Ld[lane * DLD + k];
+              x0 = fma(-l, y0, x0);
+              if (two) x1 = fma(-l, y1, x1);
+            }
           }
         } else {
 #pragma unroll
           for (int k = SBK - 1; k >= 0; --k) {
-            if (lane == k) x = squot(x, Ld[k * DLD + k], lrow_inv);
-            const T xk = __shfl_sync(0xffffffffu, x, k);
-            if (lane < k) x = fma(-Ld[k * DLD + lane], xk, x);
+            if (lane == k) {
+              x0 = squot(x0, Ld[k * DLD + k], rinv);
+              if (two) x1 = squot(x1, Ld[k * DLD + k], rinv);
+            }
+            const T y0 = __shfl_sync(0xffffffffu, x0, k);
+            const T y1 = __shfl_sync(0xffffffffu, x1, k);
+            if (lane < k) {
+              const T l = Ld[k * DLD + lane];
+              x0 = fma(-l, y0, x0);
+              if (two) x1 = fma(-l, y1, x1);
+            }
           }
         }
-        Ys[lane * YLD + c] = x;
+        Ys[lane * YLD + c0] = x0;
+        if (two) Ys[lane * YLD + c1] = x1;
       }
     } else if (tid < cols) {
       // diagonal block: one thread per right-hand side runs the substitution
@@ -526,6 +546,20 @@ using namespace chol;
 extern "C" size_t chol_solve_workspace_size(int n, int nrhs) {
   if (n < 0 || nrhs < 0) return 0;
   return solve_ws(n, nrhs);
+}
+
+extern "C" chol_status chol_solve_f32(int n, int nrhs, const float *dL, int lda, float *dB, int ldb, void *dWork,
+                                      size_t work_bytes, int *dInfo, void *stream) {
+  const chol_status st = check_args(n, nrhs, dL, lda, dB, ldb, dWork, work_bytes);
+  if (st != CHOL_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n == 0 || nrhs == 0) {
+    if (dInfo) CHOL_CUDA_TRY(cudaMemsetAsync(dInfo, 0, sizeof(int), s));
+    return CHOL_OK;
+  }
+  const chol_status r = solve_f32(n, nrhs, dL, lda, dB, ldb, dWork, nullptr, s);
+  if (r != CHOL_OK) return r;
+  return write_info(dWork, 2, dInfo, s);
 }
 
 extern "C" chol_status chol_trsm_sweep(int uplo_t, int n, int nrhs, const double *dL, int lda,

@@ -430,20 +430,9 @@ static __device__ __noinline__ int potrf_tile_smem(float *G, int64_t ld, int nk,
   return 0;
 }
 
-// TRSM X L^T = B in place (B: mb x nk, L: nk x nk lower, nk <= PANEL_MAX_N), left-looking
-// by 32-column blocks with one row of B per thread. For block j0 the thread keeps its 32
-// right-hand values in registers, applies the earlier columns of X (its own row, written by
-// itself in earlier blocks and read back from L2) against rows j0.. of L staged in shared
-// memory, then solves the 32 x 32 diagonal block in registers. The contraction is one long
-// register-resident stream per thread instead of block-wide updates with a 32-deep k, and
-// a column block costs one barrier pair.
-//
-// `emit` receives every finished 32-column block of each row (emit.row(r, j0 / 32, x)) and is
-// told about the rows past mb (emit.zero(r, j0 / 32)), for a consumer that wants the result in
-// another layout as well; emit.flush(j0 / 32) follows each block (all threads) and
-// emit.finish() the last one. The default does nothing.
+// Receivers of the finished 32-column blocks of the band TRSM's rows (see trsm_band); the
+// default does nothing.
 constexpr int TR_LD = IB + 4;
-constexpr int TRSM_ROWS_SMEM_BYTES = (PANEL_MAX_N * TR_LD + IB) * 4;
 
 struct NoEmit {
   __device__ void row(int, int, const float (&)[IB]) const {}
@@ -452,15 +441,34 @@ struct NoEmit {
   __device__ void finish() const {}
 };
 
+// TRSM X L^T = B for one band of at most 64 rows of a panel tile (nk <= PANEL_MAX_N): the
+// body of every FP32 TRSM, run band by band by one worker or as the units of a split task.
+// Four threads per row (t = 4 row + part): for each 32-column block j0 the parts accumulate
+// B(row, j0 + c) - sum_k X(row, k) L(j0 + c, k) over the k of their own 8-wide chunks
+// (chunk q goes to part q mod 4), the partial sums meet in two shuffle steps, and part 0
+// solves the 32 x 32 diagonal block (right-looking, corrected quotients). The band's rows live
+// in shared memory for the whole task, so the solved values are never read back from L2, and
+// a block costs one staging of L and two barriers. `emit` gets every finished 32-column block
+// of each row (emit.row / emit.zero for rows past `rows`, then emit.flush; emit.finish at the end).
+constexpr int BAND_ROWS = 64;
+constexpr int BX_LD = PANEL_MAX_N + 4;  // row stride of the band's rows (16-byte aligned)
+constexpr int TRSM_BAND_SMEM_BYTES = (BAND_ROWS * BX_LD + PANEL_MAX_N * TR_LD + IB) * 4;
+
 template <class Emit = NoEmit>
-static __device__ __noinline__ void trsm_tile_rows(float *B, int64_t ldb, const float *L, int64_t ldl, int mb,
-                                                   int nk, float *smem, Emit emit = Emit()) {
-  float *Lp = smem;  // Lp[k * TR_LD + c] = L(j0 + c, k), zero above the diagonal, identity padding
-  float *Rinv = smem + PANEL_MAX_N * TR_LD;
-  const int tid = threadIdx.x;
+static __device__ __noinline__ void trsm_band(float *B, int64_t ldb, const float *L, int64_t ldl, int rows, int nk,
+                                              float *smem, Emit emit = Emit()) {
+  float *Xs = smem;                          // Xs[row * BX_LD + k]: B, then X as it is solved
+  float *Lp = smem + BAND_ROWS * BX_LD;      // Lp[k * TR_LD + c] = L(j0 + c, k), identity padding
+  float *Rinv = Lp + PANEL_MAX_N * TR_LD;
+  const int tid = threadIdx.x, row = tid >> 2, part = tid & 3;
+  const int nk32 = (nk + IB - 1) / IB * IB;  // columns past nk stay zero
+  for (int e = tid; e < BAND_ROWS * nk32; e += NT) {
+    const int r = e % BAND_ROWS, c = e / BAND_ROWS;
+    Xs[r * BX_LD + c] = (r < rows && c < nk) ? ldcg(B + (int64_t)c * ldb + r) : 0.f;
+  }
   for (int j0 = 0; j0 < nk; j0 += IB) {
     const int jb = min(IB, nk - j0);
-    __syncthreads();  // the previous block is done with Lp
+    __syncthreads();  // the band's rows are loaded, the previous block is done with Lp
     for (int e = tid; e < (j0 + IB) * IB; e += NT) {
       const int c = e & (IB - 1), k = e >> 5;
       Lp[k * TR_LD + c] =
@@ -468,46 +476,62 @@ static __device__ __noinline__ void trsm_tile_rows(float *B, int64_t ldb, const 
     }
     if (tid < IB) Rinv[tid] = tid < jb ? __frcp_rn(ldcg(L + (int64_t)(j0 + tid) * ldl + j0 + tid)) : 1.f;
     __syncthreads();
-    for (int r = tid; r < mb; r += NT) {
-      float acc[IB];
+    const float *x = Xs + row * BX_LD;
+    float acc[IB];
 #pragma unroll
-      for (int c = 0; c < IB; ++c) acc[c] = c < jb ? ldcg(B + (int64_t)(j0 + c) * ldb + r) : 0.f;
-      for (int k0 = 0; k0 < j0; k0 += 8) {
-        float xk[8];
+    for (int c = 0; c < IB; ++c) acc[c] = 0.f;
+    for (int k0 = 8 * part; k0 < j0; k0 += 32) {
+      const float4 xa = *reinterpret_cast<const float4 *>(x + k0);
+      const float4 xb = *reinterpret_cast<const float4 *>(x + k0 + 4);
+      const float xk[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
 #pragma unroll
-        for (int u = 0; u < 8; ++u) xk[u] = ldcg(B + (int64_t)(k0 + u) * ldb + r);
+      for (int u = 0; u < 8; ++u) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-#pragma unroll
-          for (int c4 = 0; c4 < IB; c4 += 4) {
-            const float4 l = *reinterpret_cast<const float4 *>(Lp + (k0 + u) * TR_LD + c4);
-            acc[c4] = fmaf(-xk[u], l.x, acc[c4]);
-            acc[c4 + 1] = fmaf(-xk[u], l.y, acc[c4 + 1]);
-            acc[c4 + 2] = fmaf(-xk[u], l.z, acc[c4 + 2]);
-            acc[c4 + 3] = fmaf(-xk[u], l.w, acc[c4 + 3]);
-          }
+        for (int c4 = 0; c4 < IB; c4 += 4) {
+          const float4 l = *reinterpret_cast<const float4 *>(Lp + (k0 + u) * TR_LD + c4);
+          acc[c4] = fmaf(xk[u], l.x, acc[c4]);
+          acc[c4 + 1] = fmaf(xk[u], l.y, acc[c4 + 1]);
+          acc[c4 + 2] = fmaf(xk[u], l.z, acc[c4 + 2]);
+          acc[c4 + 3] = fmaf(xk[u], l.w, acc[c4 + 3]);
         }
       }
-      // x D^T = acc with D(c, m) = Lp[(j0 + m) * TR_LD + c]
+    }
+    // the four parts of a row are adjacent lanes
+#pragma unroll
+    for (int c = 0; c < IB; ++c) {
+      acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 1);
+      acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 2);
+    }
+    if (part == 0) {
+      float v[IB];
+#pragma unroll
+      for (int c = 0; c < IB; ++c) v[c] = x[j0 + c] - acc[c];
+      // v D^T = b with D(c, m) = Lp[(j0 + m) * TR_LD + c]
       const float *D = Lp + j0 * TR_LD;
 #pragma unroll
       for (int m = 0; m < IB; ++m) {
-        acc[m] = quot(acc[m], D[m * TR_LD + m], Rinv[m]);
+        v[m] = quot(v[m], D[m * TR_LD + m], Rinv[m]);
 #pragma unroll
         for (int c4 = (m + 1) & ~3; c4 < IB; c4 += 4) {
           const float4 d = *reinterpret_cast<const float4 *>(D + m * TR_LD + c4);
-          if (c4 > m) acc[c4] = fmaf(-acc[m], d.x, acc[c4]);
-          if (c4 + 1 > m) acc[c4 + 1] = fmaf(-acc[m], d.y, acc[c4 + 1]);
-          if (c4 + 2 > m) acc[c4 + 2] = fmaf(-acc[m], d.z, acc[c4 + 2]);
-          acc[c4 + 3] = fmaf(-acc[m], d.w, acc[c4 + 3]);
+          if (c4 > m) v[c4] = fmaf(-v[m], d.x, v[c4]);
+          if (c4 + 1 > m) v[c4 + 1] = fmaf(-v[m], d.y, v[c4 + 1]);
+          if (c4 + 2 > m) v[c4 + 2] = fmaf(-v[m], d.z, v[c4 + 2]);
+          v[c4 + 3] = fmaf(-v[m], d.w, v[c4 + 3]);
         }
       }
+      float *xw = Xs + row * BX_LD + j0;
 #pragma unroll
-      for (int c = 0; c < IB; ++c)
-        if (c < jb) stcg(B + (int64_t)(j0 + c) * ldb + r, acc[c]);
-      emit.row(r, j0 / IB, acc);
+      for (int c = 0; c < IB; ++c) xw[c] = c < jb ? v[c] : 0.f;
+      if (row < rows) {
+#pragma unroll
+        for (int c = 0; c < IB; ++c)
+          if (c < jb) stcg(B + (int64_t)(j0 + c) * ldb + row, v[c]);
+        emit.row(row, j0 / IB, v);
+      } else {
+        emit.zero(row, j0 / IB);
+      }
     }
-    if (tid >= mb) emit.zero(tid, j0 / IB);
     emit.flush(j0 / IB);
   }
   emit.finish();

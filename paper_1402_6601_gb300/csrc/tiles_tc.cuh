@@ -369,62 +369,49 @@ struct Split {
 // global, bulk async-group). Before the task completes, finish() waits for the copies and
 // orders them (async proxy) before the completion's release, so the updates that bulk-copy
 // the tile see it.
+// The BF16 terms of one band of 64 rows [r0, r0 + 64) of a panel tile, for f32::trsm_band:
+// the 64 rows of one term form one contiguous 4 KiB range of a chunk (8-row groups of 512
+// bytes), so the band is staged compactly (term t of chunk c at buf + ((c & 1) NTERM + t) 4 KiB)
+// and each flush copies NTERM ranges to their place in the chunk.
 template <int NTERM>
-struct SplitEmit {
-  unsigned char *tile;  // global: the tile's chunks
-  unsigned char *buf;   // shared: 2 x CHUNK bytes, 16-byte aligned
-  __device__ void row(int r, int c, const float (&v)[32]) const {
-    store_row<NTERM>(buf + (c & 1) * Split<NTERM>::CHUNK, v, r);
-  }
-  __device__ void zero(int r, int c) const {
-    float z[32];
-#pragma unroll
-    for (int e = 0; e < 32; ++e) z[e] = 0.f;
-    store_row<NTERM>(buf + (c & 1) * Split<NTERM>::CHUNK, z, r);
-  }
-  __device__ void flush(int c) const {
-    fence_async_smem();  // the generic-proxy writes of the chunk, before the copy engine reads
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(
-                       tile + (size_t)c * Split<NTERM>::CHUNK),
-                   "r"(smem_u32(buf + (c & 1) * Split<NTERM>::CHUNK)), "r"((uint32_t)Split<NTERM>::CHUNK)
-                   : "memory");
-      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-      // the other buffer is written next: its copy (issued one block ago) must have read it
-      asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-    }
-    __syncthreads();
-  }
-  __device__ void finish() const {
-    if (threadIdx.x == 0) {
-      asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-      asm volatile("fence.proxy.async.global;" ::: "memory");
-    }
-    __syncthreads();
-  }
-};
-
-// The same for a band of 64 rows [r0, r0 + 64) of the panel tile (a unit of a split TRSM):
-// rows are stored at their place in a band-sized part of the stage buffers, and since the 64
-// rows of one term form one contiguous 4 KiB range of a chunk (8-row groups of 512 bytes),
-// each flush copies NTERM ranges. Rows of the band past the tile are zero.
-template <int NTERM>
-struct SplitEmitRows {
+struct SplitEmitBand {
   static constexpr int ROWS = 64;
   static constexpr int BAND = ROWS / 8 * 512;  // bytes of one term of the band
+  static constexpr int BYTES = 2 * NTERM * BAND;
   unsigned char *tile;  // global: the tile's chunks
-  unsigned char *buf;   // shared: 2 x CHUNK bytes, 16-byte aligned
-  int r0;               // first row of the band (a multiple of 64)
-  __device__ void row(int r, int c, const float (&v)[32]) const {
-    if (r < ROWS) store_row<NTERM>(buf + (c & 1) * Split<NTERM>::CHUNK, v, r);
+  unsigned char *buf;   // shared: BYTES, 16-byte aligned
+  int r0;               // first row of the band in the tile (a multiple of 64)
+  __device__ void store(int r, int c, const float (&v)[32]) const {
+    unsigned char *dst = buf + (c & 1) * NTERM * BAND;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      const uint32_t off = (uint32_t)(((r >> 3) * 4 + g) * 128 + (r & 7) * 16);
+      float x[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) x[e] = v[8 * g + e];
+#pragma unroll
+      for (int t = 0; t < NTERM; ++t) {
+        float b[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          b[e] = __bfloat162float(__float2bfloat16_rn(x[e]));
+          x[e] = x[e] - b[e];
+        }
+        uint4 w;
+        w.x = pack2(b[0], b[1]);
+        w.y = pack2(b[2], b[3]);
+        w.z = pack2(b[4], b[5]);
+        w.w = pack2(b[6], b[7]);
+        *reinterpret_cast<uint4 *>(dst + t * BAND + off) = w;
+      }
+    }
   }
+  __device__ void row(int r, int c, const float (&v)[32]) const { store(r, c, v); }
   __device__ void zero(int r, int c) const {
-    if (r >= ROWS) return;
     float z[32];
 #pragma unroll
     for (int e = 0; e < 32; ++e) z[e] = 0.f;
-    store_row<NTERM>(buf + (c & 1) * Split<NTERM>::CHUNK, z, r);
+    store(r, c, z);
   }
   __device__ void flush(int c) const {
     fence_async_smem();
@@ -433,7 +420,7 @@ struct SplitEmitRows {
       for (int t = 0; t < NTERM; ++t) {
         const size_t go = (size_t)c * Split<NTERM>::CHUNK + (size_t)t * Cfg<NTERM>::OPB + (size_t)(r0 / 8) * 512;
         asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(tile + go),
-                     "r"(smem_u32(buf + (c & 1) * Split<NTERM>::CHUNK + t * Cfg<NTERM>::OPB)), "r"((uint32_t)BAND)
+                     "r"(smem_u32(buf + ((c & 1) * NTERM + t) * BAND)), "r"((uint32_t)BAND)
                      : "memory");
       }
       asm volatile("cp.async.bulk.commit_group;" ::: "memory");
