@@ -102,6 +102,11 @@ def parse():
     p.add_argument("--no-mixed-oracle", action="store_true",
                    help="skip the oracle's FP64 solution of the mixed-precision configuration (about a minute "
                         "on 16 host cores)")
+    p.add_argument("--bf16-pcg", action="store_true",
+                   help="also measure plain BF16 as a preconditioner: conjugate gradients in FP64 preconditioned "
+                        "by the shifted BF16 tensor-core factor, on the mixed-precision configuration")
+    p.add_argument("--bf16-pcg-only", action="store_true", help="run only that measurement")
+    p.add_argument("--pcg-maxit", type=int, default=3000)
     p.add_argument("--no-lu", action="store_true")
     p.add_argument("--lu-n", type=int, default=8192)
     p.add_argument("--lu-nb", type=int, default=0)
@@ -340,6 +345,13 @@ def main():
         if world > 1:
             dist.barrier()
 
+    if args.bf16_pcg_only:
+        if rank == 0:
+            print(json.dumps({"bf16_pcg": run_bf16_pcg(args, chol, dev)}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
     if args.fp64_probe_only:
         if rank == 0:
             print(json.dumps({"fp64_probe": run_fp64_probe(chol, dev)}), flush=True)
@@ -431,6 +443,9 @@ def main():
     adjoint = None
     if not args.no_adjoint and rank == 0:
         adjoint = run_adjoint(args, chol, dev)
+    pcg = None
+    if args.bf16_pcg and rank == 0:
+        pcg = run_bf16_pcg(args, chol, dev)
     lu = None
     if not args.no_lu and rank == 0:
         lu = run_lu(args, chol, dev)
@@ -448,7 +463,7 @@ def main():
             "factor_ms": round(fac_avg, 2), "factor_ms_ci95": fac_stat["ci95"],
             "step_ms": stat(step_ms, 2), "solve_backward_error": berr,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "mixed_precision": mixed, "batched": batched,
-            "adjoint": adjoint, "lu": lu,
+            "adjoint": adjoint, "lu": lu, "bf16_pcg": pcg,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
                        "reasons": clk.get("reasons"), "samples": clk.get("samples"),
@@ -582,6 +597,96 @@ def run_mixed(args, chol, dev):
             "target_backward_error": 1e-14, "fp64_backward_error": e64, "mixed_backward_error": b["backward_error"],
             "mixed_reported_backward_error": b["reported_backward_error"], "iterations": b["iterations"],
             "info": b["info"], "x_rel_diff_vs_fp64": b.get("x_rel_diff_vs_fp64"), "variants": variants}
+
+
+def run_bf16_pcg(args, chol, dev):
+    """Plain BF16 at kappa = 1e6 as a preconditioner instead of a factor for classical
+    refinement (where it breaks down): the scaled matrix D^-1/2 A D^-1/2 + sigma I, sigma the
+    smallest of 2^-12, 2^-11, ... for which the BF16 tensor-core factor exists, preconditions
+    conjugate gradients run in FP64 on A (one block of --mixed-nrhs independent solves; the
+    preconditioner applies the library's FP32 substitution to the scaled residual). Stops when
+    every column's backward error (recomputed from the true residual every 10 iterations) is
+    <= 1e-14, or after --pcg-maxit iterations. The FP64 products A p are torch matrix products
+    here (this leg measures an alternative algorithm, not the library's path); the library's
+    own symmetric FP64 product of the same shape is the refinement's residual kernel, so the
+    cost of one iteration on the library's kernels is about one refinement step."""
+    import torch
+    import synth
+    n, nrhs = args.mixed_n, args.mixed_nrhs
+    A = chol.colmajor(synth.householder_spd(n, seed=args.seed, cond=1e6, device=dev))
+    B = chol.colmajor(synth.rhs(n, nrhs, seed=args.seed + 7, device=dev))
+    d = torch.diagonal(A).rsqrt()                          # D^-1/2
+    S = (A * d[:, None] * d[None, :])
+    o = chol.opts(nb=256)
+    work = torch.empty(chol.lowp_workspace_size(n, o, precision="bf16"), dtype=torch.uint8, device=dev)
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    sigma, L = None, None
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for e in range(12, 0, -1):
+        s = 2.0 ** -e
+        L = chol.colmajor(S.to(torch.float32))
+        L.diagonal().add_(s)  # the shift (diag(S) = 1, exact in FP32)
+        e0.record()
+        chol.factor_f32(L, o, work=work, info=info, precision="bf16")
+        e1.record()
+        torch.cuda.synchronize()
+        if int(info.item()) == 0:
+            sigma = s
+            break
+    factor_ms = e0.elapsed_time(e1)
+    del S
+    swork = torch.empty(chol.solve_workspace_size(n, nrhs), dtype=torch.uint8, device=dev)
+
+    def precond(R):
+        Z = chol.colmajor((R * d[:, None]).to(torch.float32))
+        chol.solve_f32(L, Z, work=swork)
+        return Z.to(torch.float64) * d[:, None]
+
+    normA = float(A.abs().sum(1).max())
+
+    def eta(X):
+        R = B - A @ X
+        return float((R.abs().amax(0) / (normA * X.abs().amax(0) + B.abs().amax(0))).amax())
+
+    X = torch.zeros_like(B)
+    R = B.clone()
+    Z = precond(R)
+    P = Z.clone()
+    rz = (R * Z).sum(0)
+    it, e_last = 0, 1.0
+    t_mv = t_pc = 0.0
+    torch.cuda.synchronize()
+    t_start = time.perf_counter()
+    while it < args.pcg_maxit:
+        a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
+        a2 = torch.cuda.Event(enable_timing=True)
+        a0.record()
+        Q = A @ P
+        a1.record()
+        alpha = rz / (P * Q).sum(0)
+        X += alpha * P
+        R -= alpha * Q
+        Z = precond(R)
+        a2.record()
+        rz_new = (R * Z).sum(0)
+        P = Z + (rz_new / rz) * P
+        rz = rz_new
+        it += 1
+        torch.cuda.synchronize()
+        t_mv += a0.elapsed_time(a1)
+        t_pc += a1.elapsed_time(a2)
+        if it % 10 == 0:
+            e_last = eta(X)
+            if e_last <= 1e-14:
+                break
+    total_s = time.perf_counter() - t_start
+    return {"workload": "n=%d, %d RHS, kappa = 1e6 (the mixed-precision configuration)" % (n, nrhs),
+            "preconditioner": "BF16 tensor-core factor (one term, FP32 accumulation) of D^-1/2 A D^-1/2 + sigma I",
+            "sigma": sigma, "factor_ms": round(factor_ms, 2), "iterations": it, "backward_error": e_last,
+            "reached_target": e_last <= 1e-14, "seconds": round(total_s, 3),
+            "ms_per_iteration_product": round(t_mv / max(it, 1), 3),
+            "ms_per_iteration_preconditioner": round(t_pc / max(it, 1), 3)}
 
 
 def run_lu(args, chol, dev):

@@ -443,16 +443,18 @@ struct NoEmit {
 
 // TRSM X L^T = B for one band of at most 64 rows of a panel tile (nk <= PANEL_MAX_N): the
 // body of every FP32 TRSM, run band by band by one worker or as the units of a split task.
-// Four threads per row (t = 4 row + part): for each 32-column block j0 the parts accumulate
-// B(row, j0 + c) - sum_k X(row, k) L(j0 + c, k) over the k of their own 8-wide chunks
-// (chunk q goes to part q mod 4), the partial sums meet in two shuffle steps, and part 0
-// solves the 32 x 32 diagonal block (right-looking, corrected quotients). The band's rows live
-// in shared memory for the whole task, so the solved values are never read back from L2, and
-// a block costs one staging of L and two barriers. `emit` gets every finished 32-column block
+// Four threads per row, one part of the k range each (t = 64 part + row, so the 32 lanes of a
+// warp share their part and every read of L is a broadcast): for each 32-column block j0 the
+// parts accumulate sum_k X(row, k) L(j0 + c, k) over their own 8-wide chunks (chunk q goes to
+// part q mod 4), parts 1..3 leave their sums in shared memory, and part 0 adds them in part
+// order, subtracts from B(row, j0 + c) and solves the 32 x 32 diagonal block (right-looking,
+// corrected quotients). The band's rows live in shared memory for the whole task, so the
+// solved values are never read back from L2. `emit` gets every finished 32-column block
 // of each row (emit.row / emit.zero for rows past `rows`, then emit.flush; emit.finish at the end).
 constexpr int BAND_ROWS = 64;
 constexpr int BX_LD = PANEL_MAX_N + 4;  // row stride of the band's rows (16-byte aligned)
-constexpr int TRSM_BAND_SMEM_BYTES = (BAND_ROWS * BX_LD + PANEL_MAX_N * TR_LD + IB) * 4;
+constexpr int PS_LD = IB + 1;           // stride of the parts' partial sums (one row each)
+constexpr int TRSM_BAND_SMEM_BYTES = (BAND_ROWS * BX_LD + PANEL_MAX_N * TR_LD + IB + 3 * BAND_ROWS * PS_LD) * 4;
 
 template <class Emit = NoEmit>
 static __device__ __noinline__ void trsm_band(float *B, int64_t ldb, const float *L, int64_t ldl, int rows, int nk,
@@ -460,7 +462,9 @@ static __device__ __noinline__ void trsm_band(float *B, int64_t ldb, const float
   float *Xs = smem;                          // Xs[row * BX_LD + k]: B, then X as it is solved
   float *Lp = smem + BAND_ROWS * BX_LD;      // Lp[k * TR_LD + c] = L(j0 + c, k), identity padding
   float *Rinv = Lp + PANEL_MAX_N * TR_LD;
-  const int tid = threadIdx.x, row = tid >> 2, part = tid & 3;
+  float *Ps = Rinv + IB;                     // Ps[((part - 1) * BAND_ROWS + row) * PS_LD + c]
+  const int tid = threadIdx.x, row = tid & (BAND_ROWS - 1), part = tid >> 6;
+  static_assert(NT == 4 * BAND_ROWS, "four threads per row");
   const int nk32 = (nk + IB - 1) / IB * IB;  // columns past nk stay zero
   for (int e = tid; e < BAND_ROWS * nk32; e += NT) {
     const int r = e % BAND_ROWS, c = e / BAND_ROWS;
@@ -496,16 +500,20 @@ static __device__ __noinline__ void trsm_band(float *B, int64_t ldb, const float
         }
       }
     }
-    // the four parts of a row are adjacent lanes
+    if (part > 0) {
+      float *ps = Ps + ((part - 1) * BAND_ROWS + row) * PS_LD;
 #pragma unroll
-    for (int c = 0; c < IB; ++c) {
-      acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 1);
-      acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 2);
+      for (int c = 0; c < IB; ++c) ps[c] = acc[c];
     }
+    __syncthreads();
     if (part == 0) {
       float v[IB];
 #pragma unroll
-      for (int c = 0; c < IB; ++c) v[c] = x[j0 + c] - acc[c];
+      for (int c = 0; c < IB; ++c) {
+        const float s = ((acc[c] + Ps[row * PS_LD + c]) + Ps[(BAND_ROWS + row) * PS_LD + c]) +
+                        Ps[(2 * BAND_ROWS + row) * PS_LD + c];
+        v[c] = x[j0 + c] - s;
+      }
       // v D^T = b with D(c, m) = Lp[(j0 + m) * TR_LD + c]
       const float *D = Lp + j0 * TR_LD;
 #pragma unroll
