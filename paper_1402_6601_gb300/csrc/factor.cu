@@ -37,16 +37,18 @@ namespace chol {
 
 constexpr int SM_SLOTS = 1024;  // %smid values tracked by the co-scheduling rule
 
+// Control block. The counters that every task touches (done, queued, free_sms) and the words
+// that idle workers poll (abort, help_open) sit on separate 128-byte lines, so that polling
+// and the atomics of running workers do not queue behind one another on one line.
 struct Ctrl {
-  int done;
-  int abort;
+  alignas(128) int done;
+  alignas(128) int abort;
   int info;
   unsigned int fifo_seq;
   int spills;
-  int queued;    // tasks in all queues
-  int free_sms;  // SMs that host a worker and run no task
-  int help_open; // split tasks with units not yet claimed
-  int pad[56];
+  alignas(128) int queued;    // tasks in all queues
+  alignas(128) int free_sms;  // SMs that host a worker and run no task
+  alignas(128) int help_open; // split tasks with units not yet claimed
 };
 
 // A task cut into units that idle workers help with (one slot per worker, written by the
@@ -619,8 +621,10 @@ struct TilesTC : TilesF32 {
   // split units: TRSM bands, and the SYRKs that run on the FFMA body (three-term form); the
   // tensor-core updates are one MMA tile each
   static constexpr bool SPLIT_TRSM = true, SPLIT_SYRK = NTERM > 1, SPLIT_GEMM = false;
-  static constexpr int SMEM = tc::Cfg<NTERM>::SMEM > TilesF32::SMEM ? tc::Cfg<NTERM>::SMEM : TilesF32::SMEM;
   static constexpr int EMIT_OFF = (f32::TRSM_BAND_SMEM_BYTES + 127) / 128 * 128;
+  static constexpr int SMEM0 = tc::Cfg<NTERM>::SMEM > TilesF32::SMEM ? tc::Cfg<NTERM>::SMEM : TilesF32::SMEM;
+  static constexpr int SMEM = SMEM0 > EMIT_OFF + tc::SplitEmitBand<NTERM>::BYTES ? SMEM0
+                                                                                 : EMIT_OFF + tc::SplitEmitBand<NTERM>::BYTES;
   static_assert(EMIT_OFF + tc::SplitEmitBand<NTERM>::BYTES <= SMEM, "TRSM split buffers must fit");
   // one worker per SM: a second one would wait in tcgen05.alloc for columns the first holds
   static_assert(2 * SMEM > 228 * 1024, "tensor-core workers must not share an SM");

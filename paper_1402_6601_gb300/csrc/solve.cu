@@ -333,6 +333,7 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
         for (int u = 0; u < RPT; ++u) Xo[(i0 + u) * YLD + q] = t[u];
       }
     } else if (cols <= 2 * SNW) {
+      // (with one right-hand side only warp 0 works and the second column's steps are left out)
       // diagonal block, few right-hand sides: one warp per pair of right-hand sides (columns
       // warp and warp + 8), lane = row. Each step takes x_k on lane k and updates the rows
       // below it with one warp-wide FMA per column (an FP64 instruction costs the SM
@@ -353,7 +354,7 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
               if (two) x1 = squot(x1, Ld[k * DLD + k], rinv);
             }
             const T y0 = __shfl_sync(0xffffffffu, x0, k);
-            const T y1 = __shfl_sync(0xffffffffu, x1, k);
+            const T y1 = two ? __shfl_sync(0xffffffffu, x1, k) : T(0);
             if (lane > k) {
               const T l = Ld[lane * DLD + k];
               x0 = fma(-l, y0, x0);
@@ -368,7 +369,7 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
               if (two) x1 = squot(x1, Ld[k * DLD + k], rinv);
             }
             const T y0 = __shfl_sync(0xffffffffu, x0, k);
-            const T y1 = __shfl_sync(0xffffffffu, x1, k);
+            const T y1 = two ? __shfl_sync(0xffffffffu, x1, k) : T(0);
             if (lane < k) {
               const T l = Ld[k * DLD + lane];
               x0 = fma(-l, y0, x0);

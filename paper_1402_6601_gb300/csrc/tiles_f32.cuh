@@ -454,31 +454,73 @@ struct NoEmit {
 constexpr int BAND_ROWS = 64;
 constexpr int BX_LD = PANEL_MAX_N + 4;  // row stride of the band's rows (16-byte aligned)
 constexpr int PS_LD = IB + 1;           // stride of the parts' partial sums (one row each)
-constexpr int TRSM_BAND_SMEM_BYTES = (BAND_ROWS * BX_LD + PANEL_MAX_N * TR_LD + IB + 3 * BAND_ROWS * PS_LD) * 4;
+constexpr int TRSM_BAND_SMEM_BYTES = (BAND_ROWS * BX_LD + 2 * PANEL_MAX_N * TR_LD + IB + 3 * BAND_ROWS * PS_LD) * 4;
+
+// Columns j0 .. j0 + 31 of L (rows k < j0 + 32) into Lp[k * TR_LD + c] = L(j0 + c, k): 16-byte
+// asynchronous copies (cp.async, completed with the calling thread's wait_group) for whole
+// 4-column pieces inside the tile, plain stores of the identity padding past it. The strict
+// upper part of the diagonal 32 x 32 block arrives as whatever the tile holds there and is
+// cleared by trsm_band_fix once the copies have landed.
+__device__ __forceinline__ void trsm_band_stage(float *Lp, const float *L, int64_t ldl, int j0, int nk) {
+  const int jb = min(IB, nk - j0);
+  for (int idx = threadIdx.x; idx < (j0 + IB) * (IB / 4); idx += NT) {
+    const int k = idx >> 3, c4 = (idx & 7) * 4;
+    float *dst = Lp + k * TR_LD + c4;
+    const float *src = L + (int64_t)k * ldl + j0 + c4;
+    // (any leading dimension and tile size are allowed: a piece that does not start on a
+    // 16-byte boundary is loaded element by element)
+    if (c4 + 4 <= jb && k < nk && ((reinterpret_cast<uintptr_t>(src) & 15) == 0)) {
+      const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c4 + u;
+        dst[u] = (c < jb && k <= j0 + c) ? ldcg(L + (int64_t)k * ldl + j0 + c) : (k == j0 + c ? 1.f : 0.f);
+      }
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void trsm_band_fix(float *Lp, float *Rinv, int j0, int nk) {
+  const int jb = min(IB, nk - j0);
+  for (int e = threadIdx.x; e < IB * IB; e += NT) {
+    const int c = e & (IB - 1), kr = e >> 5;  // row k = j0 + kr of the diagonal block
+    if (c < kr && c < jb) Lp[(j0 + kr) * TR_LD + c] = 0.f;
+  }
+  if (threadIdx.x < IB) {
+    const int c = threadIdx.x;
+    Rinv[c] = c < jb ? __frcp_rn(Lp[(j0 + c) * TR_LD + c]) : 1.f;
+  }
+}
 
 template <class Emit = NoEmit>
 static __device__ __noinline__ void trsm_band(float *B, int64_t ldb, const float *L, int64_t ldl, int rows, int nk,
                                               float *smem, Emit emit = Emit()) {
   float *Xs = smem;                          // Xs[row * BX_LD + k]: B, then X as it is solved
-  float *Lp = smem + BAND_ROWS * BX_LD;      // Lp[k * TR_LD + c] = L(j0 + c, k), identity padding
-  float *Rinv = Lp + PANEL_MAX_N * TR_LD;
+  float *Lbuf = smem + BAND_ROWS * BX_LD;    // two Lp buffers, Lp[k * TR_LD + c] = L(j0 + c, k)
+  float *Rinv = Lbuf + 2 * PANEL_MAX_N * TR_LD;
   float *Ps = Rinv + IB;                     // Ps[((part - 1) * BAND_ROWS + row) * PS_LD + c]
   const int tid = threadIdx.x, row = tid & (BAND_ROWS - 1), part = tid >> 6;
   static_assert(NT == 4 * BAND_ROWS, "four threads per row");
   const int nk32 = (nk + IB - 1) / IB * IB;  // columns past nk stay zero
+  trsm_band_stage(Lbuf, L, ldl, 0, nk);
   for (int e = tid; e < BAND_ROWS * nk32; e += NT) {
     const int r = e % BAND_ROWS, c = e / BAND_ROWS;
     Xs[r * BX_LD + c] = (r < rows && c < nk) ? ldcg(B + (int64_t)c * ldb + r) : 0.f;
   }
   for (int j0 = 0; j0 < nk; j0 += IB) {
     const int jb = min(IB, nk - j0);
-    __syncthreads();  // the band's rows are loaded, the previous block is done with Lp
-    for (int e = tid; e < (j0 + IB) * IB; e += NT) {
-      const int c = e & (IB - 1), k = e >> 5;
-      Lp[k * TR_LD + c] =
-          (c < jb && k <= j0 + c) ? ldcg(L + (int64_t)k * ldl + j0 + c) : (k == j0 + c ? 1.f : 0.f);
+    float *Lp = Lbuf + ((j0 / IB) & 1) * PANEL_MAX_N * TR_LD;
+    __syncthreads();  // everyone is done with the other buffer (block j0 - 32)
+    if (j0 + IB < nk) {
+      trsm_band_stage(Lbuf + ((j0 / IB + 1) & 1) * PANEL_MAX_N * TR_LD, L, ldl, j0 + IB, nk);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");  // this block's copies, not the next's
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
-    if (tid < IB) Rinv[tid] = tid < jb ? __frcp_rn(ldcg(L + (int64_t)(j0 + tid) * ldl + j0 + tid)) : 1.f;
+    __syncthreads();  // every thread's copies of this block have landed
+    trsm_band_fix(Lp, Rinv, j0, nk);
     __syncthreads();
     const float *x = Xs + row * BX_LD;
     float acc[IB];

@@ -27,6 +27,28 @@ constexpr int TILE_SMEM_BYTES = (STAGE_DOUBLES + IB * DS_LD + IB) * 8;
 __device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
 __device__ __forceinline__ void stcg(double *p, double v) { __stcg(p, v); }
 
+// One 32-deep k chunk of the 4 x 4 register tile: acc[i][j] += a[i] b[j] with a[i] the rows
+// tx + 16 i, b[j] the columns ty + 16 j of the block. DIAG (a diagonal block of a lower
+// update): rows tx + 16 i and columns ty + 16 j with i < j never meet row >= column (tx, ty <
+// 16), so those six chains are left out -- their values would not be stored -- and the FP64
+// pipe, which a predicated-off instruction would still occupy, does 10 of 16 FMAs per step.
+template <bool DIAG>
+__device__ __forceinline__ void mac_chunk(double (&acc)[4][4], const double *as, const double *bs, int tx, int ty) {
+#pragma unroll 8
+  for (int kk = 0; kk < BK; ++kk) {
+    double a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = as[kk * BM + tx + 16 * i];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) b[j] = bs[kk * BN + ty + 16 * j];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (!DIAG || i >= j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+  }
+}
+
 // C[M x N] -= A[M x K] * op(B), column-major: op(B) = B^T with B N x K (B_KN = false), or
 // op(B) = B with B K x N (B_KN = true, the form of the LU updates). With `lower`, only
 // elements with row >= column (relative to C) are written and blocks wholly above the
@@ -86,18 +108,8 @@ static __device__ __noinline__ void update_core(double *C, int64_t ldc, const do
         }
         const double *as = As + buf * BK * BM;
         const double *bs = Bs + buf * BK * BN;
-#pragma unroll 8
-        for (int kk = 0; kk < BK; ++kk) {
-          double a[4], b[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) a[i] = as[kk * BM + tx + 16 * i];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) b[j] = bs[kk * BN + ty + 16 * j];
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-        }
+        if (lower && bm == bn) mac_chunk<true>(acc, as, bs, tx, ty);  // uniform over the block
+        else mac_chunk<false>(acc, as, bs, tx, ty);
         if (more) {
           double *an = As + (buf ^ 1) * BK * BM;
           double *bnx = Bs + (buf ^ 1) * BK * BN;

@@ -255,3 +255,19 @@ def test_lowp_factor_split_and_kept_bitwise(chol, precision):
                     assert oracle.rel_frobenius(L.astype(np.float64), oracle.factor(A)) <= tol
                 else:
                     np.testing.assert_array_equal(L, ref, err_msg=str((split, keep, nw)))
+
+
+@pytest.mark.parametrize("precision,nb", [("f32", 77), ("bf16x3", 80)])
+def test_lowp_factor_odd_tile_and_leading_dimension(chol, precision, nb):
+    # lda 503 (and tile 77): the band TRSM's 16-byte asynchronous copies of L cannot start on
+    # 16-byte boundaries everywhere and fall back to plain loads piece by piece
+    n, lda = 500, 503
+    L, A = synth.integer_factor(n, seed=12)
+    buf = torch.zeros(n, lda, dtype=torch.float32, device="cuda")   # column j at buf[j, :]
+    buf[:, :n] = torch.from_numpy(A.T.astype(np.float32)).to("cuda")
+    Ad = buf.t()[:n, :]                                              # n x n view, stride (1, lda)
+    assert Ad.stride() == (1, lda)
+    info, _ = chol.factor_f32(Ad, chol.opts(nb=nb), precision=precision)
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    np.testing.assert_array_equal(np.tril(Ad.cpu().numpy().astype(np.float64)), L)
