@@ -71,7 +71,9 @@ typedef struct {
   int dada_max_iter;      /* bisection steps of Algorithm 2; 0 = 16 */
   double dada_eps;        /* stop when upper - lower <= dada_eps * first upper; 0 = 0.01 */
   long long cost_ns[4];   /* predicted time of one POTRF, TRSM, SYRK, GEMM tile task (ns);
-                             0 = derived from the task's flops at 7.5 GFLOP/s per worker */
+                             0 = derived from the task's flops and a per-kind rate per SM (FP64:
+                             7.5 GFLOP/s; FP32 forms: see chol_factor_lowp), divided among
+                             the workers of an SM */
   long long timeout_ns;   /* a device wait that sees no progress for this long gives up and
                              writes CHOL_INFO_TIMEOUT; 0 = 10 s */
   int trace;              /* 1: record per task (worker, queue, start ns, end ns) */
@@ -191,8 +193,10 @@ chol_status chol_factor_f32(int n, float *dA, int lda, const chol_opts *opts, vo
 
 /* chol_factor_f32 with the tile bodies of `precision` (CHOL_F32, CHOL_BF16 or CHOL_BF16X3;
  * others return CHOL_ERR_INVALID_ARG), workspace chol_factor_lowp_workspace_size. A wait of the
- * tensor-core update
- * that exceeds its 2 s limit ends the call with *dInfo = CHOL_INFO_TIMEOUT. */
+ * tensor-core update that exceeds its 2 s limit ends the call with *dInfo = CHOL_INFO_TIMEOUT.
+ * Default task costs (chol_opts.cost_ns = 0) come from per-SM rates measured on these bodies:
+ * 40 (POTRF), 60 (TRSM), 140 (FFMA SYRK; 1000 on the tensor cores with one term) and
+ * 250 / 1000 / 730 (GEMM: FFMA / one term / three terms) GFLOP/s. */
 chol_status chol_factor_lowp(int precision, int n, float *dA, int lda, const chol_opts *opts, void *dWork,
                              size_t work_bytes, int *dInfo, void *stream);
 /* Workspace of chol_factor_lowp in `precision`. For the BF16 forms with a tile size that is a

@@ -1110,19 +1110,28 @@ static bool resolve(int n, const chol_opts *opts, Resolved &r, int prec = PREC_F
   r.max_iter = o.dada_max_iter > 0 ? o.dada_max_iter : 16;
   r.eps = o.dada_eps > 0.0 ? o.dada_eps : 0.01;
   const double nb = (double)r.nb;
-  // predicted rate per worker (GFLOP/s = flop per ns): FP64 DFMA ~7.5 per SM, FP32 FFMA tile
-  // bodies ~300, tensor-core updates ~700 (one BF16 term) and ~500 (three terms)
-  const double per_sm = prec == PREC_F64 || prec == PREC_LU_F64 ? 7.5
-                        : prec == PREC_F32                      ? 300.0
-                        : prec == PREC_BF16                     ? 700.0
-                                                                : 500.0;
-  const double rate = per_sm / (double)r.wps;
+  // predicted rate per SM of each kind (GFLOP/s = flop per ns), from the tile bodies' measured
+  // times: FP64 DFMA bodies ~7.5 for every kind; the FP32 forms' POTRF and TRSM are dependent
+  // chains (~40 and ~60), FFMA SYRK ~140, FFMA GEMM ~250, tensor-core updates ~1000 (one BF16
+  // term, SYRK and GEMM) and ~730 (three terms, GEMM only: its SYRKs run on FFMA). Equal
+  // predictions for TRSM and SYRK would tie the bottom levels of the critical TRSM(k+1, k) and
+  // the previous step's SYRK(k+1, k-1), and the tie would go to the older task.
+  double per_sm[4];
+  if (prec == PREC_F64 || prec == PREC_LU_F64) {
+    for (int k = 0; k < 4; ++k) per_sm[k] = 7.5;
+  } else {
+    per_sm[0] = 40.0;
+    per_sm[1] = 60.0;
+    per_sm[2] = prec == PREC_BF16 ? 1000.0 : 140.0;
+    per_sm[3] = prec == PREC_F32 ? 250.0 : prec == PREC_BF16 ? 1000.0 : 730.0;
+  }
   // per kind: POTRF/TRSM/SYRK/GEMM, or GETRF/GESSM/TSTRF/SSSSM
   const double chol_flops[4] = {nb * nb * nb / 3.0, nb * nb * nb, nb * nb * nb, 2.0 * nb * nb * nb};
   const double lu_flops[4] = {2.0 * nb * nb * nb / 3.0, nb * nb * nb, nb * nb * nb, 2.0 * nb * nb * nb};
   const double *flops = r.lu ? lu_flops : chol_flops;
   for (int k = 0; k < 4; ++k) {
     if (o.cost_ns[k] < 0) return false;
+    const double rate = per_sm[k] / (double)r.wps;
     r.cost[k] = o.cost_ns[k] > 0 ? o.cost_ns[k] : std::max<int64_t>(1, (int64_t)(flops[k] / rate));
   }
   r.timeout_ns = o.timeout_ns > 0 ? o.timeout_ns : 10000000000ll;

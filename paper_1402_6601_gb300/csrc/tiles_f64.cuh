@@ -32,21 +32,43 @@ __device__ __forceinline__ void stcg(double *p, double v) { __stcg(p, v); }
 // update): rows tx + 16 i and columns ty + 16 j with i < j never meet row >= column (tx, ty <
 // 16), so those six chains are left out -- their values would not be stored -- and the FP64
 // pipe, which a predicated-off instruction would still occupy, does 10 of 16 FMAs per step.
-template <bool DIAG>
+// NI, NJ: the 16-row / 16-column groups of the block that hold rows < M / columns < N (the
+// last block of a ragged update has fewer); the chains of the other groups are left out too.
+template <bool DIAG, int NI, int NJ>
 __device__ __forceinline__ void mac_chunk(double (&acc)[4][4], const double *as, const double *bs, int tx, int ty) {
 #pragma unroll 8
   for (int kk = 0; kk < BK; ++kk) {
     double a[4], b[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) a[i] = as[kk * BM + tx + 16 * i];
+    for (int i = 0; i < NI; ++i) a[i] = as[kk * BM + tx + 16 * i];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) b[j] = bs[kk * BN + ty + 16 * j];
+    for (int j = 0; j < NJ; ++j) b[j] = bs[kk * BN + ty + 16 * j];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < NI; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
+      for (int j = 0; j < NJ; ++j)
         if (!DIAG || i >= j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
   }
+}
+
+// mac_chunk for the block's live groups (block-uniform: no divergence)
+template <bool DIAG>
+__device__ __forceinline__ void mac_chunk_live(double (&acc)[4][4], const double *as, const double *bs, int tx,
+                                               int ty, int ni, int nj) {
+#define CHOL_MAC_NJ(NI)                                                          \
+  switch (nj) {                                                                  \
+    case 1: mac_chunk<DIAG, NI, 1>(acc, as, bs, tx, ty); break;                  \
+    case 2: mac_chunk<DIAG, NI, 2>(acc, as, bs, tx, ty); break;                  \
+    case 3: mac_chunk<DIAG, NI, 3>(acc, as, bs, tx, ty); break;                  \
+    default: mac_chunk<DIAG, NI, 4>(acc, as, bs, tx, ty); break;                 \
+  }
+  switch (ni) {
+    case 1: CHOL_MAC_NJ(1) break;
+    case 2: CHOL_MAC_NJ(2) break;
+    case 3: CHOL_MAC_NJ(3) break;
+    default: CHOL_MAC_NJ(4) break;
+  }
+#undef CHOL_MAC_NJ
 }
 
 // C[M x N] -= A[M x K] * op(B), column-major: op(B) = B^T with B N x K (B_KN = false), or
@@ -73,6 +95,7 @@ static __device__ __noinline__ void update_core(double *C, int64_t ldc, const do
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
       double ra[8], rb[8];
       const bool arow = bm + lrow < M, brow = bn + lrow < N;
+      const int ni = min(4, (M - bm + 15) / 16), nj = min(4, (N - bn + 15) / 16);  // live groups
       const double *Ap = A + bm + lrow;
       const double *Bp = B_KN ? B + (int64_t)(bn + ncol_b) * ldb + kk_b : B + bn + lrow;
 #pragma unroll
@@ -108,8 +131,8 @@ static __device__ __noinline__ void update_core(double *C, int64_t ldc, const do
         }
         const double *as = As + buf * BK * BM;
         const double *bs = Bs + buf * BK * BN;
-        if (lower && bm == bn) mac_chunk<true>(acc, as, bs, tx, ty);  // uniform over the block
-        else mac_chunk<false>(acc, as, bs, tx, ty);
+        if (lower && bm == bn) mac_chunk_live<true>(acc, as, bs, tx, ty, ni, nj);  // uniform over the block
+        else mac_chunk_live<false>(acc, as, bs, tx, ty, ni, nj);
         if (more) {
           double *an = As + (buf ^ 1) * BK * BM;
           double *bnx = Bs + (buf ^ 1) * BK * BN;
