@@ -102,6 +102,9 @@ def parse():
     p.add_argument("--no-mixed-oracle", action="store_true",
                    help="skip the oracle's FP64 solution of the mixed-precision configuration (about a minute "
                         "on 16 host cores)")
+    p.add_argument("--legs", default="main,mixed,batched,adjoint,lu",
+                   help="comma-separated legs to run (main = the FP64 factor + solve line); without main "
+                        "the other legs' results are printed alone, e.g. to profile one leg")
     p.add_argument("--bf16-pcg", action="store_true",
                    help="also measure plain BF16 as a preconditioner: conjugate gradients in FP64 preconditioned "
                         "by the shifted BF16 tensor-core factor, on the mixed-precision configuration")
@@ -359,6 +362,23 @@ def main():
             dist.destroy_process_group()
         return
 
+    legs = set(x.strip() for x in args.legs.split(",") if x.strip())
+    if "main" not in legs:
+        if rank == 0:
+            out = {}
+            if "mixed" in legs:
+                out["mixed_precision"] = run_mixed(args, chol, dev)
+            if "batched" in legs:
+                out["batched"] = run_batched(args, chol, dev)
+            if "adjoint" in legs:
+                out["adjoint"] = run_adjoint(args, chol, dev)
+            if "lu" in legs:
+                out["lu"] = run_lu(args, chol, dev)
+            print(json.dumps({"legs": out}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
     n, nb, nrhs = args.n, args.nb, args.nrhs
     o = chol.opts(nb=nb, policy=args.policy, alpha=args.alpha, workers_per_sm=args.workers_per_sm,
                   use_cp=args.cp)
@@ -435,19 +455,19 @@ def main():
 
     del A, B, work, R
     mixed = None
-    if not args.no_mixed and rank == 0:
+    if not args.no_mixed and "mixed" in legs and rank == 0:
         mixed = run_mixed(args, chol, dev)
     batched = None
-    if not args.no_batched and rank == 0:
+    if not args.no_batched and "batched" in legs and rank == 0:
         batched = run_batched(args, chol, dev)
     adjoint = None
-    if not args.no_adjoint and rank == 0:
+    if not args.no_adjoint and "adjoint" in legs and rank == 0:
         adjoint = run_adjoint(args, chol, dev)
     pcg = None
     if args.bf16_pcg and rank == 0:
         pcg = run_bf16_pcg(args, chol, dev)
     lu = None
-    if not args.no_lu and rank == 0:
+    if not args.no_lu and "lu" in legs and rank == 0:
         lu = run_lu(args, chol, dev)
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:

@@ -84,13 +84,14 @@ typedef struct {
                              a task placed on a worker that did not write one of its input
                              tiles last pays that tile's bytes / cp_gbs (Section 4.1) */
   double cp_gbs;          /* bandwidth per worker for that prediction, GB/s; 0 = 40 */
-  int split;              /* FP64 factor: 0 = every task runs on one worker; 1 (default) = the
-                             TRSM and SYRK tasks of the next panel (tile row k + 1, the tasks on
-                             the critical path), and any TRSM, SYRK or GEMM that starts while
-                             SMs idle with no queued task for them, are cut into 64-row (TRSM)
-                             or 64 x 64 (SYRK, GEMM) units that idle workers take before their
-                             own queues; 2 = every TRSM, SYRK and GEMM. The factor is bitwise
-                             the same in every mode */
+  int split;              /* 0 = every task runs on one worker; 1 (default) = the TRSMs of tile
+                             rows k + 1 and k + 2 and the SYRK of tile row k + 1 (the critical
+                             path), and any TRSM, SYRK or GEMM that starts while SMs idle with no
+                             queued task for them, are cut into units -- 64-row TRSM bands,
+                             64 x 64 (FP64) or 128 x 128 (FP32 FFMA) SYRK / GEMM blocks; the
+                             tensor-core updates stay whole -- that idle workers take before
+                             their own queues; 2 = every TRSM, SYRK and GEMM. The factor is
+                             bitwise the same in every mode */
   int keep_next;          /* HEFT and DADA with priority queues: 1 (default) = a worker that
                              completes a task runs the most urgent task it made ready next when
                              that task outranks everything queued on it (it would be popped

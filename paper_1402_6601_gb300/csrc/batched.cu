@@ -62,6 +62,16 @@ __global__ void __launch_bounds__(1024) batch_order_kernel(int batch, const int 
   }
 }
 
+// b / d from r = RN(1/d) with one Markstein correction: the correctly rounded quotient (the
+// same value as b / d) in three dependent operations after r, which is taken for all 32
+// diagonal entries of a block at once, off the substitution's chain.
+template <class T>
+__device__ __forceinline__ T bquot(T b, T d, T r) {
+  const T x = b * r;
+  const T e = fma(-x, d, b);
+  return fma(e, r, x);
+}
+
 // Forward and back substitution L L^T x = b for one matrix by the whole block; b in place.
 // 32-row blocks: warp 0 solves the diagonal block (lanes = rows, x_k broadcast by shuffle),
 // then all threads update the remaining rows with that block's columns.
@@ -74,9 +84,11 @@ __device__ void block_solve_vec(const T *L, int64_t lda, int n, T *b, T *xs) {
     const int pb = min(32, n - p);
     if (tid < 32) {
       T y = lane < pb ? xs[p + lane] : T(0);
+      const T dl = lane < pb ? L[(int64_t)(p + lane) * lda + p + lane] : T(1);
+      const T rl = T(1) / dl;
       for (int k = 0; k < pb; ++k) {
-        const T lkk = L[(int64_t)(p + k) * lda + p + k];
-        const T yk = __shfl_sync(0xffffffffu, y, k) / lkk;
+        const T yk = bquot(__shfl_sync(0xffffffffu, y, k), __shfl_sync(0xffffffffu, dl, k),
+                           __shfl_sync(0xffffffffu, rl, k));
         if (lane == k) y = yk;
         else if (lane > k && lane < pb) y = fma(-L[(int64_t)(p + k) * lda + p + lane], yk, y);
       }
@@ -94,9 +106,11 @@ __device__ void block_solve_vec(const T *L, int64_t lda, int n, T *b, T *xs) {
     const int pb = min(32, n - p0);
     if (tid < 32) {
       T x = lane < pb ? xs[p0 + lane] : T(0);
+      const T dl = lane < pb ? L[(int64_t)(p0 + lane) * lda + p0 + lane] : T(1);
+      const T rl = T(1) / dl;
       for (int k = pb - 1; k >= 0; --k) {
-        const T lkk = L[(int64_t)(p0 + k) * lda + p0 + k];
-        const T xk = __shfl_sync(0xffffffffu, x, k) / lkk;
+        const T xk = bquot(__shfl_sync(0xffffffffu, x, k), __shfl_sync(0xffffffffu, dl, k),
+                           __shfl_sync(0xffffffffu, rl, k));
         if (lane == k) x = xk;
         else if (lane < k) x = fma(-L[(int64_t)(p0 + lane) * lda + p0 + k], xk, x);
       }

@@ -712,9 +712,12 @@ __device__ __forceinline__ int split_units(const FactorArgs &a, const TaskDesc &
   return nbi * ((tile_dim(a, d.j) + P::UPD_UNIT - 1) / P::UPD_UNIT);
 }
 
-// Mode 1: the next panel's TRSM and SYRK (tile row k + 1, on the critical path), and any
-// TRSM, SYRK or GEMM that starts while SMs run no task and no queued task is left for them
-// (`starving`: the end of the factor, or small matrices). Mode 2: every TRSM, SYRK and GEMM.
+// Mode 1: the TRSMs of tile rows k + 1 and k + 2 and the SYRK of tile row k + 1 -- the chain
+// POTRF(k) -> TRSM(k+1, k) -> SYRK(k+1, k) -> POTRF(k+1), and the path POTRF(k) -> TRSM(k+2, k)
+// -> GEMM(k+2, k+1, k) -> TRSM(k+2, k+1) beside it, which is as long once the chain's own tasks
+// are split -- and any TRSM, SYRK or GEMM that starts while SMs run no task and no queued task
+// is left for them (`starving`: the end of the factor, or small matrices). Mode 2: every TRSM,
+// SYRK and GEMM.
 template <class P>
 __device__ __forceinline__ bool should_split(const FactorArgs &a, const TaskDesc &d, bool starving) {
   if (!a.split_mode || d.kind == K_POTRF) return false;
@@ -723,7 +726,7 @@ __device__ __forceinline__ bool should_split(const FactorArgs &a, const TaskDesc
     return false;
   if (split_units<P>(a, d) < 2 || split_units<P>(a, d) > 255) return false;
   if (a.split_mode == 2) return true;
-  if ((d.kind == K_TRSM || d.kind == K_SYRK) && d.i == d.k + 1) return true;
+  if ((d.kind == K_TRSM && d.i <= d.k + 2) || (d.kind == K_SYRK && d.i == d.k + 1)) return true;
   return starving;
 }
 
@@ -943,10 +946,20 @@ __global__ void __launch_bounds__(NT, P::MIN_BLOCKS) factor_kernel(const __grid_
       hd.i = ld_volatile(&h->i);
       hd.j = ld_volatile(&h->j);
       hd.k = ld_volatile(&h->k);
+      if (threadIdx.x == 0) {
+        // busy for about one unit's share of the task: the placement's load model must not
+        // take a helping worker for an idle one
+        const int units = (int)((ld_volatile(&h->word) >> 32) & 0xffull);
+        const uint64_t c = (uint64_t)a.cost[hd.kind] / (uint64_t)(units > 0 ? units : 1);
+        *(volatile unsigned long long *)&a.run_end[wid] = globaltimer_ns() + c;
+      }
       Runner<P>::unit(a, hd, s_hunit, smem);
       __threadfence();
       __syncthreads();
-      if (threadIdx.x == 0) atomicAdd(&a.board[s_hslot].done, 1);
+      if (threadIdx.x == 0) {
+        *(volatile unsigned long long *)&a.run_end[wid] = 0ull;
+        atomicAdd(&a.board[s_hslot].done, 1);
+      }
       continue;
     }
     if (id < 0) break;
