@@ -545,6 +545,7 @@ struct TilesF64 {
   static constexpr bool CAN_SPLIT = true;  // TRSM, SYRK and GEMM tasks can be cut into units
   static constexpr int UPD_UNIT = 64;       // SYRK / GEMM units: the update's 64 x 64 blocks
   static constexpr bool SPLIT_TRSM = true, SPLIT_SYRK = true, SPLIT_GEMM = true;
+  static constexpr bool SPLIT_EVERY_TRSM = false;
   static constexpr int SMEM = TILE_SMEM_BYTES;
   static constexpr int MIN_BLOCKS = 2;  // two workers per SM share the FP64 pipe
   __device__ static int potrf(T *G, int64_t ld, int nk, T *s) { return potrf_tile(G, ld, nk, s); }
@@ -575,6 +576,9 @@ struct TilesF32 {
   static constexpr bool CAN_SPLIT = true;
   static constexpr int UPD_UNIT = 128;      // the FFMA update's 128 x 128 blocks
   static constexpr bool SPLIT_TRSM = true, SPLIT_SYRK = true, SPLIT_GEMM = true;
+  // a whole FP32 TRSM is its 64-row bands one after another, so every TRSM is handed out band
+  // by band (mode 1): same work, and no long TRSM lands on a critical path
+  static constexpr bool SPLIT_EVERY_TRSM = true;
   static_assert(f32::TRSM_BAND_SMEM_BYTES <= (f32::PANEL_SMEM_BYTES > f32::TILE_SMEM_BYTES ? f32::PANEL_SMEM_BYTES
                                                                                          : f32::TILE_SMEM_BYTES),
                 "the band TRSM must fit the FP32 bodies' shared memory");
@@ -684,6 +688,7 @@ struct LuF64 {
   static constexpr bool CAN_SPLIT = false;  // (the LU graph has its own runner)
   static constexpr int UPD_UNIT = 64;
   static constexpr bool SPLIT_TRSM = false, SPLIT_SYRK = false, SPLIT_GEMM = false;
+  static constexpr bool SPLIT_EVERY_TRSM = false;
   static constexpr int SMEM = LU_SMEM_BYTES;
   static constexpr int MIN_BLOCKS = 2;
   __device__ static void begin() {}
@@ -726,7 +731,8 @@ __device__ __forceinline__ bool should_split(const FactorArgs &a, const TaskDesc
     return false;
   if (split_units<P>(a, d) < 2 || split_units<P>(a, d) > 255) return false;
   if (a.split_mode == 2) return true;
-  if ((d.kind == K_TRSM && d.i <= d.k + 2) || (d.kind == K_SYRK && d.i == d.k + 1)) return true;
+  if ((d.kind == K_TRSM && (d.i <= d.k + 2 || P::SPLIT_EVERY_TRSM)) || (d.kind == K_SYRK && d.i == d.k + 1))
+    return true;
   return starving;
 }
 
