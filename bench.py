@@ -222,17 +222,28 @@ def run_fp64_probe(chol, dev, target_ms=150.0, reps=5):
         return f, e0.elapsed_time(e1)
 
     for name, kind in PROBE_KINDS:
-        blocks = sms * (4 if kind == 0 else 2)
-        iters = 2000
-        _, t = once(kind, blocks, iters)
-        iters = max(1, int(iters * target_ms / max(t, 1e-3)))
-        once(kind, blocks, iters)
-        runs = [once(kind, blocks, iters) for _ in range(reps)]
-        f = runs[0][0]
-        ms = [t for _, t in runs]
-        res[name] = {"gflops_best": round(f / min(ms) / 1e6, 1), "gflops": stat([f / t / 1e6 for t in ms], 1),
-                     "ms": round(sum(ms) / len(ms), 2), "blocks": blocks, "threads": 256, "iters": iters,
-                     "flops_per_launch": f}
+        # 256-thread blocks, 1, 2 or 4 per SM (a whole number per SM; the MMA kernel's registers
+        # allow two): the best of the grids is the unit's rate
+        best = None
+        for per_sm in ((1, 2, 4) if kind == 0 else (1, 2)):
+            blocks = sms * per_sm
+            iters = 2000
+            _, t = once(kind, blocks, iters)
+            iters = max(1, int(iters * target_ms / max(t, 1e-3)))
+            once(kind, blocks, iters)
+            runs = [once(kind, blocks, iters) for _ in range(reps)]
+            f = runs[0][0]
+            ms = [t for _, t in runs]
+            v = {"gflops_best": round(f / min(ms) / 1e6, 1), "gflops": stat([f / t / 1e6 for t in ms], 1),
+                 "ms": round(sum(ms) / len(ms), 2), "blocks": blocks, "threads": 256, "iters": iters,
+                 "flops_per_launch": f}
+            v["by_blocks_per_sm"] = dict(best["by_blocks_per_sm"]) if best else {}
+            v["by_blocks_per_sm"][str(per_sm)] = v["gflops_best"]
+            if best is None or v["gflops_best"] > best["gflops_best"]:
+                best = v
+            else:
+                best["by_blocks_per_sm"] = v["by_blocks_per_sm"]
+        res[name] = best
     clk = clocks.stop()
     med, mx = clk.get("sm_mhz"), clk.get("sm_max_mhz") or SM_MAX_MHZ
     for v in res.values():
@@ -718,7 +729,7 @@ def run_lu(args, chol, dev):
     import torch
     import synth
     n = args.lu_n
-    o = chol.opts(nb=args.lu_nb, policy=args.lu_policy, alpha=args.alpha)
+    o = chol.opts(nb=args.lu_nb, policy=args.lu_policy, alpha=args.alpha, use_cp=args.cp)
     A0 = chol.colmajor(synth.general_matrix(n, seed=args.seed + 11, device=dev))
     A = torch.empty_like(A0)
     work = torch.empty(chol.lu_workspace_size(n, o), dtype=torch.uint8, device=dev)
@@ -776,8 +787,9 @@ def run_lu(args, chol, dev):
     gf = 2.0 * n ** 3 / 3.0 / (t / 1000.0) / 1e9
     T = -(-n // (o.nb if o.nb else (128 if n <= 32768 else 256)))
     return {"workload": "tile LU with incremental pivoting (GETRF/GESSM/TSTRF/SSSSM), n=%d, tile %s, inner "
-                        "block 32, %s ready queues; A with i.i.d. N(0,1) entries" % (
-                            n, o.nb or "auto", args.lu_policy.upper()),
+                        "block 32, %s%s ready queues; A with i.i.d. N(0,1) entries" % (
+                            n, o.nb or "auto", args.lu_policy.upper(),
+                            ("(%g)" % args.alpha if args.lu_policy == "dada" else "") + ("+CP" if args.cp else "")),
             "factor_ms": round(t, 2), "factor_ms_stat": stat(ms, 3), "gflops": round(gf, 1), "flops": "2n^3/3",
             "frac_of_fp64_peak": round(gf / FP64_PEAK_GFLOPS, 4), "tiles": T,
             "tasks": int(chol.lib.chol_lu_dag_task_count(T)),
