@@ -61,7 +61,8 @@ def stat(xs, digits=3):
     return {"mean": round(m, digits), "ci95": None if h is None else round(h, digits), "n": k}
 
 
-PROBE_KINDS = (("dfma", 0), ("mma_m8n8k4", 1), ("mma_m16n8k4", 2), ("mma_m16n8k8", 3), ("mma_m16n8k16", 4))
+PROBE_KINDS = (("dfma", 0), ("dfma_free_operands", 5), ("dfma_smem_tile", 6), ("mma_m8n8k4", 1),
+               ("mma_m16n8k4", 2), ("mma_m16n8k8", 3), ("mma_m16n8k16", 4))
 
 
 def parse():
@@ -225,7 +226,7 @@ def run_fp64_probe(chol, dev, target_ms=150.0, reps=5):
         # 256-thread blocks, 1, 2 or 4 per SM (a whole number per SM; the MMA kernel's registers
         # allow two): the best of the grids is the unit's rate
         best = None
-        for per_sm in ((1, 2, 4) if kind == 0 else (1, 2)):
+        for per_sm in ((1, 2, 4) if kind in (0, 5, 6) else (1, 2)):
             blocks = sms * per_sm
             iters = 2000
             _, t = once(kind, blocks, iters)

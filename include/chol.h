@@ -422,7 +422,9 @@ chol_status chol_sched_activate_device(int policy, double alpha, int max_iter, d
 /* ---------------------------------------------------------------------------------------
  * Measurement support (not part of the method): throughput probes of the FP64 units, the
  * denominator of the FP64 factor's roofline. Kind 0 keeps every thread on 16 independent
- * DFMA chains, a 4 x 4 register tile as in the FP64 tile bodies; kinds 1-4 keep every warp
+ * DFMA chains, a 4 x 4 register tile over fixed operands; kind 5 on 16 chains with operands
+ * of their own; kind 6 on the 4 x 4 tile fed from shared memory as in the FP64 tile update
+ * (iterations rounded up to 32, 256 threads); kinds 1-4 keep every warp
  * on 8 independent chains of FP64 warp MMAs, mma.sync shapes m8n8k4, m16n8k4, m16n8k8 and
  * m16n8k16. `iters` iterations per chain, grid `blocks` x `threads` (32..256, a multiple of
  * 32). chol_probe_fp64_flops returns the flops of such a launch (-1 for invalid arguments);

@@ -788,7 +788,8 @@ def lu_solve(f, B, work=None, info=None, stream=None, check=False):
             raise CholeskyError("chol_lu_solve: info %d" % int(info.item()))
     return info
 
-PROBE_KINDS = {"dfma": 0, "mma_m8n8k4": 1, "mma_m16n8k4": 2, "mma_m16n8k8": 3, "mma_m16n8k16": 4}
+PROBE_KINDS = {"dfma": 0, "mma_m8n8k4": 1, "mma_m16n8k4": 2, "mma_m16n8k8": 3, "mma_m16n8k16": 4,
+               "dfma_free_operands": 5, "dfma_smem_tile": 6}
 
 
 def probe_fp64(kind, blocks, threads=256, iters=1000, out=None, stream=None):

@@ -42,6 +42,63 @@ __global__ void __launch_bounds__(256) probe_dfma_kernel(long long iters, double
   if (s == -1.0) out[0] = s;  // never true (every accumulator stays >= 1)
 }
 
+// DFMA with every chain on its own three registers: x_c <- x_c y_c + z_c (y_c = 1 - 2^-20 c',
+// z_c small), so no two FMAs of an iteration read a common operand register.
+__global__ void __launch_bounds__(256) probe_dfma_free_kernel(long long iters, double x, double y, double *out) {
+  double a[16], m[16], c[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    a[i] = 1.0 + 1e-3 * i + 1e-9 * threadIdx.x;
+    m[i] = x - y * (double)i;
+    c[i] = y * (1.0 + 0.0625 * i);
+  }
+  for (long long it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) a[i] = fma(a[i], m[i], c[i]);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) s += a[i];
+  if (s == -1.0) out[0] = s;  // never true (every chain stays near its fixed point, about 1)
+}
+
+// DFMA fed from shared memory as in the FP64 tile update: per step every thread reads four
+// rows of A and four columns of B (k-major 32 x 64 panels) and updates its 4 x 4 register tile.
+__global__ void __launch_bounds__(256) probe_dfma_smem_kernel(long long iters, double x, double y, double *out) {
+  __shared__ double As[32 * 64], Bs[32 * 64];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int e = tid; e < 32 * 64; e += 256) {
+    As[e] = y * (1.0 + 1e-3 * (e & 63));
+    Bs[e] = x * y * (1.0 + 1e-3 * (e >> 6));
+  }
+  __syncthreads();
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 1.0;
+  for (long long it = 0; it < iters; it += 32) {
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk * 64 + tx + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk * 64 + ty + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s += acc[i][j];
+  if (s == -1.0) out[0] = s;  // never true (every accumulator stays >= 1)
+}
+
 // Per shape: fragment sizes (doubles per thread) of A, B and C/D, and M, N, K.
 template <int KIND>
 struct MmaShape;
@@ -128,7 +185,8 @@ using namespace chol;
 
 extern "C" long long chol_probe_fp64_flops(int kind, int blocks, int threads, long long iters) {
   if (blocks < 1 || threads < 32 || threads > 256 || threads % 32 || iters < 0) return -1;
-  if (kind == 0) return 2ll * 16 * iters * threads * (long long)blocks;
+  if (kind == 0 || kind == 5) return 2ll * 16 * iters * threads * (long long)blocks;
+  if (kind == 6) return 2ll * 16 * ((iters + 31) / 32 * 32) * threads * (long long)blocks;
   const long long per = mma_flops_per_warp_iter(kind);
   if (per == 0) return -1;
   return per * iters * (threads / 32) * (long long)blocks;
@@ -144,10 +202,16 @@ extern "C" chol_status chol_probe_fp64(int kind, int blocks, int threads, long l
   const double x = 1.0 - 0x1p-20, y = 0x1p-20;
   switch (kind) {
     case 0: probe_dfma_kernel<<<blocks, threads, 0, s>>>(iters, x, y, dOut); break;
+    case 5: probe_dfma_free_kernel<<<blocks, threads, 0, s>>>(iters, x, y, dOut); break;
+    case 6:
+      if (threads != 256) return CHOL_ERR_INVALID_ARG;  // the 16 x 16 thread tile
+      probe_dfma_smem_kernel<<<blocks, threads, 0, s>>>(iters, x, y, dOut);
+      break;
     case 1: probe_mma_kernel<1><<<blocks, threads, 0, s>>>(iters, x, y, dOut); break;
     case 2: probe_mma_kernel<2><<<blocks, threads, 0, s>>>(iters, x, y, dOut); break;
     case 3: probe_mma_kernel<3><<<blocks, threads, 0, s>>>(iters, x, y, dOut); break;
-    default: probe_mma_kernel<4><<<blocks, threads, 0, s>>>(iters, x, y, dOut); break;
+    case 4: probe_mma_kernel<4><<<blocks, threads, 0, s>>>(iters, x, y, dOut); break;
+    default: return CHOL_ERR_INVALID_ARG;
   }
   CHOL_CUDA_TRY(cudaGetLastError());
   return CHOL_OK;

@@ -332,8 +332,32 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
 #pragma unroll
         for (int u = 0; u < RPT; ++u) Xo[(i0 + u) * YLD + q] = t[u];
       }
+    } else if (cols <= SNW) {
+      // diagonal block, at most 8 right-hand sides: one warp per right-hand side, lane = row
+      // (see below); kept apart from the two-column form, whose extra state slows the
+      // one-column chain of the LU and refinement solves by ~40 %
+      const int c = warp;
+      if (c < cols) {
+        T x = Ys[lane * YLD + c];
+        const T rinv = Rs[lane];
+        if (!REV) {
+#pragma unroll
+          for (int k = 0; k < SBK; ++k) {
+            if (lane == k) x = squot(x, Ld[k * DLD + k], rinv);
+            const T xk = __shfl_sync(0xffffffffu, x, k);
+            if (lane > k) x = fma(-Ld[lane * DLD + k], xk, x);
+          }
+        } else {
+#pragma unroll
+          for (int k = SBK - 1; k >= 0; --k) {
+            if (lane == k) x = squot(x, Ld[k * DLD + k], rinv);
+            const T xk = __shfl_sync(0xffffffffu, x, k);
+            if (lane < k) x = fma(-Ld[k * DLD + lane], xk, x);
+          }
+        }
+        Ys[lane * YLD + c] = x;
+      }
     } else if (cols <= 2 * SNW) {
-      // (with one right-hand side only warp 0 works and the second column's steps are left out)
       // diagonal block, few right-hand sides: one warp per pair of right-hand sides (columns
       // warp and warp + 8), lane = row. Each step takes x_k on lane k and updates the rows
       // below it with one warp-wide FMA per column (an FP64 instruction costs the SM
