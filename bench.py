@@ -27,14 +27,20 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 SMS = 152
-FP64_FMA_PER_CLK_PER_SM = 2       # measured: DFMA retires 2 FMA/clk/SM on sm_103 (probe ~1197 GFLOP/s)
+FP64_FMA_PER_CLK_PER_SM = 2       # DFMA retires 2 FMA/clk/SM on sm_103 (shared-memory-fed probe: 1256.8 GFLOP/s)
 SM_MAX_MHZ = 2070.0
 FP64_PEAK_GFLOPS = SMS * FP64_FMA_PER_CLK_PER_SM * 2 * SM_MAX_MHZ / 1000.0  # 1258.6
 
-# DRAM bytes (read + write) of one factor launch, from a one-pass ncu capture of this exact
-# configuration (profiles/bench_n32768_nb256_launch_list.txt); None for configurations that
-# were not captured with the current kernel.
-MEASURED_FACTOR_TRAFFIC = {(32768, 256, "heft"): 1003565810432 + 201701767424}
+# DRAM bytes (read + write) of one FP64 factor launch (tile 256, HEFT) from one-metric ncu
+# captures of the current kernel at small sizes (profiles/factor_kernel_f64_dram_traffic_
+# n8192_n12288_n16384.txt). They do not grow in proportion to the work (the L2 hit rate falls
+# as the trailing matrix outgrows L2), so no full-size figure is scaled from them and the
+# roofline's "traffic" stays None at the benchmark size.
+FACTOR_TRAFFIC_SMALL_CASES = [
+    {"n": 8192, "nb": 256, "bytes": 5.18e9, "l2_hit_pct": 88.3},
+    {"n": 12288, "nb": 256, "bytes": 22.52e9, "l2_hit_pct": 84.1},
+    {"n": 16384, "nb": 256, "bytes": 113.33e9, "l2_hit_pct": 58.4},
+]
 
 # two-sided 95 % quantiles of Student's t for 1..30 degrees of freedom
 _T975 = [12.706, 4.303, 3.182, 2.776, 2.571, 2.447, 2.365, 2.306, 2.262, 2.228, 2.201, 2.179, 2.160, 2.145,
@@ -450,7 +456,8 @@ def main():
     fac_stat = stat(fac_ms, 2)
     roofline = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(FP64_PEAK_GFLOPS, 1),
                 "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
-                "traffic": MEASURED_FACTOR_TRAFFIC.get((n, nb, args.policy)),
+                "traffic": None,
+                "traffic_small_cases": FACTOR_TRAFFIC_SMALL_CASES,
                 "kernel": "factor_kernel (persistent data-flow, DFMA tile bodies)",
                 "launch_ms": fac_stat,
                 "achieved_ci95": None if fac_stat["ci95"] is None else round(
