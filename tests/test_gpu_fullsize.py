@@ -130,7 +130,7 @@ def factor8192():
     return A, oracle.factor(A.cpu().numpy())
 
 
-@pytest.mark.parametrize("nb", [256, 128])
+@pytest.mark.parametrize("nb", [256, 128, 512])
 @pytest.mark.parametrize("policy,alpha,cp", [("heft", 0.5, False), ("dada", 0.5, True), ("steal", 0.5, False)])
 def test_factor_n8192_whole_L(chol, factor8192, nb, policy, alpha, cp):
     A, Lo = factor8192
