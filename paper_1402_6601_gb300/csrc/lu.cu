@@ -30,8 +30,10 @@ namespace chol {
 constexpr int LG = 8;                       // right-hand sides per item
 constexpr int LNB = LU_NB_MAX / LU_IB;      // inner blocks per tile, at most
 constexpr int L11LD = LU_IB + 1;
+constexpr int LPOS = LU_IB + LU_NB_MAX;     // positions an inner block's interchanges address
+constexpr int LMOV = 2 * LU_IB;              // moves of one inner block's interchanges, at most
 constexpr int LU_FWD_SMEM_BYTES =
-    (2 * LU_NB_MAX * LG + LNB * LU_IB * L11LD) * 8 + LU_NB_MAX * 4;
+    (2 * LU_NB_MAX * LG + LNB * LU_IB * L11LD) * 8 + LU_NB_MAX * 4 + LNB * LPOS * 2 + LNB * LMOV * 4 + LNB * 4;
 constexpr int LU_FWD_EXCL_SMEM = 120 * 1024;  // request at least this much: one block per SM
 constexpr int LU_FWD_SMEM_REQ = LU_FWD_SMEM_BYTES > LU_FWD_EXCL_SMEM ? LU_FWD_SMEM_BYTES : LU_FWD_EXCL_SMEM;
 
@@ -104,6 +106,9 @@ __global__ void __launch_bounds__(NT, 1) lu_fwd_kernel(const __grid_constant__ L
   double *Yi = Yk + LU_NB_MAX * LG;
   double *L11 = Yi + LU_NB_MAX * LG;                     // [LNB][LU_IB][L11LD] row-major
   int *spiv = reinterpret_cast<int *>(L11 + LNB * LU_IB * L11LD);
+  short *pmap = reinterpret_cast<short *>(spiv + LU_NB_MAX);    // [LNB][LPOS]
+  short2 *moves = reinterpret_cast<short2 *>(pmap + LNB * LPOS); // [LNB][LMOV] (dst, src)
+  int *nmoves = reinterpret_cast<int *>(moves + LNB * LMOV);     // [LNB]
   __shared__ long long s_item;
   __shared__ int s_ok;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -139,6 +144,31 @@ __global__ void __launch_bounds__(NT, 1) lu_fwd_kernel(const __grid_constant__ L
         v = getrf ? __ldcg(Akk + (int64_t)(b * LU_IB + c) * lda + b * LU_IB + r)
                   : __ldcg(lwp + (int64_t)(b * LU_IB + c) * LU_IB + r);
       L11[(b * LU_IB + r) * L11LD + c] = v;
+    }
+    // the interchanges of each inner block as one permutation of the positions they touch
+    // (position p < w: row p of X1, else row p - w of X2): the sequence of swaps is replayed on
+    // position labels, one thread per block, and the moved positions are listed as (dst, src)
+    // pairs -- applied after the wait in one parallel gather instead of w dependent swaps
+    for (int e = tid; e < nblk * LPOS; e += NT) pmap[e] = (short)(e % LPOS);
+    __syncthreads();
+    if (tid < nblk) {
+      const int b = tid, c0 = b * LU_IB, w = min(LU_IB, nk - c0);
+      const int m2 = getrf ? nk - c0 - w : mi;
+      short *mp = pmap + b * LPOS;
+      short2 *mv = moves + b * LMOV;
+      int cnt = 0;
+      for (int j = 0; j < w; ++j) {
+        const int q = spiv[c0 + j];
+        if (q == j || q < 0 || q >= w + m2) continue;
+        const short t = mp[j];
+        mp[j] = mp[q];
+        mp[q] = t;
+        if (q >= w) mv[w + cnt++] = make_short2((short)q, 0);  // X2 positions touched (may repeat)
+      }
+      // X1 positions first (all w of them), then the touched X2 positions
+      for (int j = 0; j < w; ++j) mv[j] = make_short2((short)j, mp[j]);
+      for (int u = 0; u < cnt; ++u) mv[w + u].y = mp[mv[w + u].x];
+      nmoves[b] = w + cnt;
     }
     // row of X2 this thread eliminates in block b: GETRF rows c1 + tid of the diagonal tile,
     // TSTRF row tid of A_ik; its L21 row (w values) is held in registers, the next block's
@@ -187,16 +217,23 @@ __global__ void __launch_bounds__(NT, 1) lu_fwd_kernel(const __grid_constant__ L
       double *X1 = Yk + c0;                      // w rows
       double *X2 = getrf ? Yk + c1 : Yi;         // m2 rows
       if (b + 1 < nblk) load_l21(b + 1, lnext);
-      // interchanges in order, one thread per right-hand side
-      if (tid < gc) {
-        double *x1 = X1 + tid * LU_NB_MAX, *x2 = X2 + tid * LU_NB_MAX;
-        for (int j = 0; j < w; ++j) {
-          const int q = spiv[c0 + j];
-          if (q == j || q < 0 || q >= w + m2) continue;
-          double *o = q < w ? x1 + q : x2 + (q - w);
-          const double t = x1[j];
-          x1[j] = *o;
-          *o = t;
+      // the interchanges: gather every moved position's value, then store them (a repeated
+      // X2 position is written twice with the same value)
+      {
+        const int nm = nmoves[b], tot = nm * gc;
+        const short2 *mv = moves + b * LMOV;
+        auto at = [&](int c, int pos) { return pos < w ? X1 + c * LU_NB_MAX + pos : X2 + c * LU_NB_MAX + (pos - w); };
+        double v[(LMOV * LG + NT - 1) / NT];
+#pragma unroll
+        for (int u = 0; u < (LMOV * LG + NT - 1) / NT; ++u) {
+          const int e = tid + u * NT;
+          if (e < tot) v[u] = *at(e / nm, mv[e % nm].y);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < (LMOV * LG + NT - 1) / NT; ++u) {
+          const int e = tid + u * NT;
+          if (e < tot) *at(e / nm, mv[e % nm].x) = v[u];
         }
       }
       __syncthreads();
