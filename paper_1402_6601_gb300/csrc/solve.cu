@@ -116,6 +116,8 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
   constexpr bool INV = sizeof(T) == 4;  // FP32: multiply by the inverted diagonal block
   constexpr bool TRANS = MODE == 1;     // blocks of L read transposed
   constexpr bool REV = MODE != 0;       // blocks solved from the last one up
+  // FP64 with many right-hand sides: warps split the columns instead of the solved blocks
+  constexpr bool QS = !INV && NC >= 2 * SNW && SBK == 32;
   static_assert(SBK == 32 || (SBK == 64 && INV), "64-row items are for the FP32 sweeps");
   static_assert(MODE != 2 || !INV, "the upper sweep is FP64");
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -127,6 +129,7 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
   T *Mi = Rs + SBK;  // 16-byte aligned: YW, LT, YS and LD are multiples of four elements
   __shared__ long long s_item;
   __shared__ int s_abort;
+  __shared__ T s_xk[2][32];  // x_k of every column, by step parity (diagonal solve)
   const T *L = static_cast<const T *>(a.L);
   T *B = static_cast<T *>(a.B);
   if (a.skip && ld_volatile(a.skip)) return;
@@ -175,135 +178,227 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
         }
       }
     }
-    // this thread's entries of B_r for the final sum, loaded now (off the chain)
-    constexpr int BPT = (SBK * NC + SNT - 1) / SNT;
-    T bv[BPT];
+    if constexpr (QS) {
+      // many right-hand sides (FP64): warp w owns the columns QC w .. QC w + QC - 1 of the group
+      // over every solved block, in solve order, so the newest block's work is spread over all
+      // eight warps instead of falling to one, and each warp's sums are final (no reduction)
+      constexpr int QC = NC / SNW;
+      const int qw = warp * QC;
+      T bq[QC], accq[QC];
 #pragma unroll
-    for (int u = 0; u < BPT; ++u) {
-      const int e = tid + u * SNT, i = e % SBK, q = e / SBK;
-      bv[u] = (e < SBK * NC && i < rows && q < cols) ? __ldcg(B + (int64_t)(c0 + q) * a.ldb + r0 + i) : T(0);
-    }
-    // warp-parallel accumulation over the solved blocks
-    T acc[RPL][NC];
-#pragma unroll
-    for (int rr = 0; rr < RPL; ++rr)
-#pragma unroll
-      for (int q = 0; q < NC; ++q) acc[rr][q] = T(0);
-    const int nsteps = REV ? a.nrb - 1 - r : r;
-    // the solved blocks are consumed in 32-row chunks, one chunk per warp step: chunk kc of
-    // block m is step m * RPL + kc, so the chunks of the newest block go to different warps
-    const int nchunks = nsteps * RPL;
-    int wab = 0;
-    // readiness of the warp's next 32 chunks: bit j <-> step mbase + SNW j, one flag load per
-    // lane and a ballot, so blocks solved long ago cost no polling round trip
-    unsigned ready = 0u;
-    int mbase = warp;
-    for (int step = warp; step < nchunks; step += SNW) {
-      const int mi = step / RPL, kc = step % RPL;
-      const int m = REV ? a.nrb - 1 - mi : mi;
-      const int k0 = m * SBK + SB * kc, krows = min(SB, a.n - k0);  // this 32-row chunk of block m
-      // L chunk, issued before any wait (it does not depend on other items). Forward: lane =
-      // row of the item, lr[rr][k] = L(r0 + lane + 32 rr, k0 + k). Backward: lane = row k0 +
-      // lane, lb[i] = L(k0 + lane, r0 + i), staged transposed below.
-      T lr[TRANS ? 1 : RPL][SB];
-      T lb[TRANS ? SBK : 1];
-      if (!TRANS) {
-#pragma unroll
-        for (int rr = 0; rr < RPL; ++rr)
+      for (int u = 0; u < QC; ++u) {
+        bq[u] = (lane < rows && qw + u < cols) ? __ldcg(B + (int64_t)(c0 + qw + u) * a.ldb + r0 + lane) : T(0);
+        accq[u] = T(0);
+      }
+      const int nsteps = REV ? a.nrb - 1 - r : r;
+      int wab = 0;
+      unsigned ready = 0u;  // bit j <-> step mbase + j
+      int mbase = 0;
+      for (int step = 0; step < nsteps; ++step) {
+        const int m = REV ? a.nrb - 1 - step : step;
+        const int k0 = m * SB, krows = min(SB, a.n - k0);
+        // L block, issued before any wait: forward lane = row of the item, lr[k] = L(r0 +
+        // lane, k0 + k); backward lane = row k0 + lane, lb[i] = L(k0 + lane, r0 + i)
+        T lr[TRANS ? 1 : SB];
+        T lb[TRANS ? SB : 1];
+        if (!TRANS) {
 #pragma unroll
           for (int k = 0; k < SB; ++k)
-            lr[rr][k] = (lane + SB * rr < rows && k < krows)
-                            ? __ldcg(L + (int64_t)(k0 + k) * a.lda + r0 + lane + SB * rr) : T(0);
-      } else {
+            lr[k] = (lane < rows && k < krows) ? __ldcg(L + (int64_t)(k0 + k) * a.lda + r0 + lane) : T(0);
+        } else {
 #pragma unroll
-        for (int i = 0; i < SBK; ++i)
-          lb[i] = (lane < krows && i < rows) ? __ldcg(L + (int64_t)(r0 + i) * a.lda + k0 + lane) : T(0);
-      }
-      int jb = (step - mbase) / SNW;
-      if (jb >= 32 || !((ready >> jb) & 1u)) {
-        const int sl = step + SNW * lane;
-        int f = 1;
-        if (sl < nchunks) {
-          const int ml = REV ? a.nrb - 1 - sl / RPL : sl / RPL;
-          f = ld_volatile(&a.flags[(int64_t)ml * a.ngroups + g]) != 0;
+          for (int i = 0; i < SB; ++i)
+            lb[i] = (lane < krows && i < rows) ? __ldcg(L + (int64_t)(r0 + i) * a.lda + k0 + lane) : T(0);
         }
-        ready = __ballot_sync(0xffffffffu, f);
-        mbase = step;
-        if (!(ready & 1u)) {
-          // wait until block m of this group is solved (one lane, bounded)
-          if (lane == 0) {
-            const uint64_t t0 = globaltimer_ns();
-            int64_t spins = 0;
-            unsigned slp = 32;
-            while (ld_volatile(&a.flags[(int64_t)m * a.ngroups + g]) == 0) {
-              if (ld_volatile(&a.ctrl->abort)) { wab = 1; break; }
-              if (globaltimer_ns() - t0 > (uint64_t)a.timeout_ns || ++spins > (a.timeout_ns >> 7) + 100000) {
-                atomicCAS(&a.ctrl->info, 0, CHOL_INFO_TIMEOUT);
-                atomicExch(&a.ctrl->abort, 1);
-                wab = 1;
-                break;
-              }
-              __nanosleep(slp);
-              slp = slp < 128 ? slp * 2 : 128;
-            }
+        const int jb = step - mbase;
+        if (jb >= 32 || !((ready >> jb) & 1u)) {
+          const int sl = step + lane;
+          int f = 1;
+          if (sl < nsteps) {
+            const int ml = REV ? a.nrb - 1 - sl : sl;
+            f = ld_volatile(&a.flags[(int64_t)ml * a.ngroups + g]) != 0;
           }
-          wab = __shfl_sync(0xffffffffu, wab, 0);
-          if (wab) break;
-          ready = 1u;  // only this block is known to be solved
+          ready = __ballot_sync(0xffffffffu, f);
+          mbase = step;
+          if (!(ready & 1u)) {
+            if (lane == 0) {
+              const uint64_t t0 = globaltimer_ns();
+              int64_t spins = 0;
+              unsigned slp = 32;
+              while (ld_volatile(&a.flags[(int64_t)m * a.ngroups + g]) == 0) {
+                if (ld_volatile(&a.ctrl->abort)) { wab = 1; break; }
+                if (globaltimer_ns() - t0 > (uint64_t)a.timeout_ns || ++spins > (a.timeout_ns >> 7) + 100000) {
+                  atomicCAS(&a.ctrl->info, 0, CHOL_INFO_TIMEOUT);
+                  atomicExch(&a.ctrl->abort, 1);
+                  wab = 1;
+                  break;
+                }
+                __nanosleep(slp);
+                slp = slp < 128 ? slp * 2 : 128;
+              }
+            }
+            wab = __shfl_sync(0xffffffffu, wab, 0);
+            if (wab) break;
+            ready = 1u;
+          }
+          __threadfence();
+          __syncwarp();
         }
-        // every flag this warp observed is ordered before the loads of the blocks' data
-        __threadfence();
+        // this warp's columns of the solved block (lane k stages row k0 + k)
+#pragma unroll
+        for (int u = 0; u < QC; ++u)
+          yw[lane * YLD + u] = (lane < krows && qw + u < cols) ? __ldcg(B + (int64_t)(c0 + qw + u) * a.ldb + k0 + lane)
+                                                              : T(0);
+        if (TRANS) {
+#pragma unroll
+          for (int i = 0; i < SB; ++i) lt[lane * DLD + i] = lb[i];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < SB; ++k) {
+          const T l = TRANS ? lt[k * DLD + lane] : lr[TRANS ? 0 : k];
+#pragma unroll
+          for (int u = 0; u < QC; ++u) accq[u] = fma(l, yw[k * YLD + u], accq[u]);
+        }
         __syncwarp();
       }
-      // Y chunk (lane k stages row k0 + k), loaded once the block is known to be solved
-      T yv[NC];
+      if (wab && lane == 0) s_abort = 1;
 #pragma unroll
-      for (int q = 0; q < NC; ++q)
-        yv[q] = (lane < krows && q < cols) ? __ldcg(B + (int64_t)(c0 + q) * a.ldb + k0 + lane) : T(0);
-#pragma unroll
-      for (int q = 0; q < NC; ++q) yw[lane * YLD + q] = yv[q];
-      if (TRANS) {
-#pragma unroll
-        for (int i = 0; i < SBK; ++i) lt[lane * DLD + i] = lb[i];
+      for (int u = 0; u < QC; ++u)
+        if (qw + u < NC) Ys[lane * YLD + qw + u] = bq[u] - accq[u];
+      __syncthreads();
+      if (s_abort) break;
+    } else {
+      // this thread's entries of B_r for the final sum, loaded now (off the chain)
+      constexpr int BPT = (SBK * NC + SNT - 1) / SNT;
+      T bv[BPT];
+  #pragma unroll
+      for (int u = 0; u < BPT; ++u) {
+        const int e = tid + u * SNT, i = e % SBK, q = e / SBK;
+        bv[u] = (e < SBK * NC && i < rows && q < cols) ? __ldcg(B + (int64_t)(c0 + q) * a.ldb + r0 + i) : T(0);
       }
-      __syncwarp();
-#pragma unroll
-      for (int k = 0; k < SB; ++k) {
-        T l[RPL];
-#pragma unroll
-        for (int rr = 0; rr < RPL; ++rr) l[rr] = TRANS ? lt[k * DLD + lane + SB * rr] : lr[TRANS ? 0 : rr][k];
-#pragma unroll
-        for (int q = 0; q < NC; q += V) {
-          T y[V];
-          vload<T, V>(yw + k * YLD + q, y);
-#pragma unroll
+      // warp-parallel accumulation over the solved blocks
+      T acc[RPL][NC];
+  #pragma unroll
+      for (int rr = 0; rr < RPL; ++rr)
+  #pragma unroll
+        for (int q = 0; q < NC; ++q) acc[rr][q] = T(0);
+      const int nsteps = REV ? a.nrb - 1 - r : r;
+      // the solved blocks are consumed in 32-row chunks, one chunk per warp step: chunk kc of
+      // block m is step m * RPL + kc, so the chunks of the newest block go to different warps
+      const int nchunks = nsteps * RPL;
+      int wab = 0;
+      // readiness of the warp's next 32 chunks: bit j <-> step mbase + SNW j, one flag load per
+      // lane and a ballot, so blocks solved long ago cost no polling round trip
+      unsigned ready = 0u;
+      int mbase = warp;
+      for (int step = warp; step < nchunks; step += SNW) {
+        const int mi = step / RPL, kc = step % RPL;
+        const int m = REV ? a.nrb - 1 - mi : mi;
+        const int k0 = m * SBK + SB * kc, krows = min(SB, a.n - k0);  // this 32-row chunk of block m
+        // L chunk, issued before any wait (it does not depend on other items). Forward: lane =
+        // row of the item, lr[rr][k] = L(r0 + lane + 32 rr, k0 + k). Backward: lane = row k0 +
+        // lane, lb[i] = L(k0 + lane, r0 + i), staged transposed below.
+        T lr[TRANS ? 1 : RPL][SB];
+        T lb[TRANS ? SBK : 1];
+        if (!TRANS) {
+  #pragma unroll
           for (int rr = 0; rr < RPL; ++rr)
-#pragma unroll
-            for (int u = 0; u < V; ++u) acc[rr][q + u] = fma(l[rr], y[u], acc[rr][q + u]);
+  #pragma unroll
+            for (int k = 0; k < SB; ++k)
+              lr[rr][k] = (lane + SB * rr < rows && k < krows)
+                              ? __ldcg(L + (int64_t)(k0 + k) * a.lda + r0 + lane + SB * rr) : T(0);
+        } else {
+  #pragma unroll
+          for (int i = 0; i < SBK; ++i)
+            lb[i] = (lane < krows && i < rows) ? __ldcg(L + (int64_t)(r0 + i) * a.lda + k0 + lane) : T(0);
+        }
+        int jb = (step - mbase) / SNW;
+        if (jb >= 32 || !((ready >> jb) & 1u)) {
+          const int sl = step + SNW * lane;
+          int f = 1;
+          if (sl < nchunks) {
+            const int ml = REV ? a.nrb - 1 - sl / RPL : sl / RPL;
+            f = ld_volatile(&a.flags[(int64_t)ml * a.ngroups + g]) != 0;
+          }
+          ready = __ballot_sync(0xffffffffu, f);
+          mbase = step;
+          if (!(ready & 1u)) {
+            // wait until block m of this group is solved (one lane, bounded)
+            if (lane == 0) {
+              const uint64_t t0 = globaltimer_ns();
+              int64_t spins = 0;
+              unsigned slp = 32;
+              while (ld_volatile(&a.flags[(int64_t)m * a.ngroups + g]) == 0) {
+                if (ld_volatile(&a.ctrl->abort)) { wab = 1; break; }
+                if (globaltimer_ns() - t0 > (uint64_t)a.timeout_ns || ++spins > (a.timeout_ns >> 7) + 100000) {
+                  atomicCAS(&a.ctrl->info, 0, CHOL_INFO_TIMEOUT);
+                  atomicExch(&a.ctrl->abort, 1);
+                  wab = 1;
+                  break;
+                }
+                __nanosleep(slp);
+                slp = slp < 128 ? slp * 2 : 128;
+              }
+            }
+            wab = __shfl_sync(0xffffffffu, wab, 0);
+            if (wab) break;
+            ready = 1u;  // only this block is known to be solved
+          }
+          // every flag this warp observed is ordered before the loads of the blocks' data
+          __threadfence();
+          __syncwarp();
+        }
+        // Y chunk (lane k stages row k0 + k), loaded once the block is known to be solved
+        T yv[NC];
+  #pragma unroll
+        for (int q = 0; q < NC; ++q)
+          yv[q] = (lane < krows && q < cols) ? __ldcg(B + (int64_t)(c0 + q) * a.ldb + k0 + lane) : T(0);
+  #pragma unroll
+        for (int q = 0; q < NC; ++q) yw[lane * YLD + q] = yv[q];
+        if (TRANS) {
+  #pragma unroll
+          for (int i = 0; i < SBK; ++i) lt[lane * DLD + i] = lb[i];
+        }
+        __syncwarp();
+  #pragma unroll
+        for (int k = 0; k < SB; ++k) {
+          T l[RPL];
+  #pragma unroll
+          for (int rr = 0; rr < RPL; ++rr) l[rr] = TRANS ? lt[k * DLD + lane + SB * rr] : lr[TRANS ? 0 : rr][k];
+  #pragma unroll
+          for (int q = 0; q < NC; q += V) {
+            T y[V];
+            vload<T, V>(yw + k * YLD + q, y);
+  #pragma unroll
+            for (int rr = 0; rr < RPL; ++rr)
+  #pragma unroll
+              for (int u = 0; u < V; ++u) acc[rr][q + u] = fma(l[rr], y[u], acc[rr][q + u]);
+          }
+        }
+        __syncwarp();
+      }
+      if (wab && lane == 0) s_abort = 1;
+      // the eight partial sums, column-major per warp (consecutive lanes, consecutive words),
+      // then B_r minus their sum into Ys
+  #pragma unroll
+      for (int rr = 0; rr < RPL; ++rr)
+  #pragma unroll
+        for (int q = 0; q < NC; ++q) yw[q * SBK + lane + SB * rr] = acc[rr][q];
+      __syncthreads();
+      if (s_abort) break;
+  #pragma unroll
+      for (int u = 0; u < BPT; ++u) {
+        const int e = tid + u * SNT, i = e % SBK, q = e / SBK;
+        if (e < SBK * NC) {
+          T sum = T(0);
+  #pragma unroll
+          for (int w = 0; w < SNW; ++w) sum += Yw[(size_t)w * SBK * YLD + q * SBK + i];
+          Ys[i * YLD + q] = bv[u] - sum;
         }
       }
-      __syncwarp();
+      __syncthreads();
     }
-    if (wab && lane == 0) s_abort = 1;
-    // the eight partial sums, column-major per warp (consecutive lanes, consecutive words),
-    // then B_r minus their sum into Ys
-#pragma unroll
-    for (int rr = 0; rr < RPL; ++rr)
-#pragma unroll
-      for (int q = 0; q < NC; ++q) yw[q * SBK + lane + SB * rr] = acc[rr][q];
-    __syncthreads();
-    if (s_abort) break;
-#pragma unroll
-    for (int u = 0; u < BPT; ++u) {
-      const int e = tid + u * SNT, i = e % SBK, q = e / SBK;
-      if (e < SBK * NC) {
-        T sum = T(0);
-#pragma unroll
-        for (int w = 0; w < SNW; ++w) sum += Yw[(size_t)w * SBK * YLD + q * SBK + i];
-        Ys[i * YLD + q] = bv[u] - sum;
-      }
-    }
-    __syncthreads();
     T *Xo = Ys;  // the solved block, row-major with stride YLD
     if constexpr (INV) {
       // forward x = D^-1 (b - sum), backward x = D^-T (b - sum): independent SBK-term
@@ -332,10 +427,9 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
 #pragma unroll
         for (int u = 0; u < RPT; ++u) Xo[(i0 + u) * YLD + q] = t[u];
       }
-    } else if (cols <= SNW) {
-      // diagonal block, at most 8 right-hand sides: one warp per right-hand side, lane = row
-      // (see below); kept apart from the two-column form, whose extra state slows the
-      // one-column chain of the LU and refinement solves by ~40 %
+    } else if (cols <= SNW / 2) {
+      // diagonal block, at most 4 right-hand sides: one warp per right-hand side (one per SM
+      // sub-partition), lane = row; x_k on lane k, then one warp-wide FMA for the rows below
       const int c = warp;
       if (c < cols) {
         T x = Ys[lane * YLD + c];
@@ -357,78 +451,39 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
         }
         Ys[lane * YLD + c] = x;
       }
-    } else if (cols <= 2 * SNW) {
-      // diagonal block, few right-hand sides: one warp per pair of right-hand sides (columns
-      // warp and warp + 8), lane = row. Each step takes x_k on lane k and updates the rows
-      // below it with one warp-wide FMA per column (an FP64 instruction costs the SM
-      // sub-partition's FP64 pipe the same time with one active lane as with 32, so a single
-      // thread would pay for 32 lanes on every one of its 496 FMAs). Every x_i sees the same
-      // operations in the same order as in the thread-per-column form.
-      const int c0 = warp, c1 = warp + SNW;
-      if (c0 < cols) {
-        const bool two = c1 < cols;
-        T x0 = Ys[lane * YLD + c0];
-        T x1 = two ? Ys[lane * YLD + c1] : T(0);
-        const T rinv = Rs[lane];
-        if (!REV) {
+    } else {
+      // diagonal block, more than 4 right-hand sides: thread (warp w, lane c) holds column c
+      // of rows w, w + 8, w + 16, w + 24. Step k: warp k % 8 forms x_k for every column at
+      // once and passes it on through shared memory (two buffers by step parity, so one
+      // barrier per step), then each warp updates its rows below k (above k backward). An
+      // FP64 instruction costs its SM sub-partition the same time with one active lane as
+      // with 32, so this spends 32-wide instructions on all four sub-partitions where one
+      // thread per column would spend them on one. Every x_i sees the operations of the
+      // right-looking substitution in the same order (its updates by increasing k, then its
+      // quotient; decreasing k backward).
+      const int c = lane;
+      T y[SBK / SNW];
 #pragma unroll
-          for (int k = 0; k < SBK; ++k) {
-            if (lane == k) {
-              x0 = squot(x0, Ld[k * DLD + k], rinv);
-              if (two) x1 = squot(x1, Ld[k * DLD + k], rinv);
-            }
-            const T y0 = __shfl_sync(0xffffffffu, x0, k);
-            const T y1 = two ? __shfl_sync(0xffffffffu, x1, k) : T(0);
-            if (lane > k) {
-              const T l = Ld[lane * DLD + k];
-              x0 = fma(-l, y0, x0);
-              if (two) x1 = fma(-l, y1, x1);
-            }
-          }
-        } else {
+      for (int j = 0; j < SBK / SNW; ++j) y[j] = c < cols ? Ys[(warp + SNW * j) * YLD + c] : T(0);
 #pragma unroll
-          for (int k = SBK - 1; k >= 0; --k) {
-            if (lane == k) {
-              x0 = squot(x0, Ld[k * DLD + k], rinv);
-              if (two) x1 = squot(x1, Ld[k * DLD + k], rinv);
-            }
-            const T y0 = __shfl_sync(0xffffffffu, x0, k);
-            const T y1 = two ? __shfl_sync(0xffffffffu, x1, k) : T(0);
-            if (lane < k) {
-              const T l = Ld[k * DLD + lane];
-              x0 = fma(-l, y0, x0);
-              if (two) x1 = fma(-l, y1, x1);
-            }
-          }
+      for (int kk = 0; kk < SBK; ++kk) {
+        const int k = REV ? SBK - 1 - kk : kk;
+        if (warp == k % SNW) {
+          const T x = squot(y[k / SNW], Ld[k * DLD + k], Rs[k]);
+          y[k / SNW] = x;
+          s_xk[kk & 1][c] = x;
         }
-        Ys[lane * YLD + c0] = x0;
-        if (two) Ys[lane * YLD + c1] = x1;
-      }
-    } else if (tid < cols) {
-      // diagonal block: one thread per right-hand side runs the substitution
-      const int c = tid;
-      T x[SBK];
+        __syncthreads();
+        const T xk = s_xk[kk & 1][c];
 #pragma unroll
-      for (int i = 0; i < SBK; ++i) x[i] = Ys[i * YLD + c];
-      // right-looking: once x_k is known every later row is updated at once, so each x_k
-      // is one quotient and one multiply-add after x_{k-1}
-      if (!REV) {
-#pragma unroll
-        for (int k = 0; k < SBK; ++k) {
-          x[k] = squot(x[k], Ld[k * DLD + k], Rs[k]);
-#pragma unroll
-          for (int i = k + 1; i < SBK; ++i) x[i] = fma(-Ld[i * DLD + k], x[k], x[i]);
-        }
-      } else {
-#pragma unroll
-        for (int k = SBK - 1; k >= 0; --k) {
-          x[k] = squot(x[k], Ld[k * DLD + k], Rs[k]);
-#pragma unroll
-          for (int i = 0; i < k; ++i) x[i] = fma(-Ld[k * DLD + i], x[k], x[i]);
+        for (int j = 0; j < SBK / SNW; ++j) {
+          const int i = warp + SNW * j;
+          if (REV ? i < k : i > k) y[j] = fma(-(REV ? Ld[k * DLD + i] : Ld[i * DLD + k]), xk, y[j]);
         }
       }
 #pragma unroll
-      for (int i = 0; i < SBK; ++i) Ys[i * YLD + c] = x[i];
+      for (int j = 0; j < SBK / SNW; ++j)
+        if (c < cols) Ys[(warp + SNW * j) * YLD + c] = y[j];
     }
     __syncthreads();
     // write the solved block column by column (one warp per column: consecutive rows)
