@@ -227,6 +227,7 @@ static __device__ __noinline__ int potrf_tile(double *G, int64_t ld, int nk, dou
   double *Ds = smem + STAGE_DOUBLES;
   double *Rinv = Ds + IB * DS_LD;
   __shared__ int s_fail;
+  __shared__ int s_dfail[2];
   const int tid = threadIdx.x;
   for (int p = 0; p < nk; p += IB) {
     const int pb = min(IB, nk - p);
@@ -234,26 +235,41 @@ static __device__ __noinline__ int potrf_tile(double *G, int64_t ld, int nk, dou
     load_diag_block(Gpp, ld, pb, Ds);
     if (tid == 0) s_fail = 0;
     __syncthreads();
-    // unblocked right-looking factor of the pb x pb block by warp 0, lane r owns row r
-    if (tid < 32) {
-      const int r = tid;
+    // unblocked right-looking factor of the pb x pb block by warps 0-3 (one per SM
+    // sub-partition), lane r owns row r. Column j: warp j % 4 takes the square root and the
+    // quotients l_rj; after a barrier of the four warps each updates the columns c = w mod 4
+    // it owns with l_rj l_cj, so the 496 FMA instructions of the rank-one updates are spread
+    // over four FP64 pipes instead of one. Every entry sees the same operations in the same
+    // order as with one warp. The owner's failure flag is double-buffered by column parity,
+    // so a warp that reads it late never sees the next column's.
+    if (tid < 128) {
+      const int r = tid & 31, w = tid >> 5;
       int fail = 0;
       for (int j = 0; j < pb; ++j) {
-        const double s = Ds[j * DS_LD + j];
-        if (!(s > 0.0)) { fail = p + j + 1; break; }
-        const double ljj = sqrt(s);
-        __syncwarp();
-        if (r == j) Ds[j * DS_LD + j] = ljj;
-        if (r > j && r < pb) Ds[r * DS_LD + j] = Ds[r * DS_LD + j] / ljj;
-        __syncwarp();
+        if (w == (j & 3)) {
+          const double s = Ds[j * DS_LD + j];
+          int f = 0;
+          if (!(s > 0.0)) {
+            f = p + j + 1;
+          } else {
+            const double ljj = sqrt(s);
+            if (r > j && r < pb) Ds[r * DS_LD + j] = Ds[r * DS_LD + j] / ljj;
+            if (r == j) Ds[j * DS_LD + j] = ljj;
+          }
+          if (r == 0) s_dfail[j & 1] = f;
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        fail = s_dfail[j & 1];
+        if (fail) break;
         if (r > j && r < pb) {
           const double lrj = Ds[r * DS_LD + j];
-          for (int c = j + 1; c <= r; ++c) Ds[r * DS_LD + c] = fma(-lrj, Ds[c * DS_LD + j], Ds[r * DS_LD + c]);
+          for (int c = j + 1 + ((w - j - 1) & 3); c <= r; c += 4)
+            Ds[r * DS_LD + c] = fma(-lrj, Ds[c * DS_LD + j], Ds[r * DS_LD + c]);
         }
-        __syncwarp();
       }
-      if (r == 0) s_fail = fail;
-      if (!fail && r < pb) Rinv[r] = 1.0 / Ds[r * DS_LD + r];
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (tid == 0) s_fail = fail;
+      if (!fail && tid < pb) Rinv[tid] = 1.0 / Ds[tid * DS_LD + tid];
     }
     __syncthreads();
     if (s_fail) return s_fail;
