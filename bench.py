@@ -867,6 +867,7 @@ def run_batched(args, chol, dev):
                      "matrices_per_s": round(len(orders) / ms * 1e3, 1), "failed": bad,
                      "backward_error_sample_max": berr,
                      "autotuned": {"workers_per_sm": best.workers_per_sm, "lpt_order": best.lpt_order,
+                                   "wide_panel_min_n": best.wide_panel_min_n if name == "f64" else None,
                                    "tuning_ms_best": round(tune_ms, 3)}}
         del src, work, flat, rhs, graph
         torch.cuda.empty_cache()

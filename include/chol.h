@@ -277,8 +277,12 @@ chol_status chol_lower_copy(int n, const double *dSrc, int lds, double *dDst, in
  * dWork      chol_batched_workspace_size(batch) bytes.
  */
 typedef struct {
-  int workers_per_sm;  /* worker blocks per SM: 1 or 2 */
-  int lpt_order;       /* 1: largest matrices first; 0: in the given order */
+  int workers_per_sm;    /* worker blocks per SM: 1 or 2 */
+  int lpt_order;         /* 1: largest matrices first; 0: in the given order */
+  int wide_panel_min_n;  /* FP64: members of order >= this update their trailing matrix once per
+                            64-column panel instead of once per 32-column block (the same
+                            products, the two halves of a panel subtracted together); 0 = every
+                            member, > 4096 = none. FP32 members always use 32-column blocks. */
 } chol_batch_opts;
 void chol_batch_opts_default(chol_batch_opts *o);
 size_t chol_batched_workspace_size(int batch);
@@ -295,7 +299,8 @@ chol_status chol_factor_batched(int precision, int batch, const int *dN, void *c
 chol_status chol_solve_batched(int precision, int batch, const int *dN, void *const *dL, const int *dLda,
                                void *const *dB, int *dInfo, const chol_batch_opts *bopts, void *dWork,
                                size_t work_bytes, void *stream);
-/* Autotuner: times every launch shape (workers per SM x order) on the given batch, copying
+/* Autotuner: times every launch shape (workers per SM x order, and for FP64 the size from which
+ * members use 64-column panels: none, 384, 256, 128, all) on the given batch, copying
  * the matrices dAsrc into dAscratch before each run (both arrays of device pointers with the
  * same orders and leading dimensions), and writes the fastest shape to *best (and its time in
  * ms to *best_ms). Synchronises the stream. */

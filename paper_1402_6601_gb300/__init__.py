@@ -633,7 +633,7 @@ def solve_spd(A, B, nb=0, recompute=False):
 # Batched factor + solve
 
 class BatchOpts(ctypes.Structure):
-    _fields_ = [("workers_per_sm", ctypes.c_int), ("lpt_order", ctypes.c_int)]
+    _fields_ = [("workers_per_sm", ctypes.c_int), ("lpt_order", ctypes.c_int), ("wide_panel_min_n", ctypes.c_int)]
 
 
 class Batch:

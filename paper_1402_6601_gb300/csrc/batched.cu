@@ -29,6 +29,7 @@ struct BatchArgs {
   const int *order;
   unsigned int *counter;
   int solve_only;  // 1: A already holds the factors; only the substitutions run
+  int wide_min_n;  // FP64 members of at least this order use 64-column panels
 };
 
 // order = indices sorted by decreasing N (ties in any order), or the identity; counter = 0
@@ -133,12 +134,12 @@ struct BatchTiles;
 template <>
 struct BatchTiles<double> {
   static constexpr int SMEM = TILE_SMEM_BYTES;
-  __device__ static int potrf(double *G, int64_t ld, int n, double *s) { return potrf_tile(G, ld, n, s); }
+  __device__ static int potrf(double *G, int64_t ld, int n, double *s, int pw) { return potrf_tile(G, ld, n, s, pw); }
 };
 template <>
 struct BatchTiles<float> {
   static constexpr int SMEM = f32::TILE_SMEM_BYTES;
-  __device__ static int potrf(float *G, int64_t ld, int n, float *s) { return f32::potrf_tile(G, ld, n, s); }
+  __device__ static int potrf(float *G, int64_t ld, int n, float *s, int) { return f32::potrf_tile(G, ld, n, s); }
 };
 
 template <class T, int MINB>
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(NT, MINB) batched_kernel(const __grid_constant
       __syncthreads();
       continue;
     }
-    const int f = (n > 0 && !a.solve_only) ? BatchTiles<T>::potrf(A, lda, n, smem) : 0;
+    const int f = (n > 0 && !a.solve_only) ? BatchTiles<T>::potrf(A, lda, n, smem, n >= a.wide_min_n ? 64 : 32) : 0;
     if (threadIdx.x == 0) a.info[m] = f;
     if (!f && n > 0 && a.B && a.B[m]) block_solve_vec<T>(A, lda, n, static_cast<T *>(a.B[m]), smem);
     __syncthreads();
@@ -216,6 +217,7 @@ extern "C" void chol_batch_opts_default(chol_batch_opts *o) {
   if (!o) return;
   o->workers_per_sm = 1;
   o->lpt_order = 1;
+  o->wide_panel_min_n = 0;
 }
 
 extern "C" size_t chol_batched_workspace_size(int batch) {
@@ -248,6 +250,7 @@ static chol_status batched_impl(int precision, int batch, const int *dN, void *c
   a.counter = reinterpret_cast<unsigned int *>(ws);
   a.order = reinterpret_cast<int *>(ws + 256);
   a.solve_only = solve_only;
+  a.wide_min_n = o.wide_panel_min_n < 0 ? 0 : o.wide_panel_min_n;
   batch_order_kernel<<<1, 1024, 0, s>>>(batch, dN, const_cast<int *>(a.order), o.lpt_order, a.counter);
   CHOL_CUDA_TRY(cudaGetLastError());
   cudaError_t e;
@@ -299,27 +302,33 @@ extern "C" chol_status chol_batched_autotune(int precision, int batch, const int
   chol_batch_opts cand, win;
   chol_batch_opts_default(&win);
   chol_status st = CHOL_OK;
+  // FP64: the order from which members use 64-column panels (none, 384, 256, 128, all)
+  const int wide_cands[5] = {BATCH_MAX_N + 1, 384, 256, 128, 0};
+  const int nwide = precision == CHOL_F64 ? 5 : 1;
   for (int wps = 1; wps <= 2 && st == CHOL_OK; ++wps) {
     for (int lpt = 0; lpt <= 1 && st == CHOL_OK; ++lpt) {
-      cand.workers_per_sm = wps;
-      cand.lpt_order = lpt;
-      float t = 0.f;
-      for (int rep = 0; rep < 2 && st == CHOL_OK; ++rep) {
-        if (precision == CHOL_F64)
-          batch_copy_kernel<double><<<di.sms * 4, 256, 0, s>>>(batch, dN, dAsrc, dAscratch, dLda);
-        else
-          batch_copy_kernel<float><<<di.sms * 4, 256, 0, s>>>(batch, dN, dAsrc, dAscratch, dLda);
-        if (cudaGetLastError() != cudaSuccess) { st = CHOL_ERR_CUDA; break; }
-        if (cudaEventRecord(e0, s) != cudaSuccess) { st = CHOL_ERR_CUDA; break; }
-        st = chol_posv_batched(precision, batch, dN, dAscratch, dLda, nullptr, dInfo, &cand, dWork, work_bytes,
-                               stream);
-        if (st != CHOL_OK) break;
-        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) { st = CHOL_ERR_CUDA; break; }
-        cudaEventElapsedTime(&t, e0, e1);  // the second repetition is kept
-      }
-      if (st == CHOL_OK && t < best_t) {
-        best_t = t;
-        win = cand;
+      for (int wi = 0; wi < nwide && st == CHOL_OK; ++wi) {
+        cand.workers_per_sm = wps;
+        cand.lpt_order = lpt;
+        cand.wide_panel_min_n = precision == CHOL_F64 ? wide_cands[wi] : 0;
+        float t = 0.f;
+        for (int rep = 0; rep < 2 && st == CHOL_OK; ++rep) {
+          if (precision == CHOL_F64)
+            batch_copy_kernel<double><<<di.sms * 4, 256, 0, s>>>(batch, dN, dAsrc, dAscratch, dLda);
+          else
+            batch_copy_kernel<float><<<di.sms * 4, 256, 0, s>>>(batch, dN, dAsrc, dAscratch, dLda);
+          if (cudaGetLastError() != cudaSuccess) { st = CHOL_ERR_CUDA; break; }
+          if (cudaEventRecord(e0, s) != cudaSuccess) { st = CHOL_ERR_CUDA; break; }
+          st = chol_posv_batched(precision, batch, dN, dAscratch, dLda, nullptr, dInfo, &cand, dWork, work_bytes,
+                                 stream);
+          if (st != CHOL_OK) break;
+          if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) { st = CHOL_ERR_CUDA; break; }
+          cudaEventElapsedTime(&t, e0, e1);  // the second repetition is kept
+        }
+        if (st == CHOL_OK && t < best_t) {
+          best_t = t;
+          win = cand;
+        }
       }
     }
   }

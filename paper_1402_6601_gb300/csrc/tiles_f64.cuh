@@ -223,7 +223,14 @@ __device__ __forceinline__ void load_diag_block(const double *G, int64_t ld, int
 
 // POTRF on the nk x nk diagonal tile G (in place, lower). Returns 0, or the 1-based column
 // inside the tile whose pivot is not positive (or NaN). Called by all threads.
-static __device__ __noinline__ int potrf_tile(double *G, int64_t ld, int nk, double *smem) {
+//
+// pw (32 or 64) is the width of the panel whose update of the trailing matrix is applied at
+// once: 32-column blocks are factored and solved in turn, the later columns of the same panel
+// updated right away, and the columns past the panel updated once per panel with K = pw, so
+// with pw = 64 the trailing matrix is read and written half as often and the update runs two
+// 32-deep chunks double-buffered. The same products are formed; only the order in which the
+// two 32-column halves of a panel are subtracted from the trailing matrix changes.
+static __device__ __noinline__ int potrf_tile(double *G, int64_t ld, int nk, double *smem, int pw = IB) {
   double *Ds = smem + STAGE_DOUBLES;
   double *Rinv = Ds + IB * DS_LD;
   __shared__ int s_fail;
@@ -231,6 +238,7 @@ static __device__ __noinline__ int potrf_tile(double *G, int64_t ld, int nk, dou
   const int tid = threadIdx.x;
   for (int p = 0; p < nk; p += IB) {
     const int pb = min(IB, nk - p);
+    const int pend = min(nk, (p / pw) * pw + pw);  // end of this block's panel
     double *Gpp = G + (int64_t)p * ld + p;
     load_diag_block(Gpp, ld, pb, Ds);
     if (tid == 0) s_fail = 0;
@@ -285,9 +293,18 @@ static __device__ __noinline__ int potrf_tile(double *G, int64_t ld, int nk, dou
       if (r < rows) row_solve_lt(Pn, ld, r, pb, Ds, Rinv);
     }
     __syncthreads();
-    if (rows > 0) {
+    // the panel's later columns now; the columns past the panel once the panel is complete
+    const int pcols = pend - p - pb;
+    if (rows > 0 && pcols > 0) {
       double *Gt = G + (int64_t)(p + pb) * ld + p + pb;
-      update_nt(Gt, ld, Pn, ld, Pn, ld, rows, rows, pb, true, smem);
+      update_nt(Gt, ld, Pn, ld, Pn, ld, rows, pcols, pb, true, smem);
+    }
+    if (p + pb == pend && nk > pend) {
+      const int P0 = pend - ((pend - 1) % pw + 1);  // first column of the panel
+      const int trail = nk - pend;
+      double *Gt = G + (int64_t)pend * ld + pend;
+      const double *Pp = G + (int64_t)P0 * ld + pend;
+      update_nt(Gt, ld, Pp, ld, Pp, ld, trail, trail, pend - P0, true, smem);
     }
   }
   __syncthreads();

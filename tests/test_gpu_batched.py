@@ -95,6 +95,7 @@ def test_batched_graph_replay_and_autotune(chol):
     scratch = _make(chol, orders, seed=9)
     best, ms = chol.batched_autotune(src, scratch)
     assert best.workers_per_sm in (1, 2) and best.lpt_order in (0, 1) and ms > 0
+    assert best.wide_panel_min_n in (0, 128, 256, 384, 4097)
     work = _make(chol, orders, seed=9)
     flat0, rhs0 = work.flat.clone(), work.rhs_flat.clone()
     stream = torch.cuda.Stream()
@@ -140,3 +141,32 @@ def test_factor_then_solve_batched_equals_posv(chol, dtype):
         if orders[m] == 0:
             continue
         assert oracle.backward_error(A0[m], two.rhs(m).cpu().numpy().astype(np.float64), b0[m]) <= tol, m
+
+
+@pytest.mark.parametrize("wide", [0, 100, 4097])
+def test_batched_fp64_wide_panels(chol, wide):
+    # members of order >= wide update their trailing matrix once per 64-column panel: parity
+    # with the oracle, and integer factors stay exact (every partial sum is an integer)
+    rng = np.random.default_rng(3)
+    orders = [int(x) for x in rng.integers(1, 300, size=80)] + [64, 65, 127, 128, 129]
+    bt = _make(chol, orders, seed=13)
+    A0 = [bt.matrix(m).cpu().numpy().copy() for m in range(bt.batch)]
+    b0 = [bt.rhs(m).cpu().numpy().copy() for m in range(bt.batch)]
+    o = chol.BatchOpts()
+    chol.lib.chol_batch_opts_default(chol.ctypes.byref(o))
+    o.wide_panel_min_n = wide
+    chol.posv_batched(bt, o)
+    torch.cuda.synchronize()
+    assert int(bt.info.abs().max().item()) == 0
+    for m in range(bt.batch):
+        L = np.tril(bt.matrix(m).cpu().numpy())
+        assert oracle.rel_frobenius(L, oracle.factor(A0[m])) <= 1e-12, m
+        assert oracle.backward_error(A0[m], bt.rhs(m).cpu().numpy(), b0[m]) <= 1e-14, m
+    ints = [synth.integer_factor(n, seed=n) for n in (5, 64, 96, 130, 200)]
+    flat = torch.cat([torch.from_numpy(np.ascontiguousarray(A.T)).reshape(-1) for _, A in ints]).to("cuda")
+    offs = np.cumsum([0] + [A.shape[0] ** 2 for _, A in ints])[:-1].tolist()
+    bi = chol.Batch(flat, offs, [A.shape[0] for _, A in ints])
+    chol.posv_batched(bi, o, factor_only=True)
+    torch.cuda.synchronize()
+    for m, (L, _) in enumerate(ints):
+        np.testing.assert_array_equal(np.tril(bi.matrix(m).cpu().numpy()), L)
