@@ -166,7 +166,11 @@ def test_timeout_is_reported_not_hung(chol):
     assert int(info2.item()) == 0
 
 
-@pytest.mark.parametrize("n,nrhs", [(1024, 1), (1000, 70), (33, 3), (64, 64), (5, 1)])
+# right-hand-side counts reach every form of the sweep: one warp per column (<= 4 columns),
+# solved blocks split over warps with the eight-warp diagonal solve (5-8), columns split over
+# warps (9-16 and 17-32 per group), and ragged last groups
+@pytest.mark.parametrize("n,nrhs", [(1024, 1), (1000, 70), (33, 3), (64, 64), (5, 1), (500, 6), (700, 13),
+                                    (257, 16), (300, 40)])
 def test_solve_parity(chol, n, nrhs):
     A = synth.gram_spd(n, seed=n).numpy()
     B = synth.rhs(n, nrhs, seed=n + 1).numpy()
@@ -181,7 +185,7 @@ def test_solve_parity(chol, n, nrhs):
     assert oracle.rel_frobenius(X, Xref) <= 1e-12
 
 
-@pytest.mark.parametrize("n,nrhs", [(200, 1), (333, 65)])
+@pytest.mark.parametrize("n,nrhs", [(200, 1), (333, 65), (300, 6), (260, 16), (100, 40)])
 def test_sweeps_exact_on_integers(chol, n, nrhs):
     L, A = synth.integer_factor(n, seed=9)
     X = synth.integer_vector(n, nrhs, 4)

@@ -117,7 +117,8 @@ def test_lu_schedule_invariance_bitwise(chol, policy, alpha, cp):
     assert torch.equal(got.F, ref.F) and torch.equal(got.piv, ref.piv) and torch.equal(got.lw, ref.lw)
 
 
-@pytest.mark.parametrize("n,nb,nrhs", [(1000, 128, 70), (300, 64, 1), (33, 16, 3), (512, 256, 64)])
+@pytest.mark.parametrize("n,nb,nrhs", [(1000, 128, 70), (300, 64, 1), (33, 16, 3), (512, 256, 64), (400, 64, 13),
+                                       (250, 128, 6)])
 def test_lu_solve_backward_error_and_parity(chol, n, nb, nrhs):
     A = synth.general_matrix(n, seed=2 * n).numpy()
     B = synth.rhs(n, nrhs, seed=2 * n + 1).numpy()
