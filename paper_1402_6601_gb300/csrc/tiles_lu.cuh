@@ -121,9 +121,30 @@ static __device__ __noinline__ void lu_apply_block(double *X1, int64_t ld1, doub
                                                    int w, const int *piv, const double *L11, int mA,
                                                    const double *L21, int64_t ldl, double *smem) {
   double *Xs = smem;  // w x ncols, row-major: thread c touches column c
+  // X2 rows the interchanges touch: slot j holds position piv[j] if j is its first occurrence
+  // (later interchanges with the same position use that slot), -1 if piv[j] is not an X2 row
+  __shared__ int s_slot[LU_IB];
+  if (threadIdx.x < w) {
+    const int j = threadIdx.x, q = piv[j];
+    int sl = -1;
+    if (q != j && q >= w && q < w + mA) {
+      sl = j;
+      for (int jj = 0; jj < j; ++jj)
+        if (piv[jj] == q) { sl = jj; break; }
+    }
+    s_slot[j] = sl;
+  }
+  __syncthreads();
   for (int c = threadIdx.x; c < ncols; c += NT) {
     const double *x1 = X1 + (int64_t)c * ld1;
     for (int r = 0; r < w; ++r) Xs[r * ncols + c] = ldcg(x1 + r);
+    // the touched X2 values are loaded together, interchanged in the thread's own slots, and
+    // stored back once: the same sequence of interchanges without a dependent load from
+    // global memory per interchange
+    double *x2c = X2 + (int64_t)c * ld2;
+    double c2[LU_IB];
+    for (int j = 0; j < w; ++j)
+      if (s_slot[j] == j) c2[j] = ldcg(x2c + (piv[j] - w));
     for (int j = 0; j < w; ++j) {
       const int q = piv[j];
       if (q == j || q < 0 || q >= w + mA) continue;  // positions outside the rows: not a pivot
@@ -132,12 +153,14 @@ static __device__ __noinline__ void lu_apply_block(double *X1, int64_t ld1, doub
         Xs[j * ncols + c] = Xs[q * ncols + c];
         Xs[q * ncols + c] = t;
       } else {
-        double *x2 = X2 + (int64_t)c * ld2 + (q - w);
-        const double t = ldcg(x2);
-        stcg(x2, Xs[j * ncols + c]);
+        const int sl = s_slot[j];
+        const double t = c2[sl];
+        c2[sl] = Xs[j * ncols + c];
         Xs[j * ncols + c] = t;
       }
     }
+    for (int j = 0; j < w; ++j)
+      if (s_slot[j] == j) stcg(x2c + (piv[j] - w), c2[j]);
     for (int r = 1; r < w; ++r) {
       double t = Xs[r * ncols + c];
       for (int j = 0; j < r; ++j) t = fma(-L11[r * DS_LD + j], Xs[j * ncols + c], t);
