@@ -82,7 +82,8 @@ struct FactorArgs {
   int *qcount;
   unsigned long long *qcost;   // int64 two's complement
   unsigned long long *run_end; // ns, 0 = idle
-  int *sm_busy;                // per SM (by %smid, < SM_SLOTS): running tasks, then hosted workers
+  int *sm_busy;                // per SM (by %smid, < SM_SLOTS): running tasks, hosted workers, then
+                               // running critical-path tasks (P::critical)
   long long *trace_buf;
   int use_cp;       // communication prediction in the placement
   int64_t comm_ns;  // predicted cost of one input tile a worker did not write last
@@ -143,7 +144,7 @@ static Layout make_layout(int n, const Resolved &r, int W) {
   L.qcount = o; o += align_up((size_t)W * 4, 256);
   L.qcost = o; o += align_up((size_t)W * 8, 256);
   L.run_end = o; o += align_up((size_t)W * 8, 256);
-  L.sm_busy = o; o += align_up((size_t)2 * SM_SLOTS * 4, 256);
+  L.sm_busy = o; o += align_up((size_t)3 * SM_SLOTS * 4, 256);
   L.board = o; o += align_up((size_t)W * sizeof(HelpSlot), 256);
   L.slots = o; o += align_up((size_t)W * L.C * 8, 256);
   L.zero_end = o;
@@ -342,7 +343,8 @@ __device__ int64_t acquire(const FactorArgs &a, int wid, int smid, uint32_t &rng
     // speed, which lengthens the critical path when work is scarce
     int yield_ = 0;
     if (lane == 0 && smid >= 0 && ld_volatile(&a.sm_busy[smid]) > 0)
-      yield_ = ld_volatile(&a.ctrl->queued) <= ld_volatile(&a.ctrl->free_sms);
+      yield_ = ld_volatile(&a.ctrl->queued) <= ld_volatile(&a.ctrl->free_sms) ||
+               ld_volatile(&a.sm_busy[2 * SM_SLOTS + smid]) > 0;
     yield_ = __shfl_sync(0xffffffffu, yield_, 0);
     int64_t id = yield_ ? -1 : try_pop(a, wid);
     if (id >= 0) { from = wid; return id; }
@@ -546,6 +548,7 @@ struct TilesF64 {
   static constexpr int UPD_UNIT = 64;       // SYRK / GEMM units: the update's 64 x 64 blocks
   static constexpr bool SPLIT_TRSM = true, SPLIT_SYRK = true, SPLIT_GEMM = true;
   static constexpr bool SPLIT_EVERY_TRSM = false;
+  __device__ static bool critical(int) { return false; }
   static constexpr int SMEM = TILE_SMEM_BYTES;
   static constexpr int MIN_BLOCKS = 2;  // two workers per SM share the FP64 pipe
   __device__ static int potrf(T *G, int64_t ld, int nk, T *s) { return potrf_tile(G, ld, nk, s); }
@@ -579,6 +582,7 @@ struct TilesF32 {
   // a whole FP32 TRSM is its 64-row bands one after another, so every TRSM is handed out band
   // by band (mode 1): same work, and no long TRSM lands on a critical path
   static constexpr bool SPLIT_EVERY_TRSM = true;
+  __device__ static bool critical(int) { return false; }
   static_assert(f32::TRSM_BAND_SMEM_BYTES <= (f32::PANEL_SMEM_BYTES > f32::TILE_SMEM_BYTES ? f32::PANEL_SMEM_BYTES
                                                                                          : f32::TILE_SMEM_BYTES),
                 "the band TRSM must fit the FP32 bodies' shared memory");
@@ -689,6 +693,11 @@ struct LuF64 {
   static constexpr int UPD_UNIT = 64;
   static constexpr bool SPLIT_TRSM = false, SPLIT_SYRK = false, SPLIT_GEMM = false;
   static constexpr bool SPLIT_EVERY_TRSM = false;
+  // the panel factorizations form the graph's longest chain (TSTRF(i, k) -> TSTRF(i + 1, k),
+  // and on to step k + 1): while one runs, its SM's other worker takes no new task, so the
+  // chain gets the whole FP64 pipe instead of half of it and no dependent FP64 operation
+  // waits behind a neighbour's update
+  __device__ static bool critical(int kind) { return kind == K_GETRF || kind == K_TSTRF; }
   static constexpr int SMEM = LU_SMEM_BYTES;
   static constexpr int MIN_BLOCKS = 2;
   __device__ static void begin() {}
@@ -929,6 +938,7 @@ __global__ void __launch_bounds__(NT, P::MIN_BLOCKS) factor_kernel(const __grid_
         atomicSub(&a.ctrl->free_sms, 1);
       if (id >= 0 && lane == 0) {
         const TaskDesc d = G::desc(a.T, id);
+        if (smid >= 0 && P::critical(d.kind)) atomicAdd(&a.sm_busy[2 * SM_SLOTS + smid], 1);
         const int64_t c = a.cost[d.kind];
         if (kept < 0) atomicAdd(&a.qcost[from], (unsigned long long)(-c));
         *(volatile unsigned long long *)&a.run_end[wid] = globaltimer_ns() + (uint64_t)c;
@@ -989,6 +999,7 @@ __global__ void __launch_bounds__(NT, P::MIN_BLOCKS) factor_kernel(const __grid_
       } else {
         complete<G>(a, wid, smid, d, smem_raw, &s_nready, &s_next);
       }
+      if (lane == 0 && smid >= 0 && P::critical(d.kind)) atomicSub(&a.sm_busy[2 * SM_SLOTS + smid], 1);
       if (lane == 0 && smid >= 0 && atomicSub(&a.sm_busy[smid], 1) == 1) atomicAdd(&a.ctrl->free_sms, 1);
       if (a.trace && lane == 0) {
         long long *tr = a.trace_buf + 4 * id;
@@ -1130,14 +1141,21 @@ static bool resolve(int n, const chol_opts *opts, Resolved &r, int prec = PREC_F
   r.eps = o.dada_eps > 0.0 ? o.dada_eps : 0.01;
   const double nb = (double)r.nb;
   // predicted rate per SM of each kind (GFLOP/s = flop per ns), from the tile bodies' measured
-  // times: FP64 DFMA bodies ~7.5 for every kind; the FP32 forms' POTRF and TRSM are dependent
+  // times: FP64 DFMA bodies ~7.5 for every Cholesky kind; the FP32 forms' POTRF and TRSM are dependent
   // chains (~40 and ~60), FFMA SYRK ~140, FFMA GEMM ~250, tensor-core updates ~1000 (one BF16
   // term, SYRK and GEMM) and ~730 (three terms, GEMM only: its SYRKs run on FFMA). Equal
   // predictions for TRSM and SYRK would tie the bottom levels of the critical TRSM(k+1, k) and
   // the previous step's SYRK(k+1, k-1), and the tie would go to the older task.
   double per_sm[4];
-  if (prec == PREC_F64 || prec == PREC_LU_F64) {
+  if (prec == PREC_F64) {
     for (int k = 0; k < 4; ++k) per_sm[k] = 7.5;
+  } else if (prec == PREC_LU_F64) {
+    // GETRF / GESSM / TSTRF / SSSSM at tile 128, measured per task in a trace of the n = 8192
+    // factor: the panel factorizations are dependent chains, their transformations less so
+    per_sm[0] = 3.4;
+    per_sm[1] = 6.6;
+    per_sm[2] = 4.2;
+    per_sm[3] = 7.0;
   } else {
     per_sm[0] = 40.0;
     per_sm[1] = 60.0;
