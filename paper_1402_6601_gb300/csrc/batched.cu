@@ -75,7 +75,10 @@ __device__ __forceinline__ T bquot(T b, T d, T r) {
 
 // Forward and back substitution L L^T x = b for one matrix by the whole block; b in place.
 // 32-row blocks: warp 0 solves the diagonal block (lanes = rows, x_k broadcast by shuffle),
-// then all threads update the remaining rows with that block's columns.
+// then all threads update the remaining rows with that block's columns. The L values a lane
+// or a thread needs for a block are loaded into registers before its chain of dependent
+// operations starts, so the chain waits for memory once per block, not once per step (L was
+// just written through L2 by the factor).
 template <class T>
 __device__ void block_solve_vec(const T *L, int64_t lda, int n, T *b, T *xs) {
   const int tid = threadIdx.x, lane = tid & 31;
@@ -84,21 +87,32 @@ __device__ void block_solve_vec(const T *L, int64_t lda, int n, T *b, T *xs) {
   for (int p = 0; p < n; p += 32) {  // L y = b
     const int pb = min(32, n - p);
     if (tid < 32) {
+      T lr[32];  // row p + lane of the diagonal block
+#pragma unroll
+      for (int k = 0; k < 32; ++k) lr[k] = (lane < pb && k < pb) ? L[(int64_t)(p + k) * lda + p + lane] : T(0);
       T y = lane < pb ? xs[p + lane] : T(0);
       const T dl = lane < pb ? L[(int64_t)(p + lane) * lda + p + lane] : T(1);
       const T rl = T(1) / dl;
-      for (int k = 0; k < pb; ++k) {
-        const T yk = bquot(__shfl_sync(0xffffffffu, y, k), __shfl_sync(0xffffffffu, dl, k),
-                           __shfl_sync(0xffffffffu, rl, k));
-        if (lane == k) y = yk;
-        else if (lane > k && lane < pb) y = fma(-L[(int64_t)(p + k) * lda + p + lane], yk, y);
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        if (k < pb) {
+          const T yk = bquot(__shfl_sync(0xffffffffu, y, k), __shfl_sync(0xffffffffu, dl, k),
+                             __shfl_sync(0xffffffffu, rl, k));
+          if (lane == k) y = yk;
+          else if (lane > k && lane < pb) y = fma(-lr[k], yk, y);
+        }
       }
       if (lane < pb) xs[p + lane] = y;
     }
     __syncthreads();
     for (int i = p + pb + tid; i < n; i += blockDim.x) {
+      T lv[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) lv[k] = k < pb ? L[(int64_t)(p + k) * lda + i] : T(0);
       T t = xs[i];
-      for (int k = 0; k < pb; ++k) t = fma(-L[(int64_t)(p + k) * lda + i], xs[p + k], t);
+#pragma unroll
+      for (int k = 0; k < 32; ++k)
+        if (k < pb) t = fma(-lv[k], xs[p + k], t);
       xs[i] = t;
     }
     __syncthreads();
@@ -106,21 +120,32 @@ __device__ void block_solve_vec(const T *L, int64_t lda, int n, T *b, T *xs) {
   for (int p0 = ((n - 1) / 32) * 32; p0 >= 0; p0 -= 32) {  // L^T x = y
     const int pb = min(32, n - p0);
     if (tid < 32) {
+      T lc[32];  // column p0 + lane of the diagonal block (contiguous)
+#pragma unroll
+      for (int k = 0; k < 32; ++k) lc[k] = (lane < pb && k < pb) ? L[(int64_t)(p0 + lane) * lda + p0 + k] : T(0);
       T x = lane < pb ? xs[p0 + lane] : T(0);
       const T dl = lane < pb ? L[(int64_t)(p0 + lane) * lda + p0 + lane] : T(1);
       const T rl = T(1) / dl;
-      for (int k = pb - 1; k >= 0; --k) {
-        const T xk = bquot(__shfl_sync(0xffffffffu, x, k), __shfl_sync(0xffffffffu, dl, k),
-                           __shfl_sync(0xffffffffu, rl, k));
-        if (lane == k) x = xk;
-        else if (lane < k) x = fma(-L[(int64_t)(p0 + lane) * lda + p0 + k], xk, x);
+#pragma unroll
+      for (int k = 31; k >= 0; --k) {
+        if (k < pb) {
+          const T xk = bquot(__shfl_sync(0xffffffffu, x, k), __shfl_sync(0xffffffffu, dl, k),
+                             __shfl_sync(0xffffffffu, rl, k));
+          if (lane == k) x = xk;
+          else if (lane < k) x = fma(-lc[k], xk, x);
+        }
       }
       if (lane < pb) xs[p0 + lane] = x;
     }
     __syncthreads();
     for (int i = tid; i < p0; i += blockDim.x) {
+      T lv[32];  // row p0.. of column i (contiguous)
+#pragma unroll
+      for (int k = 0; k < 32; ++k) lv[k] = k < pb ? L[(int64_t)i * lda + p0 + k] : T(0);
       T t = xs[i];
-      for (int k = 0; k < pb; ++k) t = fma(-L[(int64_t)i * lda + p0 + k], xs[p0 + k], t);
+#pragma unroll
+      for (int k = 0; k < 32; ++k)
+        if (k < pb) t = fma(-lv[k], xs[p0 + k], t);
       xs[i] = t;
     }
     __syncthreads();
