@@ -101,7 +101,9 @@ def parse():
     p.add_argument("--adj-n", type=int, default=1024)
     p.add_argument("--adj-batch", type=int, default=64)
     p.add_argument("--adj-steps", type=int, default=10)
-    p.add_argument("--adj-streams", type=int, default=8)
+    p.add_argument("--adj-streams", type=int, default=16)
+    p.add_argument("--adj-nb", type=int, default=64, help="tile size of the adjoint leg's factors")
+    p.add_argument("--adj-workers", type=int, default=16, help="factor workers per matrix in the adjoint leg")
     p.add_argument("--no-probe", action="store_true", help="skip the FP64 throughput probe")
     p.add_argument("--fp64-probe-only", action="store_true",
                    help="run only the FP64 throughput probes (DFMA and the mma.sync .f64 shapes) and print them")
@@ -880,8 +882,9 @@ def run_adjoint(args, chol, dev):
     for every matrix the forward pass (factor + solve) and the backward pass (solve adjoint,
     then Cholesky adjoint) through the library's entry points, timed with CUDA events. The
     matrices are independent: they go round-robin to --adj-streams streams, and each factor
-    runs with 32 workers (a tile-128 factor of order 1024 has at most 28 ready tasks), so
-    several factorizations share the GPU. Flops per matrix: n^3/3 + 2n^2 forward; backward
+    runs with --adj-workers workers and tile --adj-nb (16 and 64: measured on the GB300
+    against tiles 32-256, 8-64 workers and 4-32 streams; a tile-64 factor of order 1024 has
+    at most 120 ready tasks, each one short), so several factorizations share the GPU. Flops per matrix: n^3/3 + 2n^2 forward; backward
     n^3/3 for L^T Lbar on the lower tiles, 2n^3 for the two triangular solves with n
     right-hand sides, O(n^2) for the rest."""
     import torch
@@ -891,7 +894,7 @@ def run_adjoint(args, chol, dev):
     bw = synth.rhs(n, 2 * m, seed=args.seed + 11, device=dev)
     bs = [chol.colmajor(bw[:, i:i + 1]) for i in range(m)]
     ws = [chol.colmajor(bw[:, m + i:m + i + 1]) for i in range(m)]
-    o = chol.opts(nb=128, num_workers=32)
+    o = chol.opts(nb=args.adj_nb, num_workers=args.adj_workers)
     main = torch.cuda.current_stream(dev)
     streams = [torch.cuda.Stream(dev) for _ in range(ns)]
     Fs = [torch.empty_like(As[0]) for _ in range(ns)]
@@ -941,8 +944,8 @@ def run_adjoint(args, chol, dev):
         ref = -0.5 * (lam @ x.T + x @ lam.T)
         worst = max(worst, float(torch.linalg.norm(grads[i] - ref) / torch.linalg.norm(ref)))
     return {"workload": "%d FP64 SPD matrices n=%d (A = sym(G G^T)/n + I), loss = sum(w * x), x = A^-1 b; "
-                        "forward factor + solve and backward solve + Cholesky adjoints per matrix, tile 128, "
-                        "%d streams, 32 factor workers per matrix" % (m, n, ns),
+                        "forward factor + solve and backward solve + Cholesky adjoints per matrix, tile %d, "
+                        "%d streams, %d factor workers per matrix" % (m, n, args.adj_nb, ns, args.adj_workers),
             "ms": round(ms, 2), "ms_stat": stat(step_ms, 2), "ms_per_matrix": round(ms / m, 3),
             "flops_per_step": flops,
             "gflops": round(flops / ms / 1e6, 1), "frac_of_fp64_peak": round(flops / ms / 1e6 / FP64_PEAK_GFLOPS, 4),
