@@ -285,44 +285,52 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
         for (int q = 0; q < NC; ++q) acc[rr][q] = T(0);
       const int nsteps = REV ? a.nrb - 1 - r : r;
       // the solved blocks are consumed in 32-row chunks, one chunk per warp step: chunk kc of
-      // block m is step m * RPL + kc, so the chunks of the newest block go to different warps
+      // block m is step m * RPL + kc, so the chunks of the newest block go to different warps.
+      // FP64 forward-read sweeps with one or two columns cut every chunk into QTR quarters of
+      // its 32 k values, dealt to consecutive warps (different SM sub-partitions): a warp-wide
+      // FP64 instruction costs its sub-partition ~64 cycles, so the newest block's 32 dependent
+      // FMAs on one warp were ~2000 cycles of every link of the chain, and are ~500 split
+      constexpr int QTR = (!INV && !TRANS && NC <= 2 && SBK == 32) ? 4 : 1;
+      constexpr int KQ = SB / QTR;
       const int nchunks = nsteps * RPL;
+      const int nunits = nchunks * QTR;
       int wab = 0;
-      // readiness of the warp's next 32 chunks: bit j <-> step mbase + SNW j, one flag load per
+      // readiness of the warp's next 32 units: bit j <-> unit mbase + SNW j, one flag load per
       // lane and a ballot, so blocks solved long ago cost no polling round trip
       unsigned ready = 0u;
       int mbase = warp;
-      for (int step = warp; step < nchunks; step += SNW) {
+      for (int unit = warp; unit < nunits; unit += SNW) {
+        const int step = unit / QTR, kq0 = (unit % QTR) * KQ;
         const int mi = step / RPL, kc = step % RPL;
         const int m = REV ? a.nrb - 1 - mi : mi;
         const int k0 = m * SBK + SB * kc, krows = min(SB, a.n - k0);  // this 32-row chunk of block m
         // L chunk, issued before any wait (it does not depend on other items). Forward: lane =
         // row of the item, lr[rr][k] = L(r0 + lane + 32 rr, k0 + k). Backward: lane = row k0 +
         // lane, lb[i] = L(k0 + lane, r0 + i), staged transposed below.
-        T lr[TRANS ? 1 : RPL][SB];
+        T lr[TRANS ? 1 : RPL][KQ];
         T lb[TRANS ? SBK : 1];
         if (!TRANS) {
   #pragma unroll
           for (int rr = 0; rr < RPL; ++rr)
   #pragma unroll
-            for (int k = 0; k < SB; ++k)
-              lr[rr][k] = (lane + SB * rr < rows && k < krows)
-                              ? __ldcg(L + (int64_t)(k0 + k) * a.lda + r0 + lane + SB * rr) : T(0);
+            for (int kk = 0; kk < KQ; ++kk)
+              lr[rr][kk] = (lane + SB * rr < rows && kq0 + kk < krows)
+                               ? __ldcg(L + (int64_t)(k0 + kq0 + kk) * a.lda + r0 + lane + SB * rr) : T(0);
         } else {
   #pragma unroll
           for (int i = 0; i < SBK; ++i)
             lb[i] = (lane < krows && i < rows) ? __ldcg(L + (int64_t)(r0 + i) * a.lda + k0 + lane) : T(0);
         }
-        int jb = (step - mbase) / SNW;
+        int jb = (unit - mbase) / SNW;
         if (jb >= 32 || !((ready >> jb) & 1u)) {
-          const int sl = step + SNW * lane;
+          const int sl = unit + SNW * lane;
           int f = 1;
-          if (sl < nchunks) {
-            const int ml = REV ? a.nrb - 1 - sl / RPL : sl / RPL;
+          if (sl < nunits) {
+            const int ml = REV ? a.nrb - 1 - sl / QTR / RPL : sl / QTR / RPL;
             f = ld_volatile(&a.flags[(int64_t)ml * a.ngroups + g]) != 0;
           }
           ready = __ballot_sync(0xffffffffu, f);
-          mbase = step;
+          mbase = unit;
           if (!(ready & 1u)) {
             // wait until block m of this group is solved (one lane, bounded)
             if (lane == 0) {
@@ -362,10 +370,11 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
         }
         __syncwarp();
   #pragma unroll
-        for (int k = 0; k < SB; ++k) {
+        for (int kk = 0; kk < KQ; ++kk) {
+          const int k = kq0 + kk;
           T l[RPL];
   #pragma unroll
-          for (int rr = 0; rr < RPL; ++rr) l[rr] = TRANS ? lt[k * DLD + lane + SB * rr] : lr[TRANS ? 0 : rr][k];
+          for (int rr = 0; rr < RPL; ++rr) l[rr] = TRANS ? lt[k * DLD + lane + SB * rr] : lr[TRANS ? 0 : rr][kk];
   #pragma unroll
           for (int q = 0; q < NC; q += V) {
             T y[V];
