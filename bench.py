@@ -84,7 +84,7 @@ def parse():
     p.add_argument("--alpha", type=float, default=0.5)
     p.add_argument("--workers-per-sm", type=int, default=2)
     p.add_argument("--cp", action="store_true", help="communication prediction in the placement")
-    p.add_argument("--e2e-steps", type=int, default=1)
+    p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-n", type=int, default=10240)
@@ -966,20 +966,23 @@ def run_e2e(args, chol, A0, B0, o, dev):
     stage = torch.empty(chol.lib.chol_posv_host_stage_size(n, nrhs, __import__("ctypes").byref(o)),
                         dtype=torch.uint8, device=dev)
     tt = 0.0
+    step_ms = []
     for _ in range(max(1, args.e2e_steps)):
         hA[...] = hA0
         hB[...] = hB0
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         info = chol.posv_host(hA, hB, o, stage=stage)
-        tt += time.perf_counter() - t0
+        dt = time.perf_counter() - t0
+        tt += dt
+        step_ms.append(dt * 1e3)
         if info != 0:
             raise RuntimeError("posv_host info %d" % info)
     steps = max(1, args.e2e_steps)
     del stage
     return {"value": round(step_flops(n, nrhs) * steps / tt / 1e9, 2), "unit": "GFLOP/s",
             "h2d_bytes_per_step": n * n * 8 + n * nrhs * 8, "d2h_bytes_per_step": n * n * 8 + n * nrhs * 8 + 4,
-            "steps": steps, "api": "chol_posv_host (pinned host buffers)"}
+            "steps": steps, "step_ms": stat(step_ms, 2), "api": "chol_posv_host (pinned host buffers)"}
 
 
 if __name__ == "__main__":
