@@ -398,6 +398,15 @@ chol_status chol_lu_dag_describe(int T, int *kind, int *ti, int *tj, int *tk, in
                                  long long *succ_ptr, long long *succ);
 chol_status chol_lu_dag_bottom_levels(int T, const long long *cost_ns, long long *bl);
 
+/* The bottom levels as the device computes them before every factor launch with
+ * bottom-level queues (one block, step by step from k = T-1 down, per-step maxima in shared
+ * memory): the Cholesky graph for lu = 0, the tile LU graph for lu = 1. cost_ns[4] is a HOST
+ * array; dBl is DEVICE memory of chol_dag_task_count(T) (lu = 0) or chol_lu_dag_task_count(T)
+ * (lu = 1) entries, all written. Asynchronous on `stream`; the values equal the host
+ * functions' above. Returns CHOL_ERR_INVALID_ARG for T < 1, T > 1024 or a NULL pointer. */
+chol_status chol_dag_bottom_levels_device(int lu, int T, const long long *cost_ns, long long *dBl,
+                                          void *stream);
+
 /* One activate operation on identical workers (Algorithm 1 for CHOL_POLICY_HEFT,
  * Algorithm 2 for CHOL_POLICY_DADA). Ready list of m tasks: task ids tid[m], processing
  * times p[m] (ns), priorities prio[m] (bottom levels), affinity worker aff[m] (-1: none)

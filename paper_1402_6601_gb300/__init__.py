@@ -23,7 +23,7 @@ __all__ = [
     "cholesky", "cholesky_solve", "solve_spd", "BatchOpts", "Batch", "posv_batched", "factor_batched",
     "solve_batched", "batched_autotune", "lu_factor", "lu_solve", "lu_workspace_size", "lu_solve_workspace_size",
     "LUFactors",
-    "dag_describe", "dag_bottom_levels", "lu_dag_describe", "lu_dag_bottom_levels", "chrome_trace", "sched_activate", "sched_activate_device",
+    "dag_describe", "dag_bottom_levels", "lu_dag_describe", "lu_dag_bottom_levels", "dag_bottom_levels_device", "chrome_trace", "sched_activate", "sched_activate_device",
     "CholeskyError", "probe_fp64",
 ]
 
@@ -110,6 +110,7 @@ _SIGNATURES = {
     "chol_dag_edge_count": (_LL, [_I]),
     "chol_dag_describe": (_I, [_I, _P, _P, _P, _P, _P, _P, _P]),
     "chol_dag_bottom_levels": (_I, [_I, _P, _P]),
+    "chol_dag_bottom_levels_device": (_I, [_I, _I, _P, _P, _P]),
     "chol_sched_activate": (_I, [_I, _D, _I, _D, _I, _P, _P, _P, _P, _P, _I, _P, _P, _P, _I, _P, _P, _P, _P]),
     "chol_sched_activate_device": (_I, [_I, _D, _I, _D, _I, _P, _P, _P, _P, _P, _I, _P, _P, _P, _I, _P, _P, _P,
                                         _P, _P]),
@@ -490,6 +491,20 @@ def sched_activate(policy, tasks, load, alpha=0.5, max_iter=16, eps=0.01, use_cp
                                    ld.ctypes.data, ot.ctypes.data, ow.ctypes.data, ctypes.byref(it)),
            "chol_sched_activate")
     return [(int(a), int(b)) for a, b in zip(ot[:m], ow[:m])], int(it.value)
+
+
+def dag_bottom_levels_device(T, cost_ns, lu=False, device="cuda", stream=None):
+    """Bottom levels computed by the device kernel that prepares each factor launch
+    (int64 CUDA tensor, one entry per task id)."""
+    import numpy as np
+    count = lib.chol_lu_dag_task_count(T) if lu else lib.chol_dag_task_count(T)
+    if count < 1:
+        raise ValueError(f"no task graph for T={T}")
+    c = np.ascontiguousarray(cost_ns, dtype=np.int64)
+    out = torch.empty(int(count), dtype=torch.int64, device=device)
+    _check(lib.chol_dag_bottom_levels_device(int(bool(lu)), T, c.ctypes.data, out.data_ptr(), _stream(stream)),
+           "chol_dag_bottom_levels_device")
+    return out
 
 
 def sched_activate_device(policy, tasks, load, alpha=0.5, max_iter=16, eps=0.01, device="cuda", use_cp=False):

@@ -7,6 +7,7 @@
 #include "common.cuh"
 #include "dag.cuh"
 #include "dag_lu.cuh"
+#include "internal.cuh"
 #include "sched.cuh"
 
 namespace chol {
@@ -183,6 +184,13 @@ extern "C" chol_status chol_lu_dag_bottom_levels(int T, const long long *cost_ns
   // every successor has a larger id: reverse id order
   for (int64_t id = LuGraph::count(T) - 1; id >= 0; --id) b[id] = LuGraph::bottom_level_of(T, LuGraph::desc(T, id), cost, b);
   return CHOL_OK;
+}
+
+extern "C" chol_status chol_dag_bottom_levels_device(int lu, int T, const long long *cost_ns, long long *dBl,
+                                                     void *stream) {
+  if (T < 1 || T > 1024 || !cost_ns || !dBl) return CHOL_ERR_INVALID_ARG;
+  const int64_t cost[4] = {cost_ns[0], cost_ns[1], cost_ns[2], cost_ns[3]};
+  return bottom_levels_device(lu != 0, T, cost, reinterpret_cast<int64_t *>(dBl), (cudaStream_t)stream);
 }
 
 extern "C" chol_status chol_dag_bottom_levels(int T, const long long *cost_ns, long long *bl) {

@@ -1022,56 +1022,164 @@ __global__ void init_kernel(int T, int64_t ntasks, int *cnt, int *owner, int64_t
     owner[t] = -1;
 }
 
-// Bottom levels by steps k = T-1 .. 0; inside a step GEMM/SYRK first (their successors are
-// in step k+1), then TRSM (successors in step k), then POTRF. One block.
+// Bottom levels as order-preserving unsigned keys, so the per-step maxima can be taken with
+// shared-memory atomicMax; BL_ZERO is the key of 0, the start of every maximum (a task
+// without successors has bottom level = its cost).
+constexpr unsigned long long BL_SIGN = 0x8000000000000000ull;
+constexpr unsigned long long BL_ZERO = BL_SIGN;
+__device__ __forceinline__ unsigned long long bl_key(int64_t v) { return (unsigned long long)v ^ BL_SIGN; }
+__device__ __forceinline__ int64_t bl_val(unsigned long long k) { return (int64_t)(k ^ BL_SIGN); }
+
+__device__ __forceinline__ unsigned long long warp_max_key(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+// Bottom levels of the Cholesky graph by steps k = T-1 .. 0 (one block). Each SYRK(i, k) and
+// GEMM(i, j, k) has its one successor in step k+1 (already known); one warp takes tile row
+// i of the step (SYRK(i, k) and the GEMM(i, j, k), a lane each) and folds the values into
+// the maxima, in shared memory, of the TRSMs they follow: TRSM(i, k) precedes SYRK(i, k),
+// GEMM(i, *, k) and GEMM(*, i, k). The TRSMs then fold theirs into the POTRF's maximum and
+// POTRF(k) closes the step. tmax[b][t] holds TRSM(k+1+t, k)'s maximum and tmax[b][m] the
+// POTRF's; the two buffers alternate with the parity of k and the next step's buffer is
+// cleared behind the last barrier of this one. The row maxima are reduced across the warp
+// first, so no two lanes of a warp update one entry at once.
 __global__ void __launch_bounds__(1024) bottom_level_kernel(int T, int64_t c0, int64_t c1, int64_t c2,
                                                             int64_t c3, int64_t *bl) {
-  const int64_t cost[4] = {c0, c1, c2, c3};
+  __shared__ unsigned long long tmax[2][1025];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int t = threadIdx.x; t < 2 * 1025; t += blockDim.x) (&tmax[0][0])[t] = BL_ZERO;
+  __syncthreads();
   for (int k = T - 1; k >= 0; --k) {
+    unsigned long long *mx = tmax[k & 1];
     const int64_t base = step_offset(T, k);
-    const int64_t m = T - 1 - k;
-    const int64_t end = base + step_size(m);
-    for (int64_t id = base + 1 + m + threadIdx.x; id < end; id += blockDim.x)
-      bl[id] = bottom_level_of(T, task_desc(T, id), cost, bl);
+    const int m = T - 1 - k;
+    for (int ip = warp; ip < m; ip += nwarps) {
+      const int i = k + 1 + ip;
+      unsigned long long rowkey = BL_ZERO;
+      for (int t0 = 0; t0 <= ip; t0 += 32) {
+        const int t = t0 + lane;
+        if (t <= ip) {
+          int64_t id, sid, c;
+          if (t == 0) {  // SYRK(i, k) -> POTRF(i) or SYRK(i, k+1)
+            id = task_id(T, K_SYRK, i, i, k);
+            sid = ip == 0 ? task_id(T, K_POTRF, i, i, i) : task_id(T, K_SYRK, i, i, k + 1);
+            c = c2;
+          } else {  // GEMM(i, j, k) -> TRSM(i, j) or GEMM(i, j, k+1)
+            const int j = k + t;
+            id = task_id(T, K_GEMM, i, j, k);
+            sid = j == k + 1 ? task_id(T, K_TRSM, i, j, j) : task_id(T, K_GEMM, i, j, k + 1);
+            c = c3;
+          }
+          const int64_t sv = bl[sid];
+          const int64_t v = c + (sv > 0 ? sv : 0);
+          bl[id] = v;
+          const unsigned long long key = bl_key(v);
+          rowkey = key > rowkey ? key : rowkey;
+          if (t > 0) atomicMax(&mx[t - 1], key);  // GEMM(i, j, k) also follows TRSM(j, k)
+        }
+      }
+      rowkey = warp_max_key(rowkey);
+      if (lane == 0) atomicMax(&mx[ip], rowkey);
+    }
     __syncthreads();
-    for (int64_t id = base + 1 + threadIdx.x; id <= base + m; id += blockDim.x)
-      bl[id] = bottom_level_of(T, task_desc(T, id), cost, bl);
+    for (int t0 = warp * 32; t0 < m; t0 += blockDim.x) {
+      const int t = t0 + lane;
+      unsigned long long key = BL_ZERO;
+      if (t < m) {
+        const int64_t v = c1 + bl_val(mx[t]);
+        bl[base + 1 + t] = v;
+        key = bl_key(v);
+      }
+      key = warp_max_key(key);
+      if (lane == 0) atomicMax(&mx[m], key);
+    }
     __syncthreads();
-    if (threadIdx.x == 0) bl[base] = bottom_level_of(T, task_desc(T, base), cost, bl);
+    if (threadIdx.x == 0) bl[base] = c0 + bl_val(mx[m]);
+    unsigned long long *nx = tmax[(k - 1) & 1];
+    for (int t = threadIdx.x; t <= m; t += blockDim.x) nx[t] = BL_ZERO;
     __syncthreads();
   }
 }
 
-// Bottom levels of the LU graph by steps k = T-1 .. 0. Inside a step the SSSSM and TSTRF
-// chains run down the tile rows: for i = T-1 .. k+1 the SSSSM(i, j, k) (successors in row
-// i+1 and in step k+1), then TSTRF(i, k); then the GESSM, then GETRF(k). One block.
+// Bottom levels of the LU graph by steps k = T-1 .. 0 (one block). In step k the SSSSMs of
+// tile column j form a chain down the rows (SSSSM(i, j, k) precedes SSSSM(i+1, j, k) and the
+// next writer of tile (i, j) in step k+1), so one thread per column walks i = T-1 .. k+1:
+// S(i) = c3 + max(0, next writer, S(i+1)); it then writes GESSM(k, j) (successor SSSSM(k+1,
+// j, k)). Each S(i) goes into row i's maximum (reduced across the warp first: the lanes of a
+// warp walk the same row together) and GESSM(k, j) into GETRF(k)'s. The TSTRF chain,
+// TSTRF(i, k) = c2 + max(row i's maximum, TSTRF(i+1, k)), and GETRF(k) = c0 + max(GESSMs,
+// TSTRF(k+1, k)) are then taken by one thread from shared memory. rmax[b][t] holds row
+// k+1+t's maximum, rmax[b][m] GETRF(k)'s; the buffers alternate with the parity of k.
 __global__ void __launch_bounds__(1024) lu_bottom_level_kernel(int T, int64_t c0, int64_t c1, int64_t c2,
                                                                int64_t c3, int64_t *bl) {
-  const int64_t cost[4] = {c0, c1, c2, c3};
+  __shared__ unsigned long long rmax[2][1025];
+  const int lane = threadIdx.x & 31;
+  for (int t = threadIdx.x; t < 2 * 1025; t += blockDim.x) (&rmax[0][0])[t] = BL_ZERO;
+  __syncthreads();
   for (int k = T - 1; k >= 0; --k) {
-    for (int i = T - 1; i > k; --i) {
-      for (int j = k + 1 + threadIdx.x; j < T; j += blockDim.x) {
-        const int64_t id = LuGraph::id(T, K_SSSSM, i, j, k);
-        bl[id] = LuGraph::bottom_level_of(T, LuGraph::desc(T, id), cost, bl);
+    unsigned long long *mx = rmax[k & 1];
+    const int m = T - 1 - k;
+    // warps with at least one column walk the rows together (m <= 1023 < 1024 threads)
+    if ((threadIdx.x & ~31) < m) {
+      const int jj = threadIdx.x;
+      const bool act = jj < m;
+      const int j = k + 1 + jj;
+      int64_t S = 0;
+      // the next writer of tile (i, j) is in step k+1: its value is loaded one row ahead
+      int64_t nv_next = act ? bl[LuGraph::succ(T, TaskDesc{K_SSSSM, T - 1, j, k}, 0)] : 0;
+      for (int i = T - 1; i > k; --i) {
+        unsigned long long key = 0;  // below every key: no contribution
+        if (act) {
+          const int64_t nv = nv_next;
+          if (i - 1 > k) nv_next = bl[LuGraph::succ(T, TaskDesc{K_SSSSM, i - 1, j, k}, 0)];
+          int64_t best = nv > 0 ? nv : 0;
+          if (i + 1 < T && S > best) best = S;
+          S = c3 + best;
+          bl[LuGraph::id(T, K_SSSSM, i, j, k)] = S;
+          key = bl_key(S);
+        }
+        key = warp_max_key(key);
+        if (lane == 0) atomicMax(&mx[i - k - 1], key);
       }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        const int64_t id = LuGraph::id(T, K_TSTRF, i, k, k);
-        bl[id] = LuGraph::bottom_level_of(T, LuGraph::desc(T, id), cost, bl);
+      unsigned long long gkey = 0;
+      if (act) {
+        const int64_t g = c1 + (S > 0 ? S : 0);
+        bl[LuGraph::id(T, K_GESSM, k, j, k)] = g;
+        gkey = bl_key(g);
       }
-      __syncthreads();
-    }
-    for (int j = k + 1 + threadIdx.x; j < T; j += blockDim.x) {
-      const int64_t id = LuGraph::id(T, K_GESSM, k, j, k);
-      bl[id] = LuGraph::bottom_level_of(T, LuGraph::desc(T, id), cost, bl);
+      gkey = warp_max_key(gkey);
+      if (lane == 0) atomicMax(&mx[m], gkey);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      const int64_t id = LuGraph::id(T, K_GETRF, k, k, k);
-      bl[id] = LuGraph::bottom_level_of(T, LuGraph::desc(T, id), cost, bl);
+      int64_t R = 0;
+      for (int i = T - 1; i > k; --i) {
+        int64_t best = bl_val(mx[i - k - 1]);
+        if (i + 1 < T && R > best) best = R;
+        R = c2 + best;
+        bl[LuGraph::id(T, K_TSTRF, i, k, k)] = R;
+      }
+      int64_t best = bl_val(mx[m]);
+      if (m > 0 && R > best) best = R;
+      bl[LuGraph::id(T, K_GETRF, k, k, k)] = c0 + best;
     }
+    unsigned long long *nx = rmax[(k - 1) & 1];
+    for (int t = threadIdx.x; t <= m; t += blockDim.x) nx[t] = BL_ZERO;
     __syncthreads();
   }
+}
+
+chol_status bottom_levels_device(bool lu, int T, const int64_t *cost, int64_t *dBl, cudaStream_t s) {
+  if (T < 1 || T > 1024) return CHOL_ERR_INVALID_ARG;
+  if (lu) lu_bottom_level_kernel<<<1, 1024, 0, s>>>(T, cost[0], cost[1], cost[2], cost[3], dBl);
+  else bottom_level_kernel<<<1, 1024, 0, s>>>(T, cost[0], cost[1], cost[2], cost[3], dBl);
+  CHOL_CUDA_TRY(cudaGetLastError());
+  return CHOL_OK;
 }
 
 __global__ void copy_info_kernel(const Ctrl *ctrl, int *dInfo) {
@@ -1311,9 +1419,8 @@ chol_status factor_impl(int prec, int n, void *dA, int lda, const chol_opts *opt
     CHOL_CUDA_TRY(cudaGetLastError());
   }
   if (r.queue_order == 0) {
-    if (r.lu) lu_bottom_level_kernel<<<1, 1024, 0, s>>>(r.T, r.cost[0], r.cost[1], r.cost[2], r.cost[3], a.bl);
-    else bottom_level_kernel<<<1, 1024, 0, s>>>(r.T, r.cost[0], r.cost[1], r.cost[2], r.cost[3], a.bl);
-    CHOL_CUDA_TRY(cudaGetLastError());
+    const chol_status bs = bottom_levels_device(r.lu, r.T, r.cost, a.bl, s);
+    if (bs != CHOL_OK) return bs;
   }
   const size_t smem = factor_smem_bytes(prec, r.T, W);
   void *args[] = {(void *)&a};

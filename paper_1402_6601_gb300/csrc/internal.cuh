@@ -32,4 +32,8 @@ chol_status solve_upper_f64(int n, int nrhs, const double *dU, int lda, double *
                             const int *prev_abort, cudaStream_t s);
 chol_status solve_upper_info(void *dWork, int *dInfo, cudaStream_t s);
 
+// Bottom levels of every task of the Cholesky (lu = false) or tile LU graph with T x T tiles
+// and per-kind costs cost[4], written to dBl (device, one entry per task id) on stream s.
+chol_status bottom_levels_device(bool lu, int T, const int64_t *cost, int64_t *dBl, cudaStream_t s);
+
 }  // namespace chol

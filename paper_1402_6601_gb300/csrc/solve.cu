@@ -83,7 +83,11 @@ struct SolveSmem {
   static constexpr size_t YS = (size_t)SBK * YLD;       // the item's block before the diagonal solve
   static constexpr size_t LD = (size_t)SBK * DLD + SBK; // diagonal block and its reciprocals
   static constexpr size_t DI = (size_t)SBK * MLD;       // inverse of the diagonal block (FP32)
-  static constexpr size_t NEED = (YW + LT + YS + LD + DI) * sizeof(T);
+  // FP32: the newest solved block's L block G and W = D^-1 G (D^-T G backward), k-major
+  static constexpr bool NW = sizeof(T) == 4;
+  static constexpr size_t GS = NW ? (size_t)SBK * DLD : 0;
+  static constexpr size_t WM = NW ? (size_t)SBK * MLD : 0;
+  static constexpr size_t NEED = (YW + LT + YS + LD + DI + GS + WM) * sizeof(T);
   static constexpr size_t BYTES = NEED > (size_t)SOLVE_EXCL_SMEM ? NEED : (size_t)SOLVE_EXCL_SMEM;
 };
 
@@ -127,6 +131,8 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
   T *Ld = Ys + S::YS;
   T *Rs = Ld + SBK * DLD;
   T *Mi = Rs + SBK;  // 16-byte aligned: YW, LT, YS and LD are multiples of four elements
+  T *Gs = Mi + S::DI;
+  T *Wm = Gs + S::GS;  // 16-byte aligned: DI and GS are multiples of four elements
   __shared__ long long s_item;
   __shared__ int s_abort;
   __shared__ T s_xk[2][32];  // x_k of every column, by step parity (diagonal solve)
@@ -159,6 +165,24 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
       Ld[i * DLD + j] = (i < rows && j < rows && i >= j) ? __ldcg(L + at) : (i == j ? T(1) : T(0));
     }
     if (tid < SBK) Rs[tid] = tid < rows ? T(1) / __ldcg(L + (int64_t)(r0 + tid) * a.lda + r0 + tid) : T(1);
+    // FP32: the solved block next to this one (r - 1 forward, r + 1 backward) is the last to
+    // arrive; its contribution is applied after the diagonal product as W y with W = D^-1 G
+    // (D^-T G backward), G(j, k) = L(r0 + j, mN0 + k) forward, L(mN0 + k, r0 + j) backward,
+    // so the chain of block rows holds one SBK x SBK product per link instead of the newest
+    // block's partial products, the sum over the warps and the diagonal product
+    const int nsteps_all = REV ? a.nrb - 1 - r : r;
+    const bool newest = INV && nsteps_all > 0;
+    const int mN = REV ? r + 1 : r - 1;
+    const int mN0 = mN * SBK, mrows = newest ? min(SBK, a.n - mN0) : 0;
+    if constexpr (INV) {
+      if (newest) {
+        for (int e = tid; e < SBK * SBK; e += SNT) {
+          const int j = TRANS ? e / SBK : e % SBK, k = TRANS ? e % SBK : e / SBK;
+          const int64_t at = TRANS ? (int64_t)(r0 + j) * a.lda + mN0 + k : (int64_t)(mN0 + k) * a.lda + r0 + j;
+          Gs[j * DLD + k] = (j < rows && k < mrows) ? __ldcg(L + at) : T(0);
+        }
+      }
+    }
     if constexpr (INV) {
       // D^-1 by columns: thread j of the first SBK threads solves D y = e_j (right-looking;
       // y stays zero above row j) while the other warps start accumulating. It is stored as
@@ -175,6 +199,21 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
           col[k * cs] = yk;
 #pragma unroll 4
           for (int i = k + 1; i < SBK; ++i) col[i * cs] = fma(-Ld[i * DLD + k], yk, col[i * cs]);
+        }
+        if (newest) {
+          // the same threads, once the whole inverse is in place: row i = tid of W, stored
+          // k-major like Mi, W(i, k) = sum_j Dop(i, j) G(j, k) with Dop(i, j) = Mi[j MLD + i]
+          asm volatile("bar.sync 1, %0;" ::"r"(SBK));
+          const int i = tid;
+          T mrow[SBK];
+#pragma unroll
+          for (int jj = 0; jj < SBK; ++jj) mrow[jj] = Mi[jj * MLD + i];
+          for (int k = 0; k < SBK; ++k) {
+            T w = T(0);
+#pragma unroll
+            for (int jj = 0; jj < SBK; ++jj) w = fma(mrow[jj], Gs[jj * DLD + k], w);
+            Wm[k * MLD + i] = w;
+          }
         }
       }
     }
@@ -283,7 +322,8 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
       for (int rr = 0; rr < RPL; ++rr)
   #pragma unroll
         for (int q = 0; q < NC; ++q) acc[rr][q] = T(0);
-      const int nsteps = REV ? a.nrb - 1 - r : r;
+      // (FP32: all solved blocks but the newest, which follows the diagonal product)
+      const int nsteps = newest ? nsteps_all - 1 : nsteps_all;
       // the solved blocks are consumed in 32-row chunks, one chunk per warp step: chunk kc of
       // block m is step m * RPL + kc, so the chunks of the newest block go to different warps.
       // FP64 forward-read sweeps with one or two columns cut every chunk into QTR quarters of
@@ -435,6 +475,53 @@ __global__ void __launch_bounds__(SNT, 1) solve_kernel(const __grid_constant__ S
         }
 #pragma unroll
         for (int u = 0; u < RPT; ++u) Xo[(i0 + u) * YLD + q] = t[u];
+      }
+      if (newest) {
+        // wait for the newest block (one thread, bounded), stage it in Ys (free now) and
+        // subtract W y from the diagonal product
+        __syncthreads();
+        if (tid == 0) {
+          const uint64_t t0 = globaltimer_ns();
+          int64_t spins = 0;
+          while (ld_volatile(&a.flags[(int64_t)mN * a.ngroups + g]) == 0) {
+            if (ld_volatile(&a.ctrl->abort)) { s_abort = 1; break; }
+            if (globaltimer_ns() - t0 > (uint64_t)a.timeout_ns || ++spins > (a.timeout_ns >> 7) + 100000) {
+              atomicCAS(&a.ctrl->info, 0, CHOL_INFO_TIMEOUT);
+              atomicExch(&a.ctrl->abort, 1);
+              s_abort = 1;
+              break;
+            }
+            __nanosleep(32);
+          }
+          // the flag is ordered before the block's data
+          __threadfence();
+        }
+        __syncthreads();
+        if (s_abort) break;
+        for (int e = tid; e < SBK * NC; e += SNT) {
+          const int k = e % SBK, q = e / SBK;
+          Ys[k * YLD + q] = (k < mrows && q < cols) ? __ldcg(B + (int64_t)(c0 + q) * a.ldb + mN0 + k) : T(0);
+        }
+        __syncthreads();
+        if (tid < SBK * NC / RPT) {
+          const int q = tid % NC, i0 = (tid / NC) * RPT;
+          T t[RPT];
+#pragma unroll
+          for (int u = 0; u < RPT; ++u) t[u] = Xo[(i0 + u) * YLD + q];
+#pragma unroll 8
+          for (int k = 0; k < SBK; ++k) {
+            const T y = Ys[k * YLD + q];
+#pragma unroll
+            for (int u = 0; u < RPT; u += 4) {
+              T m[4];
+              vload<T, 4>(Wm + k * MLD + i0 + u, m);
+#pragma unroll
+              for (int v = 0; v < 4; ++v) t[u + v] = fma(-m[v], y, t[u + v]);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < RPT; ++u) Xo[(i0 + u) * YLD + q] = t[u];
+        }
       }
     } else if (cols <= SNW / 2) {
       // diagonal block, at most 4 right-hand sides: one warp per right-hand side (one per SM

@@ -201,6 +201,41 @@ def test_sweeps_exact_on_integers(chol, n, nrhs):
     np.testing.assert_array_equal(Bd.cpu().numpy(), X)
 
 
+@pytest.mark.parametrize("lu", [False, True])
+@pytest.mark.parametrize("T", [1, 2, 3, 6, 9])
+def test_device_bottom_levels_match_oracle(chol, lu, T):
+    # the bottom levels the device computes before each factor launch (Section 3.1's upward
+    # rank), against the oracle's longest-path recursion over the access-mode graph
+    import oracle.dag as odag
+    cost = [11, 30, 29, 60] if lu else [7, 30, 31, 60]
+    bl = chol.dag_bottom_levels_device(T, cost, lu=lu).cpu().numpy()
+    kind, ti, tj, tk, *_ = chol.lu_dag_describe(T) if lu else chol.dag_describe(T)
+    prog = odag.program_lu(T) if lu else None
+    ref = odag.bottom_levels(T, dict(enumerate(cost)), prog) if lu else odag.bottom_levels(T, dict(enumerate(cost)))
+    assert len(bl) == len(ref)
+    for i in range(len(bl)):
+        assert bl[i] == ref[(int(kind[i]), int(ti[i]), int(tj[i]), int(tk[i]))]
+
+
+@pytest.mark.parametrize("lu", [False, True])
+@pytest.mark.parametrize("T,cost", [(32, [7, 30, 31, 60]), (64, [3_500, 9_000, 12_000, 20_000]),
+                                    (130, [1, 1, 1, 1]), (64, [5, 0, 2, 0]), (17, [4, -3, 0, 2])])
+def test_device_bottom_levels_match_host(chol, lu, T, cost):
+    # larger graphs against the library's host recursion, which the oracle pins above; zero
+    # and negative costs check that every maximum starts from 0 as the host's does
+    dev = chol.dag_bottom_levels_device(T, cost, lu=lu).cpu().numpy()
+    host = chol.lu_dag_bottom_levels(T, cost) if lu else chol.dag_bottom_levels(T, cost)
+    assert np.array_equal(dev, host)
+
+
+def test_device_bottom_levels_large_T(chol):
+    # T = 400 (10.7 million Cholesky tasks: n = 51200 at tile 128), every step with more
+    # tasks than the block has threads
+    cost = [2_000, 5_000, 6_000, 11_000]
+    dev = chol.dag_bottom_levels_device(400, cost).cpu().numpy()
+    assert np.array_equal(dev, chol.dag_bottom_levels(400, cost))
+
+
 def test_sched_device_matches_host(chol):
     import random
     rng = random.Random(3)

@@ -85,7 +85,8 @@ def test_refine_reaches_fp64_backward_error(chol, n, nrhs, nb):
     np.testing.assert_array_equal(Ad.cpu().numpy(), A)
 
 
-@pytest.mark.parametrize("n,nrhs", [(1, 1), (63, 2), (64, 16), (65, 5), (777, 16), (1100, 33), (1024, 64)])
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (63, 2), (64, 16), (65, 5), (127, 1), (128, 3), (777, 16), (1100, 33),
+                                    (1024, 64), (4097, 16), (3000, 1)])
 def test_f32_solve_matches_oracle_substitution(chol, n, nrhs):
     """The first refinement step from x0 = 0 returns the FP32 forward and back substitution of
     b (rounded to FP32) with the FP32 factor (no diagonal scaling in this form). The oracle
