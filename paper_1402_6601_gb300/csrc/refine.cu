@@ -39,8 +39,10 @@ __device__ __forceinline__ void atomic_max_nonneg(double *p, double v) {
 }
 
 // One 32 x 32 tile (I, J), I >= J, of the lower triangle per block (32 x 8 threads): A32 =
-// float(A) (with `scale`, nullable: D^-1/2 A D^-1/2, scale_i = 1 / sqrt(a_ii), 1 where
-// a_ii <= 0, applied in FP64 before rounding), and the absolute row sums of the symmetric A
+// float(A) (with `scale`, nullable: S A S with the powers of two of diag_scale_kernel, applied
+// exactly before rounding: v s_i s_j by adding the scales' exponents to v's, which keeps the
+// FP64 pipe to one conversion per entry; the FP64 product, exact as well, covers zeros,
+// subnormals, infinities and results outside the normal range), and the absolute row sums of the symmetric A
 // accumulated into rsum: |a_ij| counts for row i and, below the diagonal, for row j. The sums
 // are FP32 (the norm only scales the backward error, and FP64 adds would run on the FP64
 // pipe); entries above the diagonal of A32 are not written (nothing reads them).
@@ -58,7 +60,16 @@ __global__ void __launch_bounds__(256) convert_lower_kernel(const double *A, int
     double v = 0.0;
     if (i < n && j < n && i >= j) {
       v = A[(int64_t)j * lda + i];
-      A32[(int64_t)j * lda32 + i] = (float)(scale ? v * scale[i] * scale[j] : v);
+      double vs = v;
+      if (scale) {
+        const double si = scale[i], sj = scale[j];
+        const int k = ((__double2hiint(si) >> 20) & 0x7ff) + ((__double2hiint(sj) >> 20) & 0x7ff) - 2046;
+        const int hi = __double2hiint(v);
+        const int E = (hi >> 20) & 0x7ff;
+        vs = (E > 0 && E < 2047 && E + k > 0 && E + k < 2047) ? __hiloint2double(hi + k * (1 << 20), __double2loint(v))
+                                                               : v * si * sj;
+      }
+      A32[(int64_t)j * lda32 + i] = (float)vs;
     }
     const float av = fabsf((float)v);
     rsum_i += av;
@@ -105,10 +116,16 @@ __global__ void norm_max_kernel(const float *rsum, int n, RefineCtrl *ctrl) {
   }
 }
 
+// Diagonal scaling of the low-precision forms: s_i = 2^-q for a_ii = m 2^e (m in [1, 2)),
+// q = ceil(e / 2), so s_i^2 a_ii lies in [1/2, 2); 1 where a_ii <= 0 or is not finite. Powers
+// of two, as LAPACK's xPOEQUB chooses its factors, scale every entry without a rounding
+// error, and the scaled diagonal is within a factor two of Jacobi's unit one.
 __global__ void diag_scale_kernel(const double *A, int64_t lda, int n, double *scale) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const double d = A[(int64_t)i * lda + i];
-    scale[i] = d > 0.0 ? 1.0 / sqrt(d) : 1.0;
+    double s = 1.0;
+    if (d > 0.0 && isfinite(d)) s = ldexp(1.0, -((ilogb(d) + 1) >> 1));
+    scale[i] = s;
   }
 }
 

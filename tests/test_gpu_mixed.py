@@ -197,6 +197,31 @@ def test_refine_bf16_well_conditioned(chol):
 
 
 @pytest.mark.parametrize("precision", ["bf16", "bf16x3"])
+def test_refine_scaled_forms_wide_diagonal_and_zero_blocks(chol, precision):
+    # A = D M D with D = diag(2^u), u in [-40, 40], and M two independent Gram blocks (the
+    # off-diagonal blocks exactly zero): entries span 2^-80 .. 2^81, far outside what one
+    # FP32 exponent range keeps accurate together; the power-of-two diagonal scaling maps A
+    # back to a matrix within a factor two of M's scaling exactly (the zeros take the FP64
+    # product path of the conversion). Refinement must reach the FP64 target as on M.
+    n, nrhs = 512, 3
+    rng = np.random.default_rng(11)
+    M = np.zeros((n, n))
+    M[:256, :256] = synth.gram_spd(256, seed=12).numpy()
+    M[256:, 256:] = synth.gram_spd(256, seed=13).numpy()
+    d = np.ldexp(1.0, rng.integers(-40, 41, n))
+    A = d[:, None] * M * d[None, :]  # exact: powers of two
+    B = synth.rhs(n, nrhs, seed=14).numpy()
+    Ad = chol.colmajor(torch.from_numpy(A).to("cuda"))
+    Bd = chol.colmajor(torch.from_numpy(B).to("cuda"))
+    X, info, iters, berr = chol.solve_refine(Ad, Bd, tol=1e-14, max_iter=40, o=chol.opts(nb=128),
+                                             precision=precision)
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    assert oracle.backward_error(A, X.cpu().numpy(), B) <= 1e-14
+    assert float(berr.item()) <= 1e-14
+
+
+@pytest.mark.parametrize("precision", ["bf16", "bf16x3"])
 @pytest.mark.parametrize("n,nb", [(700, 80), (1100, 512)])
 def test_tc_register_staged_path(chol, precision, n, nb):
     # tiles that are not a multiple of 32, or larger than 256, have no pre-split side buffer:
