@@ -39,11 +39,12 @@ __device__ __forceinline__ void atomic_max_nonneg(double *p, double v) {
 }
 
 // One 32 x 32 tile (I, J), I >= J, of the lower triangle per block (32 x 8 threads): A32 =
-// float(A) (with `scale`, nullable: S A S with the powers of two of diag_scale_kernel, applied
-// exactly before rounding: v s_i s_j by adding the scales' exponents to v's, with no FP64
-// multiplication (FP64 arithmetic is slow on this part); the FP64 product, exact as well, covers zeros,
-// subnormals, infinities and results outside the normal range), and the absolute row sums of the symmetric A
-// accumulated into rsum: |a_ij| counts for row i and, below the diagonal, for row j. The sums
+// float(A) (with `scale`, nullable: S A S with the powers of two of diag_scale_kernel,
+// applied exactly before rounding: v s_i s_j by adding the scales' exponents to v's, with
+// no FP64 multiplication (FP64 arithmetic is slow on this part); the FP64 product, exact as
+// well, covers zeros, subnormals, infinities and results outside the normal range), and the
+// absolute row sums of the symmetric A accumulated into rsum: |a_ij| counts for row i and,
+// below the diagonal, for row j. The sums
 // are FP32 (the norm only scales the backward error, and FP64 adds would run on the FP64
 // pipe); entries above the diagonal of A32 are not written (nothing reads them).
 __global__ void __launch_bounds__(256) convert_lower_kernel(const double *A, int64_t lda, float *A32, int64_t lda32,
