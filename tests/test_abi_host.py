@@ -92,6 +92,18 @@ def test_lu_dag_matches_dataflow_oracle(T):
         assert all(int(s) > i for s in succ[ptr[i]:ptr[i + 1]])  # ids are a topological order
 
 
+def test_device_bottom_levels_reject_invalid_args():
+    # argument checks come before any CUDA call, so they run without a GPU
+    import paper_1402_6601_gb300 as chol
+    cost = np.array([1, 2, 3, 4], np.int64)
+    fake = ctypes.c_void_p(256)  # never dereferenced: every call below fails its checks first
+    for lu in (0, 1):
+        assert chol.lib.chol_dag_bottom_levels_device(lu, 0, cost.ctypes.data, fake, None) == -1
+        assert chol.lib.chol_dag_bottom_levels_device(lu, 1025, cost.ctypes.data, fake, None) == -1
+        assert chol.lib.chol_dag_bottom_levels_device(lu, 4, None, fake, None) == -1
+        assert chol.lib.chol_dag_bottom_levels_device(lu, 4, cost.ctypes.data, None, None) == -1
+
+
 @pytest.mark.parametrize("T", [1, 3, 6])
 def test_lu_bottom_levels_match_oracle(T):
     import paper_1402_6601_gb300 as chol
