@@ -210,8 +210,9 @@ size_t chol_factor_lowp_workspace_size(int precision, int n, const chol_opts *op
  * over the right-hand sides) with a factor in `low_precision` (CHOL_F32, CHOL_BF16 or
  * CHOL_BF16X3; others return CHOL_ERR_UNSUPPORTED) and at most max_iter refinement steps (the
  * first low-precision solve counts as one). The BF16 forms factor the diagonally scaled
- * matrix D^-1/2 A D^-1/2 (D = diag A, so every diagonal entry is 1 and every entry is in
- * [-1, 1]) and unscale each correction. Classical refinement converges when kappa(A) times
+ * matrix S A S, s_i the power of two with s_i^2 a_ii in [1/2, 2) (a_ii > 0; 1 otherwise), so
+ * the scaling adds no rounding error, every diagonal entry lies in [1/2, 2) and every entry
+ * in (-2, 2); they unscale each correction. Classical refinement converges when kappa(A) times
  * the factor's relative backward error is below 1: with plain BF16 operands (u = 2^-8) that
  * holds only for well-conditioned A; the steps are then taken to max_iter and *dBerr reports
  * the backward error reached.
