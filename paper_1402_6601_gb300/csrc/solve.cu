@@ -614,6 +614,11 @@ size_t solve_workspace_bytes(int n, int nrhs) { return solve_ws(n, nrhs); }
 template <class T>
 constexpr int item_rows() { return sizeof(T) == 4 ? 64 : 32; }
 
+// the widest instances fit one block's shared memory (227 KB of dynamic shared memory per
+// block, less the kernel's few static bytes)
+static_assert(SolveSmem<float, SG, 64>::BYTES <= 227 * 1024 - 512, "FP32 sweep shared memory");
+static_assert(SolveSmem<double, SG, 32>::BYTES <= 227 * 1024 - 512, "FP64 sweep shared memory");
+
 template <class T, int NC, int MODE>
 static cudaError_t launch_solve_mode(const SolveArgs &a, int grid, cudaStream_t s) {
   // one block per SM: the dynamic shared memory request (more than half an SM's) makes a
